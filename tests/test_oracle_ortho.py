@@ -1,0 +1,84 @@
+"""Pins of the oracle's orthogonality potential (Sec. 3.2, Eq. orthogonality,
+Eq. ortho-energy, Eq. ortho-poly) and of the per-body IP term (Sec. 4)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2201_10022_gb300 import scenes
+
+
+def _q(A, p=(0.0, 0.0, 0.0)):
+    return np.concatenate([np.asarray(p, float), np.asarray(A, float).reshape(-1)])
+
+
+def test_zero_on_rotations():
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        R = scenes.random_rotation(rng)
+        V, g, H = O.ortho(_q(R, rng.normal(size=3)), 1e8, 0.3)
+        assert abs(V) < 1e-20
+        assert np.abs(g).max() < 1e-6  # kappa*nu*|grad| ~ 1e8 * eps
+        assert np.abs(g).max() / (1e8 * 0.3) < 1e-14
+
+
+def test_energy_is_frobenius_definition():
+    rng = np.random.default_rng(2)
+    A = rng.normal(size=(3, 3))
+    V, _, _ = O.ortho(_q(A), 2.0, 0.5)
+    assert V == pytest.approx(2.0 * 0.5 * np.linalg.norm(A @ A.T - np.eye(3)) ** 2, rel=1e-13)
+
+
+def _fd(f, x, h):
+    g = np.zeros_like(x)
+    for i in range(len(x)):
+        e = np.zeros_like(x)
+        e[i] = h
+        g[i] = (f(x + e) - f(x - e)) / (2 * h)
+    return g
+
+
+def test_gradient_and_hessian_finite_differences():
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        q = _q(scenes.random_rotation(rng) + 0.05 * rng.normal(size=(3, 3)), rng.normal(size=3))
+        V, g, H = O.ortho(q, 1.0, 1.0)
+        gfd = _fd(lambda x: O.ortho(x, 1.0, 1.0)[0], q, 1e-6)
+        np.testing.assert_allclose(g, gfd, rtol=1e-6, atol=1e-9)
+        Hfd = np.stack([_fd(lambda x, i=i: O.ortho(x, 1.0, 1.0)[1][i], q, 1e-6) for i in range(12)])
+        np.testing.assert_allclose(H, Hfd, rtol=1e-6, atol=1e-8)
+        np.testing.assert_allclose(H, H.T, atol=1e-14)
+
+
+def test_paper_gradient_and_diagonal_block_forms():
+    """Eq. ortho-poly read with the sums over j != i:
+    dV/da_i = 2 kappa nu (2(a_i.a_i - 1) a_i + 2 sum_{j!=i} (a_j a_j^T) a_i),
+    d2V/da_i^2 = 2 kappa nu (4 a_i a_i^T + 2(|a_i|^2 - 1) I + 2 sum_{j!=i} a_j a_j^T);
+    the off-diagonal blocks the paper omits are 4 kappa nu (a_j a_i^T + (a_i.a_j) I)."""
+    rng = np.random.default_rng(4)
+    A = rng.normal(size=(3, 3))
+    k, nu = 3.0, 0.7
+    V, g, H = O.ortho(_q(A), k, nu)
+    for i in range(3):
+        ai = A[i]
+        s = sum(np.outer(A[j], A[j]) for j in range(3) if j != i)
+        gi = 2 * k * nu * (2 * (ai @ ai - 1) * ai + 2 * s @ ai)
+        np.testing.assert_allclose(g[3 + 3 * i:6 + 3 * i], gi, rtol=1e-12)
+        Hii = 2 * k * nu * (4 * np.outer(ai, ai) + 2 * (ai @ ai - 1) * np.eye(3) + 2 * s)
+        np.testing.assert_allclose(H[3 + 3 * i:6 + 3 * i, 3 + 3 * i:6 + 3 * i], Hii, rtol=1e-12, atol=1e-12)
+        for j in range(3):
+            if j == i:
+                continue
+            Hij = 4 * k * nu * (np.outer(A[j], ai) + (ai @ A[j]) * np.eye(3))
+            np.testing.assert_allclose(H[3 + 3 * i:6 + 3 * i, 3 + 3 * j:6 + 3 * j], Hij, rtol=1e-12, atol=1e-12)
+    assert np.abs(g[:3]).max() == 0 and np.abs(H[:3]).max() == 0
+
+
+def test_hessian_at_identity_has_six_zero_modes():
+    """At A = I the 9x9 block is PSD with exactly three zero eigenvalues (the
+    skew-symmetric directions); with p the 12x12 Hessian has six."""
+    V, g, H = O.ortho(_q(np.eye(3)), 1.0, 1.0)
+    w = np.linalg.eigvalsh(H)
+    assert (np.abs(w) < 1e-12).sum() == 6
+    assert w.min() > -1e-12
+    w9 = np.linalg.eigvalsh(H[3:, 3:])
+    assert (np.abs(w9) < 1e-12).sum() == 3
