@@ -1,0 +1,191 @@
+/* abd.h -- C ABI of the GB300 affine-body time-step library (libabd.so).
+ *
+ * The library computes one implicit time step of Affine Body Dynamics
+ * (Lan, Kaufman, Li, Jiang, Yang, "Affine Body Dynamics: Fast, Stable and
+ * Intersection-free Simulation of Stiff Materials", ACM TOG 2022):
+ * given the state (q^t, qdot^t) of affine bodies q_b = (p, a1, a2, a3)
+ * (Sec. 3, Eq. kinematic), it returns the minimiser of the incremental
+ * potential
+ *     E(q) = sum_b [ 1/2 |q_b - qtilde_b|_M^2 + dt^2 V_perp(q_b) ] + V_C(q) + V_F(q)
+ * (Sec. 4; V_perp Sec. 3.2 Eq. orthogonality; V_C Eq. barrier with the
+ * clamped log barrier Eq. clamped-b; V_F the friction potential of Sec. 4),
+ * reached by Newton iterations whose steps are filtered by additive CCD
+ * along linear vertex trajectories (Sec. 4.1) so the result is
+ * intersection-free, with contact pairs culled by d-hat-dilated boxes
+ * (Sec. 4.2) and the Hessian assembled as 12x12 body blocks (Sec. 4.3).
+ *
+ * Conventions shared by every call
+ *   Layout   q and qdot are 12 doubles per body, body-major:
+ *            q[12b+0..2] = p, q[12b+3+3i+c] = A[i][c] (rows of A, Sec. 3).
+ *            Static bodies keep their q and have no degrees of freedom.
+ *   Memory   *_dev pointers are device memory owned by the caller, borrowed
+ *            for the duration of the call; *_host pointers are host memory.
+ *            Descriptor arrays passed to abd_create_scene are copied; the
+ *            caller may free them when the call returns.
+ *   Streams  all device work is ordered on the CUDA stream given at
+ *            creation.  Calls that return host values synchronise it.
+ *   Errors   every call returns an abd_status; abd_last_error() gives a
+ *            message.  Kernels never trap: they record failures in a device
+ *            status word that the host reads.  A failed abd_step leaves the
+ *            scene state as it was before the call.
+ *   Numbers  the FP64 path decides pair membership and CCD step sizes with a
+ *            fixed operation order and reduces sums in a fixed order, so two
+ *            runs give bit-identical results.
+ */
+#ifndef ABD_H
+#define ABD_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define ABD_API __attribute__((visibility("default")))
+#else
+#define ABD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct abd_scene abd_scene;
+
+typedef enum {
+  ABD_OK = 0,
+  ABD_ERR_INVALID_ARG = 1,
+  ABD_ERR_CUDA = 2,
+  ABD_ERR_OOM = 3,
+  ABD_ERR_CAPACITY = 4,             /* internal buffer too small (the step retries with larger ones) */
+  ABD_ERR_INITIAL_INTERSECTION = 5, /* a contact pair at zero distance */
+  ABD_ERR_NONFINITE = 6,            /* NaN / Inf in the state or the system */
+  ABD_ERR_NEWTON_MAXITER = 7,
+  ABD_ERR_LINESEARCH = 8,
+  ABD_ERR_PCG_BREAKDOWN = 9,
+  ABD_ERR_PCG_MAXITER = 10,
+  ABD_ERR_CCD_MAXITER = 11
+} abd_status;
+
+/* Device allocator.  alloc returns device memory of `bytes` bytes usable on
+ * `stream` (NULL on failure); free releases it.  Passing NULL to
+ * abd_create_scene makes the library use cudaMalloc / cudaFree. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* ctx;
+} abd_allocator;
+
+/* Physical and solver parameters (Sec. 4 and Sec. 5.5 for d-hat). */
+typedef struct {
+  double dt;            /* time step (s) */
+  double dhat;          /* barrier activation distance d-hat (m) */
+  double kappa;         /* barrier stiffness of V_C */
+  double gravity[3];    /* m/s^2 */
+  double mu;            /* friction coefficient; 0 disables V_F */
+  double eps_v;         /* friction mollifier velocity (m/s); eps = eps_v * dt */
+  double newton_tol;    /* stop when max vertex |J dq| <= newton_tol (m); <= 0: 1e-5 x dynamic bbox diagonal x dt */
+  double pcg_rel_tol;   /* PCG relative residual */
+  double ls_slack_rel;  /* line search accepts E <= E0 + ls_slack_rel (|E0| + 1) */
+  double ccd_s;         /* ACCD gap fraction s (the step keeps >= s of each pair's distance) */
+  int newton_max, pcg_max, ls_max, ccd_max;
+  int precision;        /* 0: FP64 */
+} abd_params;
+
+/* Scene description (host arrays, copied).  Vertices, triangles and edges
+ * must be grouped by body in body order; tri / edge hold global vertex ids;
+ * each dynamic body's triangles form a closed, outward-oriented surface
+ * (its mass matrix comes from them by the divergence theorem, Sec. 3.1). */
+typedef struct {
+  int nb, nv, nt, ne;
+  const double* xbar;             /* nv*3 rest-frame positions */
+  const int* tri;                 /* nt*3 */
+  const int* edge;                /* ne*2 */
+  const int* vbody;               /* nv */
+  const double* q0;               /* nb*12 */
+  const double* qdot0;            /* nb*12 */
+  const double* density;          /* nb, kg/m^3 */
+  const double* kappa_body;       /* nb, orthogonality stiffness of V_perp */
+  const unsigned char* is_static; /* nb */
+} abd_scene_desc;
+
+typedef struct {
+  long n_candidates;   /* primitive pairs passing the box test (Sec. 4.2) */
+  long n_active;       /* pairs with d < d-hat (terms of V_C) */
+  long n_friction;     /* lagged friction pairs (terms of V_F) */
+  long n_body_pairs;   /* body pairs carrying an off-diagonal Hessian slot */
+} abd_pair_counts;
+
+typedef struct {
+  int iterations;
+  double rel_residual;
+} abd_solve_stats;
+
+typedef struct {
+  int newton_iters, pcg_iters, ls_halvings;
+  long n_candidates, n_active, n_swept;
+  double toi_min;      /* smallest CCD step bound seen in the step */
+  double last_step;    /* max vertex |J dq| of the last Newton step */
+} abd_step_stats;
+
+/* Fill *p with the defaults used by the benchmarks: dt 0.01, d-hat 1e-3,
+ * kappa 1e8, gravity (0,0,-9.8), mu 0, eps_v 1e-3, newton_tol 0 (relative),
+ * pcg_rel_tol 1e-4 (inexact Newton), ls_slack_rel 1e-12, ccd_s 0.1, caps 500/20000/30/10000. */
+ABD_API void abd_default_params(abd_params* p);
+
+/* Create a scene on the current CUDA device.  stream: a cudaStream_t (NULL =
+ * legacy default stream).  Validates the description (grouping, indices,
+ * closed meshes) and checks that no contact pair starts at zero distance
+ * (ABD_ERR_INITIAL_INTERSECTION).  *out receives the scene on success. */
+ABD_API abd_status abd_create_scene(const abd_scene_desc* desc, const abd_params* params, const abd_allocator* alloc,
+                            void* stream, abd_scene** out);
+
+/* Release every resource of the scene (NULL is accepted). */
+ABD_API void abd_destroy(abd_scene* s);
+
+/* Copy the state in (set) or out (get).  on_device != 0: q, qdot are device
+ * pointers; else host.  Setting the state recomputes qtilde (Sec. 4) and the
+ * lagged friction set.  Either pointer may be NULL on get. */
+ABD_API abd_status abd_set_state(abd_scene* s, const double* q, const double* qdot, int on_device);
+ABD_API abd_status abd_get_state(abd_scene* s, double* q, double* qdot, int on_device);
+
+/* Energy, gradient and projected Hessian of the incremental potential at q
+ * (Sec. 4 and Sec. 4.3), with qtilde and the friction set of the current
+ * state.  E_host[5] = {total, inertia, orthogonality, barrier, friction};
+ * g_dev: 12*nb doubles (zero rows for static bodies); counts may be NULL.
+ * The Hessian and the pair sets stay in the scene for abd_get_hessian,
+ * abd_get_pairs and abd_solve until the next call on the scene. */
+ABD_API abd_status abd_energy_grad_hess(abd_scene* s, const double* q_dev, double* E_host, double* g_dev,
+                                abd_pair_counts* counts);
+
+/* Copy the Hessian of the last abd_energy_grad_hess to the host:
+ * diag: nb*144 (row-major 12x12 per body; identity for static bodies);
+ * bi, bj, blocks: the off-diagonal blocks H[bi][bj] (bi < bj, row-major,
+ * rows = DOFs of bi), at most cap of them; *nblocks receives the count.
+ * Blocks may be zero (body pairs whose boxes are near but no pair is active). */
+ABD_API abd_status abd_get_hessian(abd_scene* s, double* diag, int* bi, int* bj, double* blocks, long cap, long* nblocks);
+
+/* Copy a pair set of the last abd_energy_grad_hess to the host: which = 0
+ * candidates, 1 active, 2 lagged friction.  kind 0 point-triangle (i vertex,
+ * j triangle), 1 edge-edge (i, j edges of bodies a < b); type: distance
+ * type (active and friction sets), d2: squared distance (active set).
+ * Arrays may be NULL to query the count only. */
+ABD_API abd_status abd_get_pairs(abd_scene* s, int which, int* kind, int* i, int* j, int* type, double* d2, long cap,
+                         long* n);
+
+/* Solve H dq = rhs with block-Jacobi PCG on the Hessian of the last
+ * abd_energy_grad_hess (the linear solve of each Newton iteration). */
+ABD_API abd_status abd_solve(abd_scene* s, const double* rhs_dev, double* dq_dev, abd_solve_stats* stats);
+
+/* Largest step alpha in (0, 1] such that the linear vertex trajectories from
+ * x(q) to x(q + alpha dq) are intersection-free by additive CCD (Sec. 4.1). */
+ABD_API abd_status abd_ccd_toi(abd_scene* s, const double* q_dev, const double* dq_dev, double* toi_host);
+
+/* Advance nsteps implicit-Euler time steps (Sec. 4); stats (may be NULL)
+ * receives the statistics of the last step. */
+ABD_API abd_status abd_step(abd_scene* s, int nsteps, abd_step_stats* stats);
+
+/* Message of the last error on the scene (empty string if none). */
+ABD_API const char* abd_last_error(const abd_scene* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

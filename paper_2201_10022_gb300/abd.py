@@ -1,0 +1,329 @@
+"""Python binding of libabd.so (include/abd.h): argument marshalling only.
+
+Every function named ``abd_*`` here calls the C function of the same name;
+all compute runs in the library's CUDA kernels.  PyTorch provides device
+memory (through the ``abd_allocator`` callbacks backed by its caching
+allocator) and the CUDA stream.  There is no CPU fallback: loading fails
+loudly when the library cannot be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+# ---------------------------------------------------------------------------
+# C structures (mirror include/abd.h)
+# ---------------------------------------------------------------------------
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+STATUS = {0: "ABD_OK", 1: "ABD_ERR_INVALID_ARG", 2: "ABD_ERR_CUDA", 3: "ABD_ERR_OOM", 4: "ABD_ERR_CAPACITY",
+          5: "ABD_ERR_INITIAL_INTERSECTION", 6: "ABD_ERR_NONFINITE", 7: "ABD_ERR_NEWTON_MAXITER",
+          8: "ABD_ERR_LINESEARCH", 9: "ABD_ERR_PCG_BREAKDOWN", 10: "ABD_ERR_PCG_MAXITER", 11: "ABD_ERR_CCD_MAXITER"}
+
+
+class abd_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class abd_params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double), ("gravity", C.c_double * 3),
+                ("mu", C.c_double), ("eps_v", C.c_double), ("newton_tol", C.c_double), ("pcg_rel_tol", C.c_double),
+                ("ls_slack_rel", C.c_double), ("ccd_s", C.c_double), ("newton_max", C.c_int), ("pcg_max", C.c_int),
+                ("ls_max", C.c_int), ("ccd_max", C.c_int), ("precision", C.c_int)]
+
+
+class abd_scene_desc(C.Structure):
+    _fields_ = [("nb", C.c_int), ("nv", C.c_int), ("nt", C.c_int), ("ne", C.c_int),
+                ("xbar", C.c_void_p), ("tri", C.c_void_p), ("edge", C.c_void_p), ("vbody", C.c_void_p),
+                ("q0", C.c_void_p), ("qdot0", C.c_void_p), ("density", C.c_void_p), ("kappa_body", C.c_void_p),
+                ("is_static", C.c_void_p)]
+
+
+class abd_pair_counts(C.Structure):
+    _fields_ = [("n_candidates", C.c_long), ("n_active", C.c_long), ("n_friction", C.c_long),
+                ("n_body_pairs", C.c_long)]
+
+
+class abd_solve_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double)]
+
+
+class abd_step_stats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int), ("pcg_iters", C.c_int), ("ls_halvings", C.c_int),
+                ("n_candidates", C.c_long), ("n_active", C.c_long), ("n_swept", C.c_long),
+                ("toi_min", C.c_double), ("last_step", C.c_double)]
+
+
+def _as_dict(st):
+    return {k: (list(getattr(st, k)) if isinstance(getattr(st, k), C.Array) else getattr(st, k))
+            for k, _ in st._fields_}
+
+
+_lib = None
+EXPORTS = ["abd_default_params", "abd_create_scene", "abd_destroy", "abd_set_state", "abd_get_state",
+           "abd_energy_grad_hess", "abd_get_hessian", "abd_get_pairs", "abd_solve", "abd_ccd_toi", "abd_step",
+           "abd_last_error"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libabd.so (compiling it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libabd.so not found at {path}: build it with paper_2201_10022_gb300.build.build()")
+    L = C.CDLL(path)
+    vp, i, l, d = C.c_void_p, C.c_int, C.c_long, C.c_double
+    sig = {
+        "abd_default_params": (None, [vp]),
+        "abd_create_scene": (i, [vp, vp, vp, vp, vp]),
+        "abd_destroy": (None, [vp]),
+        "abd_set_state": (i, [vp, vp, vp, i]),
+        "abd_get_state": (i, [vp, vp, vp, i]),
+        "abd_energy_grad_hess": (i, [vp, vp, vp, vp, vp]),
+        "abd_get_hessian": (i, [vp, vp, vp, vp, vp, l, vp]),
+        "abd_get_pairs": (i, [vp, i, vp, vp, vp, vp, vp, l, vp]),
+        "abd_solve": (i, [vp, vp, vp, vp]),
+        "abd_ccd_toi": (i, [vp, vp, vp, vp]),
+        "abd_step": (i, [vp, i, vp]),
+        "abd_last_error": (C.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+class AbdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+# ---------------------------------------------------------------------------
+# C-ABI functions, same names
+# ---------------------------------------------------------------------------
+
+def abd_default_params() -> abd_params:
+    p = abd_params()
+    load().abd_default_params(C.byref(p))
+    return p
+
+
+def abd_create_scene(desc: abd_scene_desc, params: abd_params, alloc, stream: int):
+    h = C.c_void_p()
+    r = load().abd_create_scene(C.byref(desc), C.byref(params), C.byref(alloc) if alloc is not None else None,
+                                C.c_void_p(stream), C.byref(h))
+    return r, h
+
+
+def abd_destroy(h):
+    load().abd_destroy(h)
+
+
+def abd_set_state(h, q_ptr, qdot_ptr, on_device):
+    return load().abd_set_state(h, C.c_void_p(q_ptr), C.c_void_p(qdot_ptr), int(on_device))
+
+
+def abd_get_state(h, q_ptr, qdot_ptr, on_device):
+    return load().abd_get_state(h, C.c_void_p(q_ptr), C.c_void_p(qdot_ptr), int(on_device))
+
+
+def abd_energy_grad_hess(h, q_ptr, E_host, g_ptr, counts):
+    return load().abd_energy_grad_hess(h, C.c_void_p(q_ptr), E_host, C.c_void_p(g_ptr), counts)
+
+
+def abd_get_hessian(h, diag, bi, bj, blocks, cap, nblocks):
+    return load().abd_get_hessian(h, diag, bi, bj, blocks, cap, nblocks)
+
+
+def abd_get_pairs(h, which, kind, i, j, type_, d2, cap, n):
+    return load().abd_get_pairs(h, which, kind, i, j, type_, d2, cap, n)
+
+
+def abd_solve(h, rhs_ptr, dq_ptr, stats):
+    return load().abd_solve(h, C.c_void_p(rhs_ptr), C.c_void_p(dq_ptr), stats)
+
+
+def abd_ccd_toi(h, q_ptr, dq_ptr, toi):
+    return load().abd_ccd_toi(h, C.c_void_p(q_ptr), C.c_void_p(dq_ptr), toi)
+
+
+def abd_step(h, nsteps, stats):
+    return load().abd_step(h, int(nsteps), stats)
+
+
+def abd_last_error(h) -> str:
+    s = load().abd_last_error(h)
+    return s.decode() if s else ""
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper over one scene (torch tensors in, numpy / torch out)
+# ---------------------------------------------------------------------------
+
+def _np_ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+class TorchAllocator:
+    """abd_allocator backed by PyTorch's caching allocator."""
+
+    def __init__(self, device):
+        import torch
+        self._torch = torch
+        self.device = torch.device(device)
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device.index, stream)
+            except Exception:  # out of memory: report NULL to the library
+                return None
+
+        def _free(ptr, stream, ctx):
+            self._torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc_cb = ALLOC_FN(_alloc)
+        self._free_cb = FREE_FN(_free)
+        self.struct = abd_allocator(self._alloc_cb, self._free_cb, None)
+
+
+class AbdScene:
+    """A scene of the CUDA library (one GPU, one stream).
+
+    ``scene`` is a :class:`paper_2201_10022_gb300.scenes.Scene`; keyword
+    arguments override fields of :func:`abd_default_params`."""
+
+    def __init__(self, scene, device="cuda:0", stream=None, torch_alloc=True, **params):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.scene = scene
+        self.nb = scene.nb
+        p = abd_default_params()
+        prm = dict(scene.params)
+        prm.update(params)
+        for k, v in prm.items():
+            if k == "gravity":
+                p.gravity[:] = list(v)
+            elif hasattr(p, k):
+                setattr(p, k, v)
+        self.params = p
+        self._keep = [np.ascontiguousarray(scene.xbar, dtype=np.float64),
+                      np.ascontiguousarray(scene.tri, dtype=np.int32),
+                      np.ascontiguousarray(scene.edge, dtype=np.int32),
+                      np.ascontiguousarray(scene.vbody, dtype=np.int32),
+                      np.ascontiguousarray(scene.q0, dtype=np.float64),
+                      np.ascontiguousarray(scene.qdot0, dtype=np.float64),
+                      np.ascontiguousarray(scene.density, dtype=np.float64),
+                      np.ascontiguousarray(scene.kappa_body, dtype=np.float64),
+                      np.ascontiguousarray(scene.is_static, dtype=np.uint8)]
+        d = abd_scene_desc(scene.nb, scene.nv, scene.nt, scene.ne, *[_np_ptr(a) for a in self._keep])
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.alloc = TorchAllocator(self.device) if torch_alloc else None
+            r, h = abd_create_scene(d, p, self.alloc.struct if self.alloc else None, self.stream.cuda_stream)
+        if r != 0:
+            raise AbdError(r, "abd_create_scene failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            with self.torch.cuda.device(self.device):
+                abd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, r):
+        if r != 0:
+            raise AbdError(r, abd_last_error(self.h))
+
+    def _dev(self, t):
+        t = self.torch.as_tensor(t, dtype=self.torch.float64, device=self.device).contiguous()
+        return t
+
+    # state -----------------------------------------------------------------
+    def set_state(self, q, qdot):
+        q, qd = self._dev(q), self._dev(qdot)
+        with self.torch.cuda.device(self.device):
+            self._check(abd_set_state(self.h, q.data_ptr(), qd.data_ptr(), 1))
+
+    def get_state(self):
+        q = self.torch.empty((self.nb, 12), dtype=self.torch.float64, device=self.device)
+        qd = self.torch.empty_like(q)
+        with self.torch.cuda.device(self.device):
+            self._check(abd_get_state(self.h, q.data_ptr(), qd.data_ptr(), 1))
+        return q, qd
+
+    # parity entry points ------------------------------------------------------
+    def energy_grad_hess(self, q):
+        q = self._dev(q)
+        g = self.torch.empty((self.nb, 12), dtype=self.torch.float64, device=self.device)
+        E = (C.c_double * 5)()
+        cnt = abd_pair_counts()
+        with self.torch.cuda.device(self.device):
+            self._check(abd_energy_grad_hess(self.h, q.data_ptr(), E, g.data_ptr(), C.byref(cnt)))
+        return np.array(E[:]), g, _as_dict(cnt)
+
+    def hessian(self):
+        n = C.c_long()
+        self._check(abd_get_hessian(self.h, None, None, None, None, 0, C.byref(n)))
+        m = max(n.value, 1)
+        diag = np.zeros((self.nb, 12, 12))
+        bi = np.zeros(m, np.int32)
+        bj = np.zeros(m, np.int32)
+        blocks = np.zeros((m, 12, 12))
+        self._check(abd_get_hessian(self.h, _np_ptr(diag), _np_ptr(bi), _np_ptr(bj), _np_ptr(blocks), m,
+                                    C.byref(n)))
+        k = n.value
+        return diag, np.stack([bi[:k], bj[:k]], axis=1), blocks[:k]
+
+    def pairs(self, which=1):
+        n = C.c_long()
+        self._check(abd_get_pairs(self.h, which, None, None, None, None, None, 0, C.byref(n)))
+        m = max(n.value, 1)
+        kind, pi, pj, ty = (np.zeros(m, np.int32) for _ in range(4))
+        d2 = np.zeros(m)
+        self._check(abd_get_pairs(self.h, which, _np_ptr(kind), _np_ptr(pi), _np_ptr(pj), _np_ptr(ty), _np_ptr(d2),
+                                  m, C.byref(n)))
+        k = n.value
+        return dict(kind=kind[:k], i=pi[:k], j=pj[:k], type=ty[:k], val=d2[:k])
+
+    def solve(self, rhs):
+        rhs = self._dev(rhs)
+        dq = self.torch.empty_like(rhs)
+        st = abd_solve_stats()
+        with self.torch.cuda.device(self.device):
+            r = abd_solve(self.h, rhs.data_ptr(), dq.data_ptr(), C.byref(st))
+        self._check(r)
+        return dq, _as_dict(st)
+
+    def ccd_toi(self, q, dq):
+        q, dq = self._dev(q), self._dev(dq)
+        t = C.c_double()
+        with self.torch.cuda.device(self.device):
+            self._check(abd_ccd_toi(self.h, q.data_ptr(), dq.data_ptr(), C.byref(t)))
+        return t.value
+
+    def step(self, n=1):
+        st = abd_step_stats()
+        with self.torch.cuda.device(self.device):
+            self._check(abd_step(self.h, n, C.byref(st)))
+        return _as_dict(st)

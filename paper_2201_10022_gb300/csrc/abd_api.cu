@@ -1,0 +1,787 @@
+// C ABI of the affine-body library and the host driver of the time step:
+// Newton iterations on the incremental potential (Sec. 4) with the linear
+// solve, the CCD step bound (Sec. 4.1) and a backtracking line search, all
+// enqueued on the scene's stream; the host reads the device status word
+// once per Newton iteration and once per line-search trial.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "abd_internal.cuh"
+
+namespace abd {
+
+void* Alloc::get(size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (custom) return a.alloc(bytes, (void*)stream, a.ctx);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  return p;
+}
+
+void Alloc::put(void* p) {
+  if (!p) return;
+  if (custom) a.free(p, (void*)stream, a.ctx);
+  else cudaFree(p);
+}
+
+namespace {
+
+struct OomError {};
+
+template <typename T>
+void grow(Scene& s, Buf<T>& b, size_t n) {
+  if (b.cap >= n && b.p) return;
+  if (b.p) {
+    cudaStreamSynchronize(s.stream);
+    s.alloc.put(b.p);
+  }
+  b.p = (T*)s.alloc.get(sizeof(T) * (n ? n : 1));
+  b.cap = n;
+  if (!b.p) throw OomError{};
+}
+
+template <typename T>
+void release(Scene& s, Buf<T>& b) {
+  s.alloc.put(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+// buffers whose size follows the body-pair capacity, the candidates per pair
+// and the active-term capacity
+void size_pair_buffers(Scene& s, size_t pcap) {
+  grow(s, s.P, pcap);
+  grow(s, s.ccount, pcap);
+  grow(s, s.acount, pcap);
+  grow(s, s.aoff, pcap + 1);
+  grow(s, s.in_list, pcap);
+  grow(s, s.pblk, pcap * kBlkStride);
+  grow(s, s.fpairs, pcap);
+  grow(s, s.fpoff, pcap + 1);
+  grow(s, s.flagbuf, pcap);
+  grow(s, s.posbuf, pcap + 1);
+  grow(s, s.Epair, pcap);
+  grow(s, s.cand, pcap * (size_t)s.maxc);
+  grow(s, s.act, pcap * (size_t)s.maxc);
+  grow(s, s.act_d2, pcap * (size_t)s.maxc);
+}
+
+void size_term_buffers(Scene& s, size_t tcap) {
+  grow(s, s.term, tcap * kTermStride);
+  grow(s, s.termv, tcap);
+  grow(s, s.fric, tcap);
+  grow(s, s.fterm, tcap * kTermStride);
+  grow(s, s.ftermv, tcap);
+}
+
+size_t term_cap(const Scene& s) { return s.termv.cap; }
+
+void reset_status(Scene& s) {
+  // clear flags and per-pass counters, keep np / nact / nfr / nfp
+  DevStatus h;
+  memset(&h, 0, sizeof(h));
+  cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
+  cudaStreamSynchronize(s.stream);
+  h = *s.st_host;
+  h.flags = 0;
+  h.need_row = h.need_cand = 0;
+  h.need_pairs = h.need_act = h.need_misc = 0;
+  double one = 1.0;
+  memcpy(&h.toi_bits, &one, 8);
+  h.step_bits = 0;
+  h.n_cand = 0;
+  *s.st_host = h;
+  cudaMemcpyAsync(s.st, s.st_host, sizeof(DevStatus), cudaMemcpyHostToDevice, s.stream);
+}
+
+void read_status(Scene& s) {
+  cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
+  cudaStreamSynchronize(s.stream);
+}
+
+void set_counter(Scene& s, int* field, int v) { cudaMemcpyAsync(field, &v, sizeof(int), cudaMemcpyHostToDevice, s.stream); }
+
+double bits_to_double(unsigned long long b) {
+  double d;
+  memcpy(&d, &b, 8);
+  return d;
+}
+
+// grow every buffer whose capacity flag is raised; returns true if any grew
+bool handle_capacity(Scene& s) {
+  const DevStatus& h = *s.st_host;
+  bool grew = false;
+  if (h.flags & ST_CAP_ROWS) {
+    s.maxn = std::max(2 * s.maxn, h.need_row + 16);
+    grow(s, s.nbr, (size_t)s.nb * s.maxn);
+    grew = true;
+  }
+  size_t pcap = s.P.cap;
+  if (h.flags & ST_CAP_PAIRS) {
+    pcap = std::max<size_t>(2 * pcap, (size_t)(1.5 * (double)std::max(h.need_pairs, h.need_misc)) + 64);
+    grew = true;
+  }
+  if (h.flags & ST_CAP_CANDS) {
+    s.maxc = std::max(2 * s.maxc, h.need_cand + 64);
+    release(s, s.cand);
+    release(s, s.act);
+    release(s, s.act_d2);
+    grew = true;
+  }
+  if (grew) size_pair_buffers(s, pcap);
+  if (h.flags & ST_CAP_ACTIVE) {
+    size_term_buffers(s, std::max<size_t>(2 * term_cap(s), (size_t)(1.5 * (double)h.need_act) + 64));
+    grew = true;
+  }
+  return grew;
+}
+
+abd_status check_cuda(Scene& s) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    s.err = std::string("CUDA error: ") + cudaGetErrorString(e);
+    return ABD_ERR_CUDA;
+  }
+  return ABD_OK;
+}
+
+// ---- pipeline stages --------------------------------------------------------
+
+// body pairs and their candidate pairs at s.x (static) or over s.x -> s.x1
+// (swept, with additive CCD when ccd is set)
+void broad_and_enumerate(Scene& s, bool swept, bool ccd) {
+  cudaMemsetAsync(&s.st->n_cand, 0, sizeof(unsigned long long), s.stream);
+  launch_body_boxes(s, swept);
+  launch_body_pairs(s);
+  launch_enumerate(s, swept, ccd);
+}
+
+// actives, terms, assembly and preconditioner at positions s.x (from q)
+void eval_system(Scene& s, const double* q, int project) {
+  launch_active(s, s.x.p);
+  launch_scan(s, s.acount.p, s.aoff.p, &s.st->np, &s.st->nact, (long)term_cap(s), ST_CAP_ACTIVE, &s.st->need_act);
+  launch_barrier(s, project, (long)term_cap(s));
+  launch_friction_eval(s, s.x.p, true);
+  launch_incoming(s);
+  launch_assemble(s);
+  launch_body_terms(s, q, true);
+  launch_gather(s);
+  launch_precond(s);
+  launch_energy_total(s, true);
+}
+
+// energy only at positions s.xt (from qv), over the stored candidates
+void eval_energy(Scene& s, const double* qv) {
+  launch_pair_energy(s, s.xt.p);
+  launch_friction_eval(s, s.xt.p, false);
+  launch_body_terms(s, qv, false);
+  launch_energy_total(s, false);
+}
+
+// lag friction at q^t: proximity pairs at x(q^t), one record per active pair
+void lag_friction(Scene& s) {
+  set_counter(s, &s.st->nfp, 0);
+  set_counter(s, &s.st->nfr, 0);
+  if (!(s.prm.mu > 0.0)) return;
+  launch_transform(s, s.qt.p, s.x.p);
+  broad_and_enumerate(s, false, false);
+  launch_active(s, s.x.p);
+  launch_scan(s, s.acount.p, s.aoff.p, &s.st->np, &s.st->nact, (long)term_cap(s), ST_CAP_ACTIVE, &s.st->need_act);
+  launch_friction_lag(s);
+  launch_fpairs(s);
+}
+
+abd_status flags_to_status(Scene& s, unsigned f) {
+  if (f & ST_INTERSECT) {
+    s.err = "a contact pair reached zero distance";
+    return ABD_ERR_INITIAL_INTERSECTION;
+  }
+  if (f & ST_NONFINITE) {
+    s.err = "non-finite value in the state or the system";
+    return ABD_ERR_NONFINITE;
+  }
+  if (f & ST_CCD_MAXITER) {
+    s.err = "additive CCD iteration cap reached";
+    return ABD_ERR_CCD_MAXITER;
+  }
+  return ABD_OK;
+}
+
+const unsigned kCapFlags = ST_CAP_ROWS | ST_CAP_CANDS | ST_CAP_PAIRS | ST_CAP_ACTIVE;
+
+// run fn until no capacity flag is raised (buffers grow in between)
+template <typename F>
+abd_status with_capacity(Scene& s, F fn) {
+  for (int attempt = 0; attempt < 12; ++attempt) {
+    reset_status(s);
+    abd_status r = fn();
+    if (r != ABD_OK && r != ABD_ERR_CAPACITY) return r;
+    read_status(s);
+    if (abd_status c = check_cuda(s)) return c;
+    if (!(s.st_host->flags & kCapFlags)) return r;
+    handle_capacity(s);
+  }
+  s.err = "buffer capacity did not converge";
+  return ABD_ERR_CAPACITY;
+}
+
+// one implicit-Euler step from (q^t, qdot^t); on error the state is unchanged
+abd_status newton_step(Scene& s, abd_step_stats* stats) {
+  const size_t qb = sizeof(double) * 12 * s.nb;
+  cudaMemcpyAsync(s.q.p, s.qt.p, qb, cudaMemcpyDeviceToDevice, s.stream);
+  abd_step_stats loc;
+  memset(&loc, 0, sizeof(loc));
+  loc.toi_min = 1.0;
+  launch_transform(s, s.q.p, s.x.p);
+  broad_and_enumerate(s, false, false);
+  abd_status status = ABD_ERR_NEWTON_MAXITER;
+  for (int it = 0; it < s.prm.newton_max; ++it) {
+    launch_transform(s, s.q.p, s.x.p);
+    eval_system(s, s.q.p, 1);
+    read_status(s);
+    if (s.st_host->flags & kCapFlags) return ABD_ERR_CAPACITY;
+    if (abd_status r = flags_to_status(s, s.st_host->flags)) return r;
+    loc.n_active = s.st_host->nact;
+    loc.n_candidates = (long)s.st_host->n_cand;
+    // Newton direction: H dq = -g
+    launch_negate(s, s.g.p, s.qsave.p, 12L * s.nb);
+    double rel;
+    int its = run_pcg(s, s.qsave.p, s.dq.p, s.prm.pcg_max, s.prm.pcg_rel_tol, &rel);
+    if (its == -2) {
+      s.err = "PCG breakdown";
+      return ABD_ERR_PCG_BREAKDOWN;
+    }
+    loc.pcg_iters += its < 0 ? s.prm.pcg_max : its;
+    // convergence on the vertex-space step, before the line search
+    launch_transform_dq(s, s.dq.p);
+    cudaMemsetAsync(&s.st->step_bits, 0, sizeof(unsigned long long), s.stream);
+    launch_max_step(s);
+    read_status(s);
+    double step = bits_to_double(s.st_host->step_bits);
+    loc.last_step = step;
+    if (!(step == step)) {
+      s.err = "non-finite Newton step";
+      return ABD_ERR_NONFINITE;
+    }
+    if (step <= s.newton_tol) {
+      status = ABD_OK;
+      break;
+    }
+    loc.newton_iters++;
+    // CCD bound over the swept candidates; they also serve the next iteration
+    {
+      DevStatus& h = *s.st_host;
+      double one = 1.0;
+      memcpy(&h.toi_bits, &one, 8);
+      h.n_cand = 0;
+      cudaMemcpyAsync(&s.st->toi_bits, &h.toi_bits, 16, cudaMemcpyHostToDevice, s.stream);
+    }
+    broad_and_enumerate(s, true, true);
+    read_status(s);
+    if (s.st_host->flags & kCapFlags) return ABD_ERR_CAPACITY;
+    if (abd_status r = flags_to_status(s, s.st_host->flags)) return r;
+    double alpha = bits_to_double(s.st_host->toi_bits);
+    loc.n_swept = (long)s.st_host->n_cand;
+    loc.toi_min = std::min(loc.toi_min, alpha);
+    // line search: E(q + alpha dq) <= E(q) + slack over the swept candidates
+    cudaMemcpyAsync(s.xt.p, s.x.p, sizeof(double4) * s.nv, cudaMemcpyDeviceToDevice, s.stream);
+    eval_energy(s, s.q.p);
+    read_status(s);
+    const double E0 = s.st_host->energy[0];
+    const double slack = s.prm.ls_slack_rel * (fabs(E0) + 1.0);
+    bool ok = false;
+    for (int ls = 0; ls <= s.prm.ls_max; ++ls) {
+      launch_trial(s, alpha);
+      launch_transform(s, s.qtrial.p, s.xt.p);
+      eval_energy(s, s.qtrial.p);
+      read_status(s);
+      if (s.st_host->flags & ST_INTERSECT) {
+        s.err = "line search reached zero distance";
+        return ABD_ERR_INITIAL_INTERSECTION;
+      }
+      double E = s.st_host->energy[0];
+      if (E <= E0 + slack) {
+        ok = true;
+        break;
+      }
+      alpha *= 0.5;
+      loc.ls_halvings++;
+    }
+    if (!ok) {
+      s.err = "line search did not decrease the energy";
+      return ABD_ERR_LINESEARCH;
+    }
+    std::swap(s.q, s.qtrial);
+  }
+  if (status != ABD_OK) {
+    if (s.err.empty()) s.err = "Newton iteration cap reached";
+    return status;
+  }
+  launch_finish_step(s);
+  if (stats) *stats = loc;
+  return ABD_OK;
+}
+
+}  // namespace
+}  // namespace abd
+
+using namespace abd;
+
+struct abd_scene {
+  Scene s;
+};
+
+extern "C" {
+
+void abd_default_params(abd_params* p) {
+  memset(p, 0, sizeof(*p));
+  p->dt = 0.01;
+  p->dhat = 1e-3;
+  p->kappa = 1e8;
+  p->gravity[2] = -9.8;
+  p->mu = 0.0;
+  p->eps_v = 1e-3;
+  p->newton_tol = 0.0;
+  p->pcg_rel_tol = 1e-4;
+  p->ls_slack_rel = 1e-12;
+  p->ccd_s = 0.1;
+  p->newton_max = 500;
+  p->pcg_max = 20000;
+  p->ls_max = 30;
+  p->ccd_max = 10000;
+  p->precision = 0;
+}
+
+static bool grouped(const int* owner, int n, int nb, std::vector<int>& beg) {
+  beg.assign(nb + 1, 0);
+  int prev = 0;
+  std::vector<int> cnt(nb, 0);
+  for (int k = 0; k < n; ++k) {
+    int b = owner[k];
+    if (b < 0 || b >= nb || b < prev) return false;
+    prev = b;
+    cnt[b]++;
+  }
+  for (int b = 0; b < nb; ++b) beg[b + 1] = beg[b] + cnt[b];
+  return true;
+}
+
+abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, const abd_allocator* alloc,
+                            void* stream, abd_scene** out) {
+  if (!d || !prm || !out || d->nb <= 0 || d->nv <= 0 || d->nt < 0 || d->ne < 0 || !d->xbar || !d->vbody ||
+      !d->q0 || !d->qdot0 || !d->density || !d->kappa_body || !d->is_static || (d->nt && !d->tri) ||
+      (d->ne && !d->edge))
+    return ABD_ERR_INVALID_ARG;
+  if (!(prm->dt > 0) || !(prm->dhat > 0) || !(prm->kappa > 0) || prm->newton_max <= 0 || prm->pcg_max <= 0 ||
+      prm->ls_max < 0 || prm->ccd_max <= 0 || !(prm->ccd_s > 0 && prm->ccd_s < 1) || prm->precision != 0)
+    return ABD_ERR_INVALID_ARG;
+  const int nb = d->nb, nv = d->nv, nt = d->nt, ne = d->ne;
+  std::vector<int> vbeg, tbeg, ebeg, towner(nt), eowner(ne);
+  for (int t = 0; t < nt; ++t) {
+    for (int k = 0; k < 3; ++k)
+      if (d->tri[3 * t + k] < 0 || d->tri[3 * t + k] >= nv) return ABD_ERR_INVALID_ARG;
+    towner[t] = d->vbody[d->tri[3 * t]];
+    if (d->vbody[d->tri[3 * t + 1]] != towner[t] || d->vbody[d->tri[3 * t + 2]] != towner[t])
+      return ABD_ERR_INVALID_ARG;
+  }
+  for (int e = 0; e < ne; ++e) {
+    for (int k = 0; k < 2; ++k)
+      if (d->edge[2 * e + k] < 0 || d->edge[2 * e + k] >= nv) return ABD_ERR_INVALID_ARG;
+    eowner[e] = d->vbody[d->edge[2 * e]];
+    if (d->vbody[d->edge[2 * e + 1]] != eowner[e]) return ABD_ERR_INVALID_ARG;
+  }
+  if (!grouped(d->vbody, nv, nb, vbeg) || !grouped(towner.data(), nt, nb, tbeg) ||
+      !grouped(eowner.data(), ne, nb, ebeg))
+    return ABD_ERR_INVALID_ARG;
+  for (int k = 0; k < 12 * nb; ++k)
+    if (!std::isfinite(d->q0[k]) || !std::isfinite(d->qdot0[k])) return ABD_ERR_NONFINITE;
+
+  abd_scene* S = new abd_scene();
+  Scene& s = S->s;
+  s.prm = *prm;
+  s.nb = nb;
+  s.nv = nv;
+  s.nt = nt;
+  s.ne = ne;
+  s.stream = (cudaStream_t)stream;
+  s.alloc.stream = s.stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    s.alloc.a = *alloc;
+    s.alloc.custom = true;
+  }
+  try {
+    grow(s, s.xbar, nv);
+    grow(s, s.vbody, nv);
+    grow(s, s.tri, 3L * nt + 1);
+    grow(s, s.edge, 2L * ne + 1);
+    grow(s, s.vbeg, nb + 1);
+    grow(s, s.tbeg, nb + 1);
+    grow(s, s.ebeg, nb + 1);
+    grow(s, s.is_static, nb);
+    grow(s, s.mass10, 10L * nb);
+    grow(s, s.vol, nb);
+    grow(s, s.kappa_b, nb);
+    grow(s, s.density, nb);
+    for (Buf<double>* b : {&s.q, &s.qdot, &s.qt, &s.qtilde, &s.dq, &s.qtrial, &s.qsave, &s.qdotsave, &s.gb, &s.g,
+                           &s.r, &s.z, &s.pv, &s.Ap})
+      grow(s, *b, 12L * nb);
+    grow(s, s.Eb, 2L * nb);
+    for (Buf<double>* b : {&s.Db, &s.D, &s.Pinv}) grow(s, *b, 144L * nb);
+    grow(s, s.part, 2L * nb + 1024);
+    for (Buf<double4>* b : {&s.x, &s.dx, &s.x1, &s.xt}) grow(s, *b, nv);
+    grow(s, s.bbox, 6L * nb);
+    s.maxn = 64;
+    grow(s, s.nbr, (size_t)nb * s.maxn);
+    grow(s, s.ncount, nb);
+    grow(s, s.rowoff, nb + 1);
+    grow(s, s.in_off, nb + 1);
+    grow(s, s.in_cnt, nb);
+    s.maxc = 256;
+    size_pair_buffers(s, std::max<size_t>(1024, 8L * nb));
+    size_term_buffers(s, std::max<size_t>(4096, 16L * nb));
+    if (cudaMalloc(&s.st, sizeof(DevStatus)) != cudaSuccess) throw OomError{};
+    if (cudaMallocHost(&s.st_host, sizeof(DevStatus)) != cudaSuccess) throw OomError{};
+  } catch (OomError&) {
+    abd_destroy(S);
+    return ABD_ERR_OOM;
+  }
+  std::vector<double4> xb(nv);
+  for (int v = 0; v < nv; ++v) xb[v] = make_double4(d->xbar[3 * v], d->xbar[3 * v + 1], d->xbar[3 * v + 2], 0.0);
+  cudaMemcpyAsync(s.xbar.p, xb.data(), sizeof(double4) * nv, cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.vbody.p, d->vbody, sizeof(int) * nv, cudaMemcpyHostToDevice, s.stream);
+  if (nt) cudaMemcpyAsync(s.tri.p, d->tri, sizeof(int) * 3 * nt, cudaMemcpyHostToDevice, s.stream);
+  if (ne) cudaMemcpyAsync(s.edge.p, d->edge, sizeof(int) * 2 * ne, cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.vbeg.p, vbeg.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.tbeg.p, tbeg.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.ebeg.p, ebeg.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.is_static.p, d->is_static, nb, cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.kappa_b.p, d->kappa_body, sizeof(double) * nb, cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.density.p, d->density, sizeof(double) * nb, cudaMemcpyHostToDevice, s.stream);
+  DevStatus z;
+  memset(&z, 0, sizeof(z));
+  *s.st_host = z;
+  cudaMemcpyAsync(s.st, s.st_host, sizeof(DevStatus), cudaMemcpyHostToDevice, s.stream);
+  launch_mass_moments(s);
+  s.ndyn = 0;
+  for (int b = 0; b < nb; ++b) s.ndyn += d->is_static[b] ? 0 : 1;
+  // Newton tolerance (the paper states none): IPC's rule |dx|_inf <= 1e-5 l dt,
+  // l the diagonal of the dynamic bodies' box at q0
+  s.newton_tol = prm->newton_tol;
+  if (!(s.newton_tol > 0)) {
+    cudaMemcpyAsync(s.qt.p, d->q0, sizeof(double) * 12 * nb, cudaMemcpyHostToDevice, s.stream);
+    launch_transform(s, s.qt.p, s.x.p);
+    launch_body_boxes(s, false);
+    std::vector<double> bb(6L * nb);
+    cudaMemcpyAsync(bb.data(), s.bbox.p, sizeof(double) * 6 * nb, cudaMemcpyDeviceToHost, s.stream);
+    cudaStreamSynchronize(s.stream);
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int b = 0; b < nb; ++b) {
+      if (d->is_static[b]) continue;
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = std::min(lo[k], bb[6 * b + k]);
+        hi[k] = std::max(hi[k], bb[6 * b + 3 + k]);
+      }
+    }
+    double l2 = 0;
+    for (int k = 0; k < 3; ++k) l2 += s.ndyn ? (hi[k] - lo[k]) * (hi[k] - lo[k]) : 0.0;
+    s.newton_tol = 1e-5 * std::max(sqrt(l2), 1e-3) * prm->dt;
+  }
+  abd_status r = abd_set_state(S, d->q0, d->qdot0, 0);
+  if (r != ABD_OK) {
+    abd_destroy(S);
+    return r;
+  }
+  // no pair may start at zero distance
+  r = with_capacity(s, [&]() {
+    launch_transform(s, s.qt.p, s.x.p);
+    broad_and_enumerate(s, false, false);
+    launch_active(s, s.x.p);
+    return ABD_OK;
+  });
+  if (r == ABD_OK && (s.st_host->flags & ST_INTERSECT)) r = ABD_ERR_INITIAL_INTERSECTION;
+  if (r == ABD_OK) r = check_cuda(s);
+  if (r != ABD_OK) {
+    abd_destroy(S);
+    return r;
+  }
+  *out = S;
+  return ABD_OK;
+}
+
+void abd_destroy(abd_scene* S) {
+  if (!S) return;
+  Scene& s = S->s;
+  if (s.stream || s.st) cudaStreamSynchronize(s.stream);
+  release(s, s.xbar);
+  release(s, s.vbody);
+  release(s, s.tri);
+  release(s, s.edge);
+  release(s, s.vbeg);
+  release(s, s.tbeg);
+  release(s, s.ebeg);
+  release(s, s.is_static);
+  release(s, s.mass10);
+  release(s, s.vol);
+  release(s, s.kappa_b);
+  release(s, s.density);
+  for (Buf<double>* b : {&s.q, &s.qdot, &s.qt, &s.qtilde, &s.dq, &s.qtrial, &s.qsave, &s.qdotsave, &s.gb, &s.g, &s.r,
+                         &s.z, &s.pv, &s.Ap, &s.Eb, &s.Db, &s.D, &s.Pinv, &s.part, &s.bbox, &s.term, &s.fterm,
+                         &s.pblk, &s.Epair, &s.act_d2, &s.red})
+    release(s, *b);
+  for (Buf<double4>* b : {&s.x, &s.dx, &s.x1, &s.xt}) release(s, *b);
+  for (Buf<int>* b : {&s.nbr, &s.ncount, &s.rowoff, &s.in_off, &s.in_cnt, &s.in_list, &s.ccount, &s.acount, &s.aoff,
+                      &s.fpoff, &s.flagbuf, &s.posbuf})
+    release(s, *b);
+  release(s, s.P);
+  release(s, s.fpairs);
+  release(s, s.cand);
+  release(s, s.act);
+  release(s, s.termv);
+  release(s, s.ftermv);
+  release(s, s.fric);
+  if (s.st) cudaFree(s.st);
+  if (s.st_host) cudaFreeHost(s.st_host);
+  delete S;
+}
+
+abd_status abd_set_state(abd_scene* S, const double* q, const double* qdot, int on_device) {
+  if (!S || !q || !qdot) return ABD_ERR_INVALID_ARG;
+  Scene& s = S->s;
+  s.err.clear();
+  const size_t qb = sizeof(double) * 12 * s.nb;
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaMemcpyAsync(s.qt.p, q, qb, k, s.stream);
+  cudaMemcpyAsync(s.qdot.p, qdot, qb, k, s.stream);
+  launch_predictor(s);
+  s.have_hess = false;
+  abd_status r = with_capacity(s, [&]() {
+    lag_friction(s);
+    return ABD_OK;
+  });
+  if (r == ABD_OK) r = check_cuda(s);
+  return r;
+}
+
+abd_status abd_get_state(abd_scene* S, double* q, double* qdot, int on_device) {
+  if (!S) return ABD_ERR_INVALID_ARG;
+  Scene& s = S->s;
+  const size_t qb = sizeof(double) * 12 * s.nb;
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (q) cudaMemcpyAsync(q, s.qt.p, qb, k, s.stream);
+  if (qdot) cudaMemcpyAsync(qdot, s.qdot.p, qb, k, s.stream);
+  cudaStreamSynchronize(s.stream);
+  return check_cuda(s);
+}
+
+abd_status abd_energy_grad_hess(abd_scene* S, const double* q_dev, double* E_host, double* g_dev,
+                                abd_pair_counts* counts) {
+  if (!S || !q_dev) return ABD_ERR_INVALID_ARG;
+  Scene& s = S->s;
+  s.err.clear();
+  abd_status r = with_capacity(s, [&]() {
+    launch_transform(s, q_dev, s.x.p);
+    broad_and_enumerate(s, false, false);
+    eval_system(s, q_dev, 1);
+    return ABD_OK;
+  });
+  if (r != ABD_OK) return r;
+  if (abd_status f = flags_to_status(s, s.st_host->flags & ~ST_CCD_MAXITER)) return f;
+  s.have_hess = true;
+  s.last_np = s.st_host->np;
+  if (E_host)
+    for (int k = 0; k < 5; ++k) E_host[k] = s.st_host->energy[k];
+  if (g_dev) cudaMemcpyAsync(g_dev, s.g.p, sizeof(double) * 12 * s.nb, cudaMemcpyDeviceToDevice, s.stream);
+  if (counts) {
+    counts->n_candidates = (long)s.st_host->n_cand;
+    counts->n_active = s.st_host->nact;
+    counts->n_friction = s.st_host->nfr;
+    counts->n_body_pairs = s.st_host->np;
+  }
+  cudaStreamSynchronize(s.stream);
+  return check_cuda(s);
+}
+
+abd_status abd_get_hessian(abd_scene* S, double* diag, int* bi, int* bj, double* blocks, long cap, long* nblocks) {
+  if (!S) return ABD_ERR_INVALID_ARG;
+  Scene& s = S->s;
+  if (!s.have_hess) {
+    s.err = "no Hessian: call abd_energy_grad_hess first";
+    return ABD_ERR_INVALID_ARG;
+  }
+  read_status(s);
+  const long np = s.st_host->np;
+  if (nblocks) *nblocks = np;
+  if (diag) cudaMemcpyAsync(diag, s.D.p, sizeof(double) * 144 * s.nb, cudaMemcpyDeviceToHost, s.stream);
+  const long n = std::min(np, cap);
+  if (n > 0 && (bi || bj)) {
+    std::vector<int2> P(n);
+    cudaMemcpyAsync(P.data(), s.P.p, sizeof(int2) * n, cudaMemcpyDeviceToHost, s.stream);
+    cudaStreamSynchronize(s.stream);
+    for (long k = 0; k < n; ++k) {
+      if (bi) bi[k] = P[k].x;
+      if (bj) bj[k] = P[k].y;
+    }
+  }
+  if (n > 0 && blocks)
+    cudaMemcpy2DAsync(blocks, sizeof(double) * 144, s.pblk.p, sizeof(double) * kBlkStride, sizeof(double) * 144, n,
+                      cudaMemcpyDeviceToHost, s.stream);
+  cudaStreamSynchronize(s.stream);
+  return check_cuda(s);
+}
+
+abd_status abd_get_pairs(abd_scene* S, int which, int* kind, int* i, int* j, int* type, double* d2, long cap,
+                         long* n) {
+  if (!S || which < 0 || which > 2) return ABD_ERR_INVALID_ARG;
+  Scene& s = S->s;
+  read_status(s);
+  if (which == 2) {
+    const long nf = s.st_host->nfr;
+    if (n) *n = nf;
+    if (!kind && !i && !j && !type && !d2) return ABD_OK;
+    std::vector<FricRec> F(nf);
+    if (nf) cudaMemcpy(F.data(), s.fric.p, sizeof(FricRec) * nf, cudaMemcpyDeviceToHost);
+    for (long k = 0; k < std::min(nf, cap); ++k) {
+      if (kind) kind[k] = F[k].kind;
+      if (i) i[k] = F[k].i;
+      if (j) j[k] = F[k].j;
+      if (type) type[k] = F[k].type;
+      if (d2) d2[k] = F[k].mu_lambda;
+    }
+    return check_cuda(s);
+  }
+  if (!s.have_hess) {
+    s.err = "no pair sets: call abd_energy_grad_hess first";
+    return ABD_ERR_INVALID_ARG;
+  }
+  const long np = s.st_host->np;
+  std::vector<int> cnt(np);
+  if (np) cudaMemcpy(cnt.data(), which == 0 ? s.ccount.p : s.acount.p, sizeof(int) * np, cudaMemcpyDeviceToHost);
+  long total = 0;
+  for (long p = 0; p < np; ++p) total += std::min(cnt[p], s.maxc);
+  if (n) *n = total;
+  if (!kind && !i && !j && !type && !d2) return check_cuda(s);
+  long o = 0;
+  std::vector<int2> C;
+  std::vector<int4> A;
+  std::vector<double> D2;
+  for (long p = 0; p < np && o < cap; ++p) {
+    const int c = std::min(cnt[p], s.maxc);
+    if (!c) continue;
+    if (which == 0) {
+      C.resize(c);
+      cudaMemcpy(C.data(), s.cand.p + p * s.maxc, sizeof(int2) * c, cudaMemcpyDeviceToHost);
+    } else {
+      A.resize(c);
+      D2.resize(c);
+      cudaMemcpy(A.data(), s.act.p + p * s.maxc, sizeof(int4) * c, cudaMemcpyDeviceToHost);
+      cudaMemcpy(D2.data(), s.act_d2.p + p * s.maxc, sizeof(double) * c, cudaMemcpyDeviceToHost);
+    }
+    for (int k = 0; k < c && o < cap; ++k, ++o) {
+      int x = which == 0 ? C[k].x : A[k].x, y = which == 0 ? C[k].y : A[k].y;
+      if (kind) kind[o] = (unsigned)x >> 31;
+      if (i) i[o] = x & 0x7fffffff;
+      if (j) j[o] = y;
+      if (type) type[o] = which == 0 ? -1 : A[k].z;
+      if (d2) d2[o] = which == 0 ? 0.0 : D2[k];
+    }
+  }
+  return check_cuda(s);
+}
+
+abd_status abd_solve(abd_scene* S, const double* rhs_dev, double* dq_dev, abd_solve_stats* stats) {
+  if (!S || !rhs_dev || !dq_dev) return ABD_ERR_INVALID_ARG;
+  Scene& s = S->s;
+  if (!s.have_hess) {
+    s.err = "no Hessian: call abd_energy_grad_hess first";
+    return ABD_ERR_INVALID_ARG;
+  }
+  double rel;
+  int its = run_pcg(s, rhs_dev, dq_dev, s.prm.pcg_max, s.prm.pcg_rel_tol, &rel);
+  if (stats) {
+    stats->iterations = its < 0 ? s.prm.pcg_max : its;
+    stats->rel_residual = rel;
+  }
+  if (abd_status c = check_cuda(s)) return c;
+  if (its == -2) {
+    s.err = "PCG breakdown";
+    return ABD_ERR_PCG_BREAKDOWN;
+  }
+  if (its == -1) {
+    s.err = "PCG iteration cap reached";
+    return ABD_ERR_PCG_MAXITER;
+  }
+  return ABD_OK;
+}
+
+abd_status abd_ccd_toi(abd_scene* S, const double* q_dev, const double* dq_dev, double* toi_host) {
+  if (!S || !q_dev || !dq_dev || !toi_host) return ABD_ERR_INVALID_ARG;
+  Scene& s = S->s;
+  s.err.clear();
+  abd_status r = with_capacity(s, [&]() {
+    launch_transform(s, q_dev, s.x.p);
+    launch_transform_dq(s, dq_dev);
+    broad_and_enumerate(s, true, true);
+    return ABD_OK;
+  });
+  if (r != ABD_OK) return r;
+  s.have_hess = false;
+  if (abd_status f = flags_to_status(s, s.st_host->flags)) return f;
+  *toi_host = bits_to_double(s.st_host->toi_bits);
+  return ABD_OK;
+}
+
+abd_status abd_step(abd_scene* S, int nsteps, abd_step_stats* stats) {
+  if (!S || nsteps < 0) return ABD_ERR_INVALID_ARG;
+  Scene& s = S->s;
+  s.err.clear();
+  s.have_hess = false;
+  const size_t qb = sizeof(double) * 12 * s.nb;
+  for (int k = 0; k < nsteps; ++k) {
+    cudaMemcpyAsync(s.qdotsave.p, s.qdot.p, qb, cudaMemcpyDeviceToDevice, s.stream);
+    abd_status r = ABD_ERR_CAPACITY;
+    for (int attempt = 0; attempt < 12 && r == ABD_ERR_CAPACITY; ++attempt) {
+      reset_status(s);
+      try {
+        r = newton_step(s, stats);
+      } catch (OomError&) {
+        r = ABD_ERR_OOM;
+      }
+      if (r == ABD_ERR_CAPACITY) {
+        read_status(s);
+        handle_capacity(s);
+        // grown buffers lose their contents: rebuild the friction set at q^t
+        abd_status lr = with_capacity(s, [&]() {
+          lag_friction(s);
+          return ABD_OK;
+        });
+        if (lr != ABD_OK) r = lr;
+      }
+    }
+    if (r == ABD_OK)  // the new q^t: lag friction for the next step
+      r = with_capacity(s, [&]() {
+        lag_friction(s);
+        return ABD_OK;
+      });
+    if (r != ABD_OK) {
+      // transactional: q^t was never modified before the step completed; the
+      // velocity and the lagged friction set are restored from the copy
+      cudaMemcpyAsync(s.qdot.p, s.qdotsave.p, qb, cudaMemcpyDeviceToDevice, s.stream);
+      launch_predictor(s);
+      with_capacity(s, [&]() {
+        lag_friction(s);
+        return ABD_OK;
+      });
+      cudaStreamSynchronize(s.stream);
+      return r;
+    }
+  }
+  cudaStreamSynchronize(s.stream);
+  return check_cuda(s);
+}
+
+const char* abd_last_error(const abd_scene* S) { return S ? S->s.err.c_str() : "null scene"; }
+
+}  // extern "C"

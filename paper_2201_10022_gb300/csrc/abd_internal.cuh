@@ -1,0 +1,167 @@
+// Internal declarations of the affine-body library: the device-resident
+// scene, the device status word and the kernel launchers shared by the
+// translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/abd.h"
+
+namespace abd {
+
+// ---- device status word ----------------------------------------------------
+enum : unsigned {
+  ST_CAP_ROWS = 1u << 0,       // body-pair row capacity exceeded
+  ST_CAP_CANDS = 1u << 1,      // candidate slots per body pair exceeded
+  ST_CAP_PAIRS = 1u << 2,      // body-pair list capacity exceeded
+  ST_CAP_ACTIVE = 1u << 3,     // flat active-term storage exceeded
+  ST_CCD_MAXITER = 1u << 4,
+  ST_INTERSECT = 1u << 5,      // a pair at zero distance
+  ST_NONFINITE = 1u << 6,
+  ST_PCG_BREAKDOWN = 1u << 7,
+};
+
+struct DevStatus {
+  unsigned flags;
+  int need_row;                 // largest body-pair row seen
+  int need_cand;                // largest candidate count of one body pair
+  int np;                       // body pairs in the current list
+  int nact;                     // active barrier terms
+  int nfr;                      // lagged friction terms
+  int nfp;                      // friction body pairs
+  int pad;
+  unsigned long long need_pairs;  // body pairs needed
+  unsigned long long need_act;    // active terms needed
+  unsigned long long need_misc;   // other scans
+  unsigned long long toi_bits;  // min time of impact (bits of a positive double)
+  unsigned long long step_bits; // max vertex step length (bits of a positive double)
+  unsigned long long n_cand;    // candidates of the last enumeration
+  double scal[8];               // PCG scalars: 0 rz, 1 pAp, 2 rr, 3 rr0, 4 alpha, 5 beta, 6 done
+  double energy[8];             // 0 total, 1 inertia, 2 ortho, 3 barrier, 4 friction
+};
+
+// ---- allocation -------------------------------------------------------------
+struct Alloc {
+  abd_allocator a{};
+  bool custom = false;
+  cudaStream_t stream = nullptr;
+  void* get(size_t bytes);
+  void put(void* p);
+};
+
+template <typename T>
+struct Buf {
+  T* p = nullptr;
+  size_t cap = 0;  // elements
+};
+
+// lagged friction record (one per friction term)
+struct FricRec {
+  int v[4];
+  int a, b;        // body pair (a < b)
+  double gam[4], n[3], r[3], mu_lambda;
+  int kind, i, j, type;
+};
+
+// ---- scene ------------------------------------------------------------------
+struct Scene {
+  abd_params prm{};
+  int nb = 0, nv = 0, nt = 0, ne = 0, ndyn = 0;
+  double newton_tol = 0;
+  Alloc alloc;
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  // topology and body constants
+  Buf<double4> xbar;   // nv (w unused)
+  Buf<int> vbody, tri, edge, vbeg, tbeg, ebeg;
+  Buf<uint8_t> is_static;
+  Buf<double> mass10;  // nb*10: rho*vol, rho*m1[3], rho*S[xx,xy,xz,yy,yz,zz]
+  Buf<double> vol, kappa_b, density;
+
+  // state
+  Buf<double> q, qdot, qt, qtilde, dq, qtrial, qsave, qdotsave;
+  Buf<double4> x, dx, x1, xt;
+  Buf<double> bbox;    // nb*6
+
+  // body pairs
+  int maxn = 0;        // neighbours per row
+  Buf<int> nbr, ncount, rowoff;  // rows
+  Buf<int2> P;                   // body pairs (a, b), a < b, row-major
+  Buf<int> in_off, in_cnt, in_list;   // incoming lists (pairs whose b is the body)
+
+  // candidates / actives per body pair
+  int maxc = 0;
+  Buf<int2> cand;      // np*maxc: (i | kind << 31, j)
+  Buf<int> ccount;
+  Buf<int4> act;       // np*maxc: (i | kind << 31, j, type, unused)
+  Buf<int> acount, aoff;
+  Buf<double> act_d2;  // np*maxc
+
+  // per-term energy and derivatives: E, g12, H78 (kTermStride doubles) and
+  // the term's four vertices
+  Buf<double> term;    // barrier terms
+  Buf<int4> termv;
+  Buf<double> fterm;   // friction terms
+  Buf<int4> ftermv;
+  Buf<double> Epair;   // energy-only pass: barrier energy per body pair
+
+  // friction
+  Buf<FricRec> fric;
+  Buf<int2> fpairs;    // friction body pairs, sorted
+  Buf<int> fpoff;      // nfp+1 ranges into fric
+  Buf<int> flagbuf, posbuf;  // scan scratch (body-pair sized)
+
+  // assembly
+  Buf<double> pblk;    // np * (3*144 + 24 + 2): Hab, Dlo, Dhi, glo, ghi, Eb, Ef
+  Buf<double> Db, gb, Eb;   // body terms
+  Buf<double> D, g, Pinv;   // assembled diagonal, gradient, preconditioner
+  Buf<double> red;     // reduction scratch
+
+  // PCG
+  Buf<double> r, z, pv, Ap, part;
+
+  DevStatus* st = nullptr;       // device
+  DevStatus* st_host = nullptr;  // pinned mirror
+  long last_np = 0;
+  bool have_hess = false;
+};
+
+constexpr int kTermStride = 91;
+constexpr int kBlkStride = 3 * 144 + 24 + 2;
+
+// ---- launchers (k_system.cu) -----------------------------------------------
+void launch_mass_moments(Scene& s);
+void launch_predictor(Scene& s);
+void launch_transform(Scene& s, const double* q, double4* x);
+void launch_transform_dq(Scene& s, const double* dq);   // dx = J dq, x1 = x + dx
+void launch_body_boxes(Scene& s, bool swept);
+void launch_body_pairs(Scene& s);                       // rows -> P (uses friction pairs)
+void launch_incoming(Scene& s);
+void launch_assemble(Scene& s);
+void launch_body_terms(Scene& s, const double* q, bool hess);
+void launch_gather(Scene& s);
+void launch_precond(Scene& s);
+void launch_energy_total(Scene& s, bool with_pairs);
+int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res);
+void launch_max_step(Scene& s);
+void launch_trial(Scene& s, double alpha);
+void launch_finish_step(Scene& s);
+// exclusive scan of cnt[0..*n_dev) into off[0..*n_dev] (off[n] = total), total
+// also to *total_dev; if the total exceeds cap, flag_bit is raised.
+void launch_scan(Scene& s, const int* cnt, int* off, const int* n_dev, int* total_dev, long cap, unsigned flag_bit,
+                 unsigned long long* need);
+void launch_fpairs(Scene& s);
+void launch_negate(Scene& s, const double* in, double* out, long n);
+
+// ---- launchers (k_contact.cu) ------------------------------------------------
+void launch_enumerate(Scene& s, bool swept, bool ccd);
+void launch_active(Scene& s, const double4* x);
+void launch_barrier(Scene& s, int project, long cap);
+void launch_friction_lag(Scene& s);
+void launch_friction_eval(Scene& s, const double4* x, bool derivs);
+void launch_pair_energy(Scene& s, const double4* x);   // energy only, over candidates
+
+}  // namespace abd

@@ -1,0 +1,472 @@
+// Contact kernels: primitive candidate enumeration per body pair with the
+// d-hat box test (Sec. 4.2, i-AABB culling restated per body pair), additive
+// CCD over linear trajectories (Sec. 4.1), active-set detection, barrier and
+// friction terms (Sec. 4) and their energies.
+#include <float.h>
+
+#include "abd_internal.cuh"
+#include "derivs.cuh"
+
+namespace abd {
+
+namespace {
+
+constexpr int kWarpsPerBlock = 4;
+constexpr int kChunk = 64;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct Box {
+  double lo[3], hi[3];
+};
+
+__device__ __forceinline__ void box_point(Box& b, const double4& p) {
+  b.lo[0] = b.hi[0] = p.x;
+  b.lo[1] = b.hi[1] = p.y;
+  b.lo[2] = b.hi[2] = p.z;
+}
+__device__ __forceinline__ void box_add(Box& b, const double4& p) {
+  b.lo[0] = fmin(b.lo[0], p.x);
+  b.hi[0] = fmax(b.hi[0], p.x);
+  b.lo[1] = fmin(b.lo[1], p.y);
+  b.hi[1] = fmax(b.hi[1], p.y);
+  b.lo[2] = fmin(b.lo[2], p.z);
+  b.hi[2] = fmax(b.hi[2], p.z);
+}
+// canonical proximity test: on every axis lo_P - hi_Q <= dhat and lo_Q - hi_P <= dhat
+__device__ __forceinline__ bool box_near(const double* plo, const double* phi, const double* qlo, const double* qhi,
+                                         double dhat) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (!(__dsub_rn(plo[k], qhi[k]) <= dhat)) return false;
+    if (!(__dsub_rn(qlo[k], phi[k]) <= dhat)) return false;
+  }
+  return true;
+}
+
+// box of primitive `id` of type t (0 vertex, 1 edge, 2 triangle)
+__device__ __forceinline__ void prim_box(int t, int id, const int* tri, const int* edge, const double4* x,
+                                         const double4* x1, Box& b) {
+  int nvtx = t == 0 ? 1 : (t == 1 ? 2 : 3);
+  int v0 = t == 0 ? id : (t == 1 ? edge[2 * id] : tri[3 * id]);
+  box_point(b, x[v0]);
+  if (x1) box_add(b, x1[v0]);
+  for (int k = 1; k < nvtx; ++k) {
+    int v = t == 1 ? edge[2 * id + k] : tri[3 * id + k];
+    box_add(b, x[v]);
+    if (x1) box_add(b, x1[v]);
+  }
+}
+
+__device__ __forceinline__ void pair_vertices(int kind, int i, int j, const int* tri, const int* edge, int v[4]) {
+  if (kind == 0) {
+    v[0] = i;
+    v[1] = tri[3 * j];
+    v[2] = tri[3 * j + 1];
+    v[3] = tri[3 * j + 2];
+  } else {
+    v[0] = edge[2 * i];
+    v[1] = edge[2 * i + 1];
+    v[2] = edge[2 * j];
+    v[3] = edge[2 * j + 1];
+  }
+}
+
+__device__ __forceinline__ void set_flag(DevStatus* st, unsigned f) { atomicOr(&st->flags, f); }
+
+struct WarpLists {
+  int pid[kChunk], qid[kChunk];
+  double pb[kChunk][6], qb[kChunk][6];
+};
+
+// Fill a chunk of primitives of type t from [cur, hi) that pass the box test
+// against the other body's box; returns the new cursor.
+__device__ int fill_chunk(int t, int cur, int hi, const double* olo, const double* ohi, double dhat, const int* tri,
+                          const int* edge, const double4* x, const double4* x1, int* ids, double (*boxes)[6],
+                          int& n) {
+  const int lane = threadIdx.x & 31;
+  n = 0;
+  while (cur < hi && n <= kChunk - 32) {
+    int id = cur + lane;
+    bool ok = false;
+    Box b;
+    if (id < hi) {
+      prim_box(t, id, tri, edge, x, x1, b);
+      ok = box_near(b.lo, b.hi, olo, ohi, dhat);
+    }
+    unsigned m = __ballot_sync(kFull, ok);
+    if (ok) {
+      int pos = n + __popc(m & ((1u << lane) - 1u));
+      ids[pos] = id;
+      for (int k = 0; k < 3; ++k) {
+        boxes[pos][k] = b.lo[k];
+        boxes[pos][3 + k] = b.hi[k];
+      }
+    }
+    n += __popc(m);
+    cur += 32;
+  }
+  __syncwarp();
+  return cur;
+}
+
+// Enumerate the candidates of one kind between primitive ranges of two
+// bodies.  P side: vertices (PT) or edges (EE) of body `pa`; Q side:
+// triangles (PT) or edges (EE) of body `qa`.
+__device__ void enum_kind(int kind, int p_lo, int p_hi, int q_lo, int q_hi, const Box& boxP, const Box& boxQ,
+                          double dhat, const int* tri, const int* edge, const double4* x, const double4* x1,
+                          const double4* dx, WarpLists& L, int2* out, int maxc, int& base, bool ccd, double ccd_s,
+                          int ccd_max, double& tmin, DevStatus* st) {
+  const int lane = threadIdx.x & 31;
+  const int tp = kind == 0 ? 0 : 1, tq = kind == 0 ? 2 : 1;
+  int qc = q_lo;
+  while (qc < q_hi) {
+    int nq;
+    qc = fill_chunk(tq, qc, q_hi, boxP.lo, boxP.hi, dhat, tri, edge, x, x1, L.qid, L.qb, nq);
+    if (nq == 0) continue;
+    int pc = p_lo;
+    while (pc < p_hi) {
+      int npp;
+      pc = fill_chunk(tp, pc, p_hi, boxQ.lo, boxQ.hi, dhat, tri, edge, x, x1, L.pid, L.pb, npp);
+      const int tot = npp * nq;
+      for (int t0 = 0; t0 < tot; t0 += 32) {
+        int t = t0 + lane;
+        bool c = false;
+        int pi = 0, qi = 0;
+        if (t < tot) {
+          pi = t / nq;
+          qi = t - pi * nq;
+          c = box_near(L.pb[pi], L.pb[pi] + 3, L.qb[qi], L.qb[qi] + 3, dhat);
+        }
+        unsigned m = __ballot_sync(kFull, c);
+        if (c) {
+          int pos = base + __popc(m & ((1u << lane) - 1u));
+          int i = L.pid[pi], j = L.qid[qi];
+          if (pos < maxc) out[pos] = make_int2(i | (kind << 31), j);
+          if (ccd) {
+            int v[4];
+            pair_vertices(kind, i, j, tri, edge, v);
+            v3 xs[4], ds[4];
+            for (int k = 0; k < 4; ++k) {
+              xs[k] = mk(x[v[k]]);
+              ds[k] = mk(dx[v[k]]);
+            }
+            double toi;
+            if (accd(kind, xs, ds, ccd_s, 1.0, ccd_max, toi)) set_flag(st, ST_CCD_MAXITER);
+            tmin = fmin(tmin, toi);
+          }
+        }
+        base += __popc(m);
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void k_enumerate(const int2* __restrict__ P, const DevStatus* __restrict__ cst, const int* vbeg,
+                            const int* tbeg, const int* ebeg, const int* tri, const int* edge, const double4* x,
+                            const double4* x1, const double4* dx, const double* bbox, double dhat, int maxc,
+                            int2* cand, int* ccount, bool ccd, double ccd_s, int ccd_max, DevStatus* st) {
+  __shared__ WarpLists lists[kWarpsPerBlock];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * kWarpsPerBlock;
+  const int np = cst->np;
+  WarpLists& L = lists[warp];
+  double tmin = 1.0;
+  unsigned long long ncand = 0;
+  for (int p = blockIdx.x * kWarpsPerBlock + warp; p < np; p += nwarps) {
+    const int a = P[p].x, b = P[p].y;
+    Box Ba, Bb;
+    for (int k = 0; k < 3; ++k) {
+      Ba.lo[k] = bbox[6 * a + k];
+      Ba.hi[k] = bbox[6 * a + 3 + k];
+      Bb.lo[k] = bbox[6 * b + k];
+      Bb.hi[k] = bbox[6 * b + 3 + k];
+    }
+    int base = 0;
+    int2* out = cand + (size_t)p * maxc;
+    // vertices of a against triangles of b, vertices of b against triangles of a
+    enum_kind(0, vbeg[a], vbeg[a + 1], tbeg[b], tbeg[b + 1], Ba, Bb, dhat, tri, edge, x, x1, dx, L, out, maxc, base,
+              ccd, ccd_s, ccd_max, tmin, st);
+    enum_kind(0, vbeg[b], vbeg[b + 1], tbeg[a], tbeg[a + 1], Bb, Ba, dhat, tri, edge, x, x1, dx, L, out, maxc, base,
+              ccd, ccd_s, ccd_max, tmin, st);
+    // edges of a against edges of b
+    enum_kind(1, ebeg[a], ebeg[a + 1], ebeg[b], ebeg[b + 1], Ba, Bb, dhat, tri, edge, x, x1, dx, L, out, maxc, base,
+              ccd, ccd_s, ccd_max, tmin, st);
+    if (lane == 0) {
+      ccount[p] = base;
+      if (base > maxc) {
+        set_flag(st, ST_CAP_CANDS);
+        atomicMax(&st->need_cand, base);
+      }
+    }
+    ncand += base;
+  }
+  if (ccd) {
+    for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_xor_sync(kFull, tmin, o));
+    if (lane == 0 && tmin < 1.0) atomicMin(&st->toi_bits, (unsigned long long)__double_as_longlong(tmin));
+  }
+  if (lane == 0 && ncand) atomicAdd(&st->n_cand, ncand);
+}
+
+// active pairs: canonical d^2 < dhat^2, compacted per body pair in slot order
+__global__ void k_active(const int2* __restrict__ P, const DevStatus* __restrict__ cst, const int2* cand,
+                         const int* ccount, const int* tri, const int* edge, const double4* x, double dhat, int maxc,
+                         int4* act, double* act_d2, int* acount, DevStatus* st) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int np = cst->np;
+  const double dh2 = __dmul_rn(dhat, dhat);
+  for (int p = blockIdx.x * (blockDim.x >> 5) + warp; p < np; p += nwarps) {
+    const int n = min(ccount[p], maxc);
+    int base = 0;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+      int k = k0 + lane;
+      bool a = false;
+      int type = 0;
+      double d2 = 0.0;
+      int2 c = make_int2(0, 0);
+      if (k < n) {
+        c = cand[(size_t)p * maxc + k];
+        int kind = (unsigned)c.x >> 31, i = c.x & 0x7fffffff;
+        int v[4];
+        pair_vertices(kind, i, c.y, tri, edge, v);
+        v3 xs[4];
+        for (int m = 0; m < 4; ++m) xs[m] = mk(x[v[m]]);
+        d2 = pair_dist2(kind, xs, type);
+        a = d2 < dh2;
+        if (a && d2 == 0.0) set_flag(st, ST_INTERSECT);
+        if (!(d2 == d2)) set_flag(st, ST_NONFINITE);
+      }
+      unsigned m = __ballot_sync(kFull, a);
+      if (a) {
+        int pos = base + __popc(m & ((1u << lane) - 1u));
+        act[(size_t)p * maxc + pos] = make_int4(c.x, c.y, type, 0);
+        act_d2[(size_t)p * maxc + pos] = d2;
+      }
+      base += __popc(m);
+    }
+    if (lane == 0) acount[p] = base;
+  }
+}
+
+__device__ __forceinline__ int owner(const int* off, int n, int f) {
+  // largest p with off[p] <= f (off has n+1 entries, nondecreasing)
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (off[mid] <= f) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// barrier terms: energy, vertex gradient and projected vertex Hessian
+__global__ void k_barrier(const DevStatus* __restrict__ cst, const int* aoff, const int4* act, const int* tri,
+                          const int* edge, const double4* x, double dhat, double kappa, int maxc, int project,
+                          long cap, double* term, int4* termv) {
+  const int np = cst->np, nact = (int)min((long)cst->nact, cap);
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nact; f += gridDim.x * blockDim.x) {
+    int p = owner(aoff, np, f);
+    int k = f - aoff[p];
+    int4 r = act[(size_t)p * maxc + k];
+    int kind = (unsigned)r.x >> 31, i = r.x & 0x7fffffff;
+    int v[4];
+    pair_vertices(kind, i, r.y, tri, edge, v);
+    v3 xs[4];
+    for (int m = 0; m < 4; ++m) xs[m] = mk(x[v[m]]);
+    double* T = term + (size_t)f * kTermStride;
+    T[0] = barrier_term(kind, r.z, xs, dhat, kappa, project, T + 1, T + 13);
+    termv[f] = make_int4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+// closest-point weights of a pair of the given distance type: point on the
+// first primitive minus point on the second = sum gamma_k x_k
+__device__ void closest_weights(int kind, int type, const v3* x, double* g) {
+  auto seg = [](v3 p, v3 a, v3 b) { return dot(p - a, b - a) / dot(b - a, b - a); };
+  g[0] = g[1] = g[2] = g[3] = 0.0;
+  if (kind == 0) {
+    double b1 = 0, b2 = 0, b3 = 0, t;
+    switch (type) {
+      case 0: b1 = 1; break;
+      case 1: b2 = 1; break;
+      case 2: b3 = 1; break;
+      case 3: t = seg(x[0], x[1], x[2]); b1 = 1 - t; b2 = t; break;
+      case 4: t = seg(x[0], x[2], x[3]); b2 = 1 - t; b3 = t; break;
+      case 5: t = seg(x[0], x[3], x[1]); b3 = 1 - t; b1 = t; break;
+      default: {
+        v3 e1 = x[2] - x[1], e2 = x[3] - x[1], w = x[0] - x[1];
+        double a11 = dot(e1, e1), a12 = dot(e1, e2), a22 = dot(e2, e2), r1 = dot(e1, w), r2 = dot(e2, w);
+        double det = a11 * a22 - a12 * a12;
+        b2 = (r1 * a22 - r2 * a12) / det;
+        b3 = (a11 * r2 - a12 * r1) / det;
+        b1 = 1 - b2 - b3;
+      } break;
+    }
+    g[0] = 1.0;
+    g[1] = -b1;
+    g[2] = -b2;
+    g[3] = -b3;
+  } else {
+    double s = 0, t = 0;
+    switch (type) {
+      case 0: break;
+      case 1: t = 1; break;
+      case 2: s = 1; break;
+      case 3: s = 1; t = 1; break;
+      case 4: t = seg(x[0], x[2], x[3]); break;
+      case 5: s = 1; t = seg(x[1], x[2], x[3]); break;
+      case 6: s = seg(x[2], x[0], x[1]); break;
+      case 7: t = 1; s = seg(x[3], x[0], x[1]); break;
+      default: {
+        v3 e0 = x[1] - x[0], e1 = x[3] - x[2], w0 = x[0] - x[2];
+        double A = dot(e0, e0), B = dot(e0, e1), C = dot(e1, e1), D = dot(e0, w0), E = dot(e1, w0);
+        double den = A * C - B * B;
+        s = (B * E - C * D) / den;
+        t = (A * E - B * D) / den;
+      } break;
+    }
+    g[0] = 1 - s;
+    g[1] = s;
+    g[2] = -(1 - t);
+    g[3] = -t;
+  }
+}
+
+// lag friction at the current positions: one record per active pair
+// (lambda = -kappa B'(d), closest-point weights, normal, lagged offset)
+__global__ void k_friction_lag(DevStatus* cst, const int2* P, const int* aoff, const int4* act,
+                               const double* act_d2, const int* tri, const int* edge, const int* vbody,
+                               const double4* x, double dhat, double kappa, double mu, int maxc, FricRec* fr) {
+  const int np = cst->np, nact = cst->nact;
+  if (blockIdx.x == 0 && threadIdx.x == 0) cst->nfr = nact;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nact; f += gridDim.x * blockDim.x) {
+    int p = owner(aoff, np, f);
+    int k = f - aoff[p];
+    int4 r = act[(size_t)p * maxc + k];
+    int kind = (unsigned)r.x >> 31, i = r.x & 0x7fffffff;
+    FricRec R;
+    pair_vertices(kind, i, r.y, tri, edge, R.v);
+    v3 xs[4];
+    for (int m = 0; m < 4; ++m) xs[m] = mk(x[R.v[m]]);
+    double d = sqrt(act_d2[(size_t)p * maxc + k]);
+    double B, B1, B2;
+    barrier_derivs(d, dhat, B, B1, B2);
+    R.mu_lambda = mu * (-kappa * B1);
+    closest_weights(kind, r.z, xs, R.gam);
+    v3 w = (R.gam[0] * xs[0] + R.gam[1] * xs[1]) + (R.gam[2] * xs[2] + R.gam[3] * xs[3]);
+    double nn = sqrt(dot(w, w));
+    R.n[0] = w.x / nn;
+    R.n[1] = w.y / nn;
+    R.n[2] = w.z / nn;
+    R.r[0] = w.x;
+    R.r[1] = w.y;
+    R.r[2] = w.z;
+    R.a = P[p].x;
+    R.b = P[p].y;
+    R.kind = kind;
+    R.i = i;
+    R.j = r.y;
+    R.type = r.z;
+    fr[f] = R;
+  }
+}
+
+__global__ void k_friction_eval(const DevStatus* __restrict__ cst, const FricRec* fr, const double4* x, double eps,
+                                double* fterm, int4* ftermv, bool derivs) {
+  const int nfr = cst->nfr;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nfr; f += gridDim.x * blockDim.x) {
+    const FricRec& R = fr[f];
+    v3 xs[4];
+    for (int m = 0; m < 4; ++m) xs[m] = mk(x[R.v[m]]);
+    double* T = fterm + (size_t)f * kTermStride;
+    double g12[12], H78[78];
+    double e = friction_term(xs, R.gam, v3{R.n[0], R.n[1], R.n[2]}, v3{R.r[0], R.r[1], R.r[2]}, R.mu_lambda, eps,
+                             g12, H78);
+    T[0] = e;
+    if (derivs) {
+      for (int m = 0; m < 12; ++m) T[1 + m] = g12[m];
+      for (int m = 0; m < 78; ++m) T[13 + m] = H78[m];
+      ftermv[f] = make_int4(R.v[0], R.v[1], R.v[2], R.v[3]);
+    }
+  }
+}
+
+// energy of the barrier over the stored candidates at positions x: one value
+// per body pair, summed in slot order (energy-only pass of the line search)
+__global__ void k_pair_energy(const DevStatus* __restrict__ cst, const int2* cand, const int* ccount,
+                              const int* tri, const int* edge, const double4* x, double dhat, double kappa, int maxc,
+                              double* Ep, DevStatus* st) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int np = cst->np;
+  const double dh2 = __dmul_rn(dhat, dhat);
+  for (int p = blockIdx.x * (blockDim.x >> 5) + warp; p < np; p += nwarps) {
+    const int n = min(ccount[p], maxc);
+    double e = 0.0;
+    for (int k = lane; k < n; k += 32) {
+      int2 c = cand[(size_t)p * maxc + k];
+      int kind = (unsigned)c.x >> 31, i = c.x & 0x7fffffff;
+      int v[4];
+      pair_vertices(kind, i, c.y, tri, edge, v);
+      v3 xs[4];
+      for (int m = 0; m < 4; ++m) xs[m] = mk(x[v[m]]);
+      int type;
+      double d2 = pair_dist2(kind, xs, type);
+      if (d2 < dh2) {
+        if (d2 == 0.0) set_flag(st, ST_INTERSECT);
+        double B, B1, B2;
+        barrier_derivs(sqrt(d2), dhat, B, B1, B2);
+        e += kappa * B;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(kFull, e, o);
+    if (lane == 0) Ep[p] = e;
+  }
+}
+
+int grid_for(long n, int per_block, int max_blocks) {
+  long g = (n + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > max_blocks) g = max_blocks;
+  return (int)g;
+}
+
+}  // namespace
+
+void launch_enumerate(Scene& s, bool swept, bool ccd) {
+  const int threads = 32 * kWarpsPerBlock;
+  int grid = grid_for(s.last_np > 0 ? s.last_np : s.nb, kWarpsPerBlock, 152 * 16);
+  k_enumerate<<<grid, threads, 0, s.stream>>>(s.P.p, s.st, s.vbeg.p, s.tbeg.p, s.ebeg.p, s.tri.p, s.edge.p, s.x.p,
+                                              swept ? s.x1.p : nullptr, s.dx.p, s.bbox.p, s.prm.dhat, s.maxc,
+                                              s.cand.p, s.ccount.p, ccd, s.prm.ccd_s, s.prm.ccd_max, s.st);
+}
+
+void launch_active(Scene& s, const double4* x) {
+  int grid = grid_for(s.last_np > 0 ? s.last_np : s.nb, 8, 152 * 16);
+  k_active<<<grid, 256, 0, s.stream>>>(s.P.p, s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.prm.dhat, s.maxc,
+                                       s.act.p, s.act_d2.p, s.acount.p, s.st);
+}
+
+void launch_barrier(Scene& s, int project, long cap) {
+  k_barrier<<<152 * 8, 128, 0, s.stream>>>(s.st, s.aoff.p, s.act.p, s.tri.p, s.edge.p, s.x.p, s.prm.dhat,
+                                          s.prm.kappa, s.maxc, project, cap, s.term.p, s.termv.p);
+}
+
+void launch_friction_lag(Scene& s) {
+  k_friction_lag<<<152 * 4, 128, 0, s.stream>>>(s.st, s.P.p, s.aoff.p, s.act.p, s.act_d2.p, s.tri.p, s.edge.p,
+                                               s.vbody.p, s.x.p, s.prm.dhat, s.prm.kappa, s.prm.mu, s.maxc, s.fric.p);
+}
+
+void launch_friction_eval(Scene& s, const double4* x, bool derivs) {
+  k_friction_eval<<<152 * 4, 128, 0, s.stream>>>(s.st, s.fric.p, x, s.prm.eps_v * s.prm.dt, s.fterm.p,
+                                                s.ftermv.p, derivs);
+}
+
+void launch_pair_energy(Scene& s, const double4* x) {
+  int grid = grid_for(s.last_np > 0 ? s.last_np : s.nb, 8, 152 * 16);
+  k_pair_energy<<<grid, 256, 0, s.stream>>>(s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.prm.dhat,
+                                            s.prm.kappa, s.maxc, s.Epair.p, s.st);
+}
+
+}  // namespace abd

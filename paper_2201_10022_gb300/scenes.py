@@ -344,6 +344,30 @@ def throw_stack(seed: int = 4, n_throw: int = 64, n_stack: int = 10, edge: float
     return B.build(params)
 
 
+def packed_cubes(seed: int = 6, nx: int = 22, ny: int = 22, nz: int = 21, edge: float = 0.2,
+                 gap: float = 0.9999e-3, max_deg: float = 1e-4, **params) -> Scene:
+    """Contact-dense block of cubes: neighbouring faces `gap` apart (just
+    below d-hat = 1e-3, where the barrier force is of the order of the
+    weight, so the block starts close to rest), tiny seeded rotations, on a
+    static ground box.  Every face-to-face neighbour pair carries active
+    point-triangle and edge-edge terms from the first iteration."""
+    rng = np.random.default_rng(seed)
+    B = _Builder("packed_cubes", seed)
+    pitch = edge + gap
+    ground = max(nx, ny) * pitch + 2.0
+    gv, gt = box_mesh(ground, ground, 1.0)
+    B.add(gv, gt, p=(0.0, 0.0, -0.5), static=True)
+    cv, ct = cube_mesh(edge)
+    for iz in range(nz):
+        for iy in range(ny):
+            for ix in range(nx):
+                p = ((ix - 0.5 * (nx - 1)) * pitch, (iy - 0.5 * (ny - 1)) * pitch, gap + 0.5 * edge + iz * pitch)
+                B.add(cv, ct, R=small_rotation(rng, max_deg), p=p)
+    prm = dict(mu=0.3, eps_v=1e-3)
+    prm.update(params)
+    return B.build(prm)
+
+
 def random_pair(seed: int, kinds=("cube", "ico1"), sep: float = 0.0005, **params) -> Scene:
     """Two bodies, the second placed so that its closest approach to the first
     is a few d-hat; random orientations."""
@@ -370,6 +394,7 @@ def random_pair(seed: int, kinds=("cube", "ico1"), sep: float = 0.0005, **params
 
 
 CONFIGS = {
+    0: lambda **kw: packed_cubes(**kw),
     1: lambda **kw: cube_stack(**kw),
     2: lambda **kw: ico_bowl(**kw),
     3: lambda **kw: lattice_pile(**kw),
