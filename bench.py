@@ -1,0 +1,290 @@
+#!/usr/bin/env python
+"""Benchmark of the affine-body time step on GB300.
+
+Metric: milliseconds per time step of the 10,001-body lattice pile (25x20x20
+jittered lattice of cubes, subdivision-1 icospheres and 1x0.2x0.2 m boxes
+collapsing onto a static ground, friction mu = 0.3, FP64), with contact-pair
+evaluations per second beside it.  The pile's first steps are free fall; the
+timed window starts `--start-step` steps into the run (advanced untimed on
+the GPU), after `--warmup` further untimed steps, and covers `--steps` steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl abd|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank steps its own
+replica of the scene; rank 0 prints the line with the maximum time over
+ranks.  The reference arm times the CPU oracle on a bounded sample of the
+same workload (see `cpu_baseline`).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2201_10022_gb300 import scenes  # noqa: E402
+
+WORKLOAD = dict(name="lattice_pile", nx=25, ny=20, nz=20, seed=3)
+METRIC = "ms/timestep, 10k-body lattice pile (FP64, friction)"
+
+
+def workload_scene(nx=None, ny=None, nz=None):
+    return scenes.lattice_pile(seed=WORKLOAD["seed"], nx=nx or WORKLOAD["nx"], ny=ny or WORKLOAD["ny"],
+                               nz=nz or WORKLOAD["nz"])
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.rows, self.proc, self.uuid = [], None, uuid
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def oracle_sample(start_step, warmup, steps, dims=(6, 6, 3)):
+    """Time the CPU oracle on a sub-lattice of the workload's recipe over the
+    same step window; ms/step is scaled to the full body count."""
+    import oracle as O
+    s = workload_scene(*dims)
+    full = workload_scene()
+    # the library's Newton rule: |dx|_inf <= 1e-5 * bbox diagonal * dt
+    o = O.Oracle(s, newton_rel=1e-5 * s.params["dt"], newton_max=500, cg_tol=1e-4)
+    r, _ = o.step(start_step + warmup)
+    if r:
+        raise RuntimeError(f"oracle failed while advancing: {O.ERRORS[r]}")
+    steps = min(steps, 5)
+    t0 = time.perf_counter()
+    r, st = o.step(steps)
+    dt = time.perf_counter() - t0
+    if r:
+        raise RuntimeError(f"oracle failed: {O.ERRORS[r]}")
+    scale = full.nb / s.nb
+    return {"value": 1e3 * dt / steps * scale, "unit": "ms/step", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle (1 thread) on a {dims[0]}x{dims[1]}x{dims[2]} sub-lattice ({s.nb} bodies) of the "
+                       f"same recipe, steps {start_step + warmup}..{start_step + warmup + steps - 1}, "
+                       f"{1e3 * dt / steps:.1f} ms/step scaled by bodies x{scale:.1f}"),
+            "seconds": dt}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_abd(args, rank, world):
+    import torch
+    from paper_2201_10022_gb300.abd import AbdScene, abd_get_state, abd_set_state, abd_step, abd_step_stats
+    import ctypes as C
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    s = workload_scene()
+    g = AbdScene(s, device=dev)
+    if args.start_step:
+        g.step(args.start_step)
+    g.step(args.warmup)
+    torch.cuda.synchronize()
+    q0, qd0 = g.get_state()
+    q0, qd0 = q0.clone(), qd0.clone()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    # ---- device-timed region: inputs resident in HBM ----------------------
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clk = ClockSampler(uuid)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    g.set_profiling(True)
+    ms, stats = [], []
+    for k in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = g.step(1)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        stats.append(st)
+    prof = g.profile()
+    g.set_profiling(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    qh = torch.empty((s.nb, 12), dtype=torch.float64).pin_memory()
+    qdh = torch.empty_like(qh).pin_memory()
+    qh.copy_(q0.cpu())
+    qdh.copy_(qd0.cpu())
+    torch.cuda.synchronize()
+    sst = abd_step_stats()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        r = abd_set_state(g.h, qh.data_ptr(), qdh.data_ptr(), 0)
+        r = r or abd_step(g.h, 1, C.byref(sst))
+        r = r or abd_get_state(g.h, qh.data_ptr(), qdh.data_ptr(), 0)
+        if r:
+            raise RuntimeError(f"e2e step failed: {r}")
+    e2e_ms = 1e3 * (time.perf_counter() - t0)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    steps_total = args.steps * world
+    ms_per_step = total_ms / steps_total
+    newton = sum(st["newton_iters"] for st in stats)
+    cand = sum(st["candidates_tested"] for st in stats)
+    act = sum(st["active_evaluated"] for st in stats)
+    launches = sum(st["kernel_launches"] for st in stats)
+    pk, src = peaks()
+    # roofline of the kernel class that took the most device time
+    top = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
+    name, p = top
+    roof = None
+    if p["launches"] and p["total_ms"] > 0:
+        if p["bytes"] > 0:
+            achieved = p["bytes"] / (p["total_ms"] * 1e-3) / 1e9
+            roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": src,
+                    "launches": p["launches"], "avg_launch_ms": p["total_ms"] / p["launches"]}
+        else:
+            roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": 1.259, "unit": "TFLOP/s",
+                    "frac": None, "traffic": None, "launches": p["launches"],
+                    "avg_launch_ms": p["total_ms"] / p["launches"]}
+    out = {
+        "metric": METRIC, "value": ms_per_step, "unit": "ms/step", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"lattice_pile {WORKLOAD['nx']}x{WORKLOAD['ny']}x{WORKLOAD['nz']} seed "
+                               f"{WORKLOAD['seed']}, {s.nb} bodies ({s.nv} vertices, {s.nt} triangles, {s.ne} edges), "
+                               f"mu 0.3, kappa 1e8, dt 0.01, dhat 1e-3",
+                   "timed_steps": f"{args.start_step + args.warmup}..{args.start_step + args.warmup + args.steps - 1}",
+                   "l2": "256 MB buffer written between timed steps",
+                   "newton_tol": "1e-5 * bbox diagonal * dt", "pcg_rel_tol": 1e-4, "parallelism": f"replicas x{world}"},
+        "steps_per_s": 1e3 / ms_per_step,
+        "newton_iters_per_s": newton / (total_ms * 1e-3),
+        "contact_evals_per_s": cand / (total_ms * 1e-3),
+        "active_evals_per_s": act / (total_ms * 1e-3),
+        "newton_iters_per_step": newton / args.steps,
+        "e2e": {"value": e2e_ms / steps_total, "unit": "ms/step", "h2d_bytes_per_step": 2 * 12 * 8 * s.nb,
+                "d2h_bytes_per_step": 2 * 12 * 8 * s.nb},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernel_ms": {k: round(v["total_ms"], 3) for k, v in prof.items()},
+        "clocks": clocks,
+    }
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--start-step", type=int, default=20)
+    ap.add_argument("--impl", default="abd", choices=["abd", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = oracle_sample(args.start_step, args.warmup, args.steps)
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "ms/step", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["value"], "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "same recipe, sub-lattice sample (see cpu_baseline.sample)"},
+                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": cb["value"], "unit": "ms/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_abd(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            cb = oracle_sample(args.start_step, args.warmup, args.steps)
+            out["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        else:
+            out["cpu_baseline"] = None
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -123,7 +123,18 @@ typedef struct {
   long n_candidates, n_active, n_swept;
   double toi_min;      /* smallest CCD step bound seen in the step */
   double last_step;    /* max vertex |J dq| of the last Newton step */
+  long kernel_launches;       /* kernels the library launched for the step(s) */
+  long candidates_tested;     /* candidate pairs distance-tested in the step(s) */
+  long active_evaluated;      /* barrier terms (E, gradient, Hessian) evaluated */
 } abd_step_stats;
+
+/* Per-kernel timing of one kernel class, accumulated while profiling is on. */
+typedef struct {
+  const char* name;
+  long launches;
+  double total_ms;     /* sum of per-launch durations (CUDA events on the scene's stream) */
+  double bytes;        /* algorithmic bytes of those launches (0 if not defined) */
+} abd_kernel_profile;
 
 /* Fill *p with the defaults used by the benchmarks: dt 0.01, d-hat 1e-3,
  * kappa 1e8, gravity (0,0,-9.8), mu 0, eps_v 1e-3, newton_tol 0 (relative),
@@ -181,6 +192,13 @@ ABD_API abd_status abd_ccd_toi(abd_scene* s, const double* q_dev, const double* 
 /* Advance nsteps implicit-Euler time steps (Sec. 4); stats (may be NULL)
  * receives the statistics of the last step. */
 ABD_API abd_status abd_step(abd_scene* s, int nsteps, abd_step_stats* stats);
+
+/* Profiling (the step's tracing facility): on != 0 starts recording CUDA
+ * events around each launch of the timed kernel classes and clears the
+ * accumulators; 0 stops.  abd_get_profile synchronises the stream and fills
+ * up to cap entries (one per kernel class), *n the number of classes. */
+ABD_API abd_status abd_set_profiling(abd_scene* s, int on);
+ABD_API abd_status abd_get_profile(abd_scene* s, abd_kernel_profile* out, int cap, int* n);
 
 /* Message of the last error on the scene (empty string if none). */
 ABD_API const char* abd_last_error(const abd_scene* s);

@@ -56,7 +56,12 @@ class abd_solve_stats(C.Structure):
 class abd_step_stats(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("pcg_iters", C.c_int), ("ls_halvings", C.c_int),
                 ("n_candidates", C.c_long), ("n_active", C.c_long), ("n_swept", C.c_long),
-                ("toi_min", C.c_double), ("last_step", C.c_double)]
+                ("toi_min", C.c_double), ("last_step", C.c_double), ("kernel_launches", C.c_long),
+                ("candidates_tested", C.c_long), ("active_evaluated", C.c_long)]
+
+
+class abd_kernel_profile(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("launches", C.c_long), ("total_ms", C.c_double), ("bytes", C.c_double)]
 
 
 def _as_dict(st):
@@ -67,7 +72,7 @@ def _as_dict(st):
 _lib = None
 EXPORTS = ["abd_default_params", "abd_create_scene", "abd_destroy", "abd_set_state", "abd_get_state",
            "abd_energy_grad_hess", "abd_get_hessian", "abd_get_pairs", "abd_solve", "abd_ccd_toi", "abd_step",
-           "abd_last_error"]
+           "abd_set_profiling", "abd_get_profile", "abd_last_error"]
 
 
 def lib_path() -> str:
@@ -96,6 +101,8 @@ def load(build_if_missing: bool = True):
         "abd_solve": (i, [vp, vp, vp, vp]),
         "abd_ccd_toi": (i, [vp, vp, vp, vp]),
         "abd_step": (i, [vp, i, vp]),
+        "abd_set_profiling": (i, [vp, i]),
+        "abd_get_profile": (i, [vp, vp, i, vp]),
         "abd_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -163,6 +170,14 @@ def abd_ccd_toi(h, q_ptr, dq_ptr, toi):
 
 def abd_step(h, nsteps, stats):
     return load().abd_step(h, int(nsteps), stats)
+
+
+def abd_set_profiling(h, on):
+    return load().abd_set_profiling(h, int(on))
+
+
+def abd_get_profile(h, out, cap, n):
+    return load().abd_get_profile(h, out, cap, n)
 
 
 def abd_last_error(h) -> str:
@@ -327,3 +342,13 @@ class AbdScene:
         with self.torch.cuda.device(self.device):
             self._check(abd_step(self.h, n, C.byref(st)))
         return _as_dict(st)
+
+    def set_profiling(self, on):
+        self._check(abd_set_profiling(self.h, on))
+
+    def profile(self):
+        arr = (abd_kernel_profile * 16)()
+        n = C.c_int()
+        self._check(abd_get_profile(self.h, arr, 16, C.byref(n)))
+        return {arr[k].name.decode(): dict(launches=arr[k].launches, total_ms=arr[k].total_ms, bytes=arr[k].bytes)
+                for k in range(min(n.value, 16))}

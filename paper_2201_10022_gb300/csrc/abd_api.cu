@@ -13,6 +13,15 @@
 
 namespace abd {
 
+cudaEvent_t prof_event(Scene& s) {
+  if (s.prof.used == s.prof.pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    s.prof.pool.push_back(e);
+  }
+  return s.prof.pool[s.prof.used++];
+}
+
 void* Alloc::get(size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (custom) return a.alloc(bytes, (void*)stream, a.ctx);
@@ -228,6 +237,9 @@ abd_status with_capacity(Scene& s, F fn) {
   return ABD_ERR_CAPACITY;
 }
 
+// candidates of the enumeration that produced the current candidate set
+long cand_total(Scene& s) { return s.cand_last; }
+
 // one implicit-Euler step from (q^t, qdot^t); on error the state is unchanged
 abd_status newton_step(Scene& s, abd_step_stats* stats) {
   const size_t qb = sizeof(double) * 12 * s.nb;
@@ -237,6 +249,8 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
   loc.toi_min = 1.0;
   launch_transform(s, s.q.p, s.x.p);
   broad_and_enumerate(s, false, false);
+  read_status(s);
+  s.cand_last = (long)s.st_host->n_cand;
   abd_status status = ABD_ERR_NEWTON_MAXITER;
   for (int it = 0; it < s.prm.newton_max; ++it) {
     launch_transform(s, s.q.p, s.x.p);
@@ -244,8 +258,11 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
     read_status(s);
     if (s.st_host->flags & kCapFlags) return ABD_ERR_CAPACITY;
     if (abd_status r = flags_to_status(s, s.st_host->flags)) return r;
+    s.last_np = s.st_host->np;
     loc.n_active = s.st_host->nact;
-    loc.n_candidates = (long)s.st_host->n_cand;
+    loc.candidates_tested += cand_total(s);
+    loc.active_evaluated += s.st_host->nact;
+    loc.n_candidates = cand_total(s);
     // Newton direction: H dq = -g
     launch_negate(s, s.g.p, s.qsave.p, 12L * s.nb);
     double rel;
@@ -281,10 +298,12 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
     }
     broad_and_enumerate(s, true, true);
     read_status(s);
+    s.cand_last = (long)s.st_host->n_cand;
     if (s.st_host->flags & kCapFlags) return ABD_ERR_CAPACITY;
     if (abd_status r = flags_to_status(s, s.st_host->flags)) return r;
     double alpha = bits_to_double(s.st_host->toi_bits);
     loc.n_swept = (long)s.st_host->n_cand;
+    loc.candidates_tested += (long)s.st_host->n_cand;
     loc.toi_min = std::min(loc.toi_min, alpha);
     // line search: E(q + alpha dq) <= E(q) + slack over the swept candidates
     cudaMemcpyAsync(s.xt.p, s.x.p, sizeof(double4) * s.nv, cudaMemcpyDeviceToDevice, s.stream);
@@ -321,7 +340,12 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
     return status;
   }
   launch_finish_step(s);
-  if (stats) *stats = loc;
+  if (stats) {
+    loc.kernel_launches = stats->kernel_launches;
+    loc.candidates_tested += stats->candidates_tested;
+    loc.active_evaluated += stats->active_evaluated;
+    *stats = loc;
+  }
   return ABD_OK;
 }
 
@@ -542,6 +566,7 @@ void abd_destroy(abd_scene* S) {
   release(s, s.termv);
   release(s, s.ftermv);
   release(s, s.fric);
+  for (cudaEvent_t e : s.prof.pool) cudaEventDestroy(e);
   if (s.st) cudaFree(s.st);
   if (s.st_host) cudaFreeHost(s.st_host);
   delete S;
@@ -739,13 +764,32 @@ abd_status abd_step(abd_scene* S, int nsteps, abd_step_stats* stats) {
   s.err.clear();
   s.have_hess = false;
   const size_t qb = sizeof(double) * 12 * s.nb;
+  const long launches0 = s.nlaunch;
+  abd_step_stats acc;
+  memset(&acc, 0, sizeof(acc));
   for (int k = 0; k < nsteps; ++k) {
     cudaMemcpyAsync(s.qdotsave.p, s.qdot.p, qb, cudaMemcpyDeviceToDevice, s.stream);
     abd_status r = ABD_ERR_CAPACITY;
     for (int attempt = 0; attempt < 12 && r == ABD_ERR_CAPACITY; ++attempt) {
       reset_status(s);
       try {
-        r = newton_step(s, stats);
+        abd_step_stats one;
+        memset(&one, 0, sizeof(one));
+        r = newton_step(s, &one);
+        if (r == ABD_OK) {
+          long tested = acc.candidates_tested + one.candidates_tested;
+          long evald = acc.active_evaluated + one.active_evaluated;
+          int ni = acc.newton_iters + one.newton_iters, pi = acc.pcg_iters + one.pcg_iters;
+          int lh = acc.ls_halvings + one.ls_halvings;
+          double tmin = k ? std::min(acc.toi_min, one.toi_min) : one.toi_min;
+          acc = one;
+          acc.candidates_tested = tested;
+          acc.active_evaluated = evald;
+          acc.newton_iters = ni;
+          acc.pcg_iters = pi;
+          acc.ls_halvings = lh;
+          acc.toi_min = tmin;
+        }
       } catch (OomError&) {
         r = ABD_ERR_OOM;
       }
@@ -779,6 +823,41 @@ abd_status abd_step(abd_scene* S, int nsteps, abd_step_stats* stats) {
     }
   }
   cudaStreamSynchronize(s.stream);
+  acc.kernel_launches = s.nlaunch - launches0;
+  if (stats) *stats = acc;
+  return check_cuda(s);
+}
+
+static const char* kSlotNames[PF_COUNT] = {"enumerate_ccd", "active_set", "barrier_terms", "friction_terms",
+                                           "assemble_blocks", "body_terms", "pcg_spmv", "body_pairs"};
+
+abd_status abd_set_profiling(abd_scene* S, int on) {
+  if (!S) return ABD_ERR_INVALID_ARG;
+  Scene& s = S->s;
+  cudaStreamSynchronize(s.stream);
+  s.prof.on = on != 0;
+  s.prof.used = 0;
+  for (auto& sl : s.prof.slot) sl = Prof::Slot();
+  return check_cuda(s);
+}
+
+abd_status abd_get_profile(abd_scene* S, abd_kernel_profile* out, int cap, int* n) {
+  if (!S) return ABD_ERR_INVALID_ARG;
+  Scene& s = S->s;
+  cudaStreamSynchronize(s.stream);
+  if (n) *n = PF_COUNT;
+  for (int k = 0; k < PF_COUNT && k < cap && out; ++k) {
+    double ms = 0.0;
+    for (auto& e : s.prof.slot[k].ev) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e.first, e.second);
+      ms += t;
+    }
+    out[k].name = kSlotNames[k];
+    out[k].launches = s.prof.slot[k].launches;
+    out[k].total_ms = ms;
+    out[k].bytes = s.prof.slot[k].bytes;
+  }
   return check_cuda(s);
 }
 

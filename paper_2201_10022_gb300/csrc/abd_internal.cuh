@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/abd.h"
 
@@ -63,6 +65,20 @@ struct FricRec {
   int a, b;        // body pair (a < b)
   double gam[4], n[3], r[3], mu_lambda;
   int kind, i, j, type;
+};
+
+// ---- optional per-kernel timing (CUDA events on the scene's stream) -----------
+enum ProfSlot { PF_ENUM = 0, PF_ACTIVE, PF_BARRIER, PF_FRICTION, PF_ASSEMBLE, PF_BODY, PF_SPMV, PF_ROWS, PF_COUNT };
+
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  struct Slot {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    long launches = 0;
+    double bytes = 0;  // algorithmic bytes of the recorded launches
+  } slot[PF_COUNT];
 };
 
 // ---- scene ------------------------------------------------------------------
@@ -123,6 +139,10 @@ struct Scene {
   // PCG
   Buf<double> r, z, pv, Ap, part;
 
+  long nlaunch = 0;              // kernels launched by the library
+  long cand_last = 0;            // candidates of the last enumeration
+  Prof prof;
+
   DevStatus* st = nullptr;       // device
   DevStatus* st_host = nullptr;  // pinned mirror
   long last_np = 0;
@@ -130,6 +150,32 @@ struct Scene {
 };
 
 constexpr int kTermStride = 91;
+
+// launch bookkeeping: count every kernel; with profiling on, bracket the
+// launches of a slot with events
+cudaEvent_t prof_event(Scene& s);
+inline void counted(Scene& s, int n = 1) { s.nlaunch += n; }
+struct ProfScope {
+  Scene& s;
+  int slot;
+  cudaEvent_t a = nullptr;
+  double bytes;
+  ProfScope(Scene& sc, int sl, double b = 0) : s(sc), slot(sl), bytes(b) {
+    if (s.prof.on) {
+      a = prof_event(s);
+      cudaEventRecord(a, s.stream);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t e = prof_event(s);
+      cudaEventRecord(e, s.stream);
+      s.prof.slot[slot].ev.emplace_back(a, e);
+      s.prof.slot[slot].launches++;
+      s.prof.slot[slot].bytes += bytes;
+    }
+  }
+};
 constexpr int kBlkStride = 3 * 144 + 24 + 2;
 
 // ---- launchers (k_system.cu) -----------------------------------------------

@@ -437,6 +437,8 @@ int grid_for(long n, int per_block, int max_blocks) {
 void launch_enumerate(Scene& s, bool swept, bool ccd) {
   const int threads = 32 * kWarpsPerBlock;
   int grid = grid_for(s.last_np > 0 ? s.last_np : s.nb, kWarpsPerBlock, 152 * 16);
+  counted(s);
+  ProfScope ps(s, PF_ENUM);
   k_enumerate<<<grid, threads, 0, s.stream>>>(s.P.p, s.st, s.vbeg.p, s.tbeg.p, s.ebeg.p, s.tri.p, s.edge.p, s.x.p,
                                               swept ? s.x1.p : nullptr, s.dx.p, s.bbox.p, s.prm.dhat, s.maxc,
                                               s.cand.p, s.ccount.p, ccd, s.prm.ccd_s, s.prm.ccd_max, s.st);
@@ -444,27 +446,35 @@ void launch_enumerate(Scene& s, bool swept, bool ccd) {
 
 void launch_active(Scene& s, const double4* x) {
   int grid = grid_for(s.last_np > 0 ? s.last_np : s.nb, 8, 152 * 16);
+  counted(s);
+  ProfScope ps(s, PF_ACTIVE);
   k_active<<<grid, 256, 0, s.stream>>>(s.P.p, s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.prm.dhat, s.maxc,
                                        s.act.p, s.act_d2.p, s.acount.p, s.st);
 }
 
 void launch_barrier(Scene& s, int project, long cap) {
+  counted(s);
+  ProfScope ps(s, PF_BARRIER);
   k_barrier<<<152 * 8, 128, 0, s.stream>>>(s.st, s.aoff.p, s.act.p, s.tri.p, s.edge.p, s.x.p, s.prm.dhat,
                                           s.prm.kappa, s.maxc, project, cap, s.term.p, s.termv.p);
 }
 
 void launch_friction_lag(Scene& s) {
+  counted(s);
   k_friction_lag<<<152 * 4, 128, 0, s.stream>>>(s.st, s.P.p, s.aoff.p, s.act.p, s.act_d2.p, s.tri.p, s.edge.p,
                                                s.vbody.p, s.x.p, s.prm.dhat, s.prm.kappa, s.prm.mu, s.maxc, s.fric.p);
 }
 
 void launch_friction_eval(Scene& s, const double4* x, bool derivs) {
+  counted(s);
+  ProfScope ps(s, PF_FRICTION);
   k_friction_eval<<<152 * 4, 128, 0, s.stream>>>(s.st, s.fric.p, x, s.prm.eps_v * s.prm.dt, s.fterm.p,
                                                 s.ftermv.p, derivs);
 }
 
 void launch_pair_energy(Scene& s, const double4* x) {
   int grid = grid_for(s.last_np > 0 ? s.last_np : s.nb, 8, 152 * 16);
+  counted(s);
   k_pair_energy<<<grid, 256, 0, s.stream>>>(s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.prm.dhat,
                                             s.prm.kappa, s.maxc, s.Epair.p, s.st);
 }

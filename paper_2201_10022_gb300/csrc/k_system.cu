@@ -818,57 +818,73 @@ int blocks(long n, int t) { return (int)((n + t - 1) / t > 0 ? (n + t - 1) / t :
 // launchers
 // ---------------------------------------------------------------------------
 void launch_mass_moments(Scene& s) {
+  counted(s);
   k_mass_moments<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.tbeg.p, s.tri.p, s.xbar.p,
                                                                  s.density.p, s.is_static.p, s.mass10.p,
                                                                  s.vol.p);
 }
 
 void launch_predictor(Scene& s) {
+  counted(s);
   k_predictor<<<blocks(s.nb, 128), 128, 0, s.stream>>>(s.nb, s.is_static.p, s.qt.p, s.qdot.p, s.prm.dt,
                                                         s.prm.gravity[0], s.prm.gravity[1], s.prm.gravity[2],
                                                         s.qtilde.p);
 }
 
 void launch_transform(Scene& s, const double* q, double4* x) {
+  counted(s);
   k_transform<<<blocks(s.nv, 256), 256, 0, s.stream>>>(s.nv, s.vbody.p, s.xbar.p, q, x);
 }
 
 void launch_transform_dq(Scene& s, const double* dq) {
+  counted(s);
   k_transform_dq<<<blocks(s.nv, 256), 256, 0, s.stream>>>(s.nv, s.vbody.p, s.xbar.p, dq, s.x.p, s.dx.p, s.x1.p);
 }
 
 void launch_body_boxes(Scene& s, bool swept) {
+  counted(s);
   k_body_boxes<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.vbeg.p, s.x.p, swept ? s.x1.p : nullptr,
                                                                s.bbox.p);
 }
 
 void launch_scan(Scene& s, const int* cnt, int* off, const int* n_dev, int* total_dev, long cap, unsigned flag_bit,
                  unsigned long long* need) {
+  counted(s);
   k_scan<<<1, 1024, 0, s.stream>>>(cnt, off, n_dev, n_dev ? 0 : s.nb, total_dev, cap, flag_bit, need, s.st);
 }
 
 void launch_body_pairs(Scene& s) {
+  counted(s);
+  ProfScope pr(s, PF_ROWS);
   k_rows<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.is_static.p, s.bbox.p, s.prm.dhat, s.fpairs.p, s.st,
                                                         s.maxn, s.nbr.p, s.ncount.p, s.st);
   launch_scan(s, s.ncount.p, s.rowoff.p, nullptr, &s.st->np, (long)s.P.cap, ST_CAP_PAIRS, &s.st->need_pairs);
+  counted(s);
   k_rows_compact<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.nbr.p, s.ncount.p, s.rowoff.p, s.maxn, s.P.p,
                                                                 (long)s.P.cap);
 }
 
 void launch_incoming(Scene& s) {
   cudaMemsetAsync(s.in_cnt.p, 0, sizeof(int) * s.nb, s.stream);
+  counted(s);
   k_in_count<<<152 * 4, 256, 0, s.stream>>>(s.st, s.P.p, s.in_cnt.p);
+  counted(s);
   k_scan<<<1, 1024, 0, s.stream>>>(s.in_cnt.p, s.in_off.p, nullptr, s.nb, &s.st->pad, (long)s.P.cap, 0,
                                    &s.st->need_misc, s.st);
   cudaMemsetAsync(s.in_cnt.p, 0, sizeof(int) * s.nb, s.stream);
+  counted(s);
   k_in_fill<<<152 * 4, 256, 0, s.stream>>>(s.st, s.P.p, s.in_off.p, s.in_cnt.p, s.in_list.p);
+  counted(s);
   k_in_sort<<<blocks(s.nb, 128), 128, 0, s.stream>>>(s.nb, s.in_off.p, s.in_list.p);
 }
 
 void launch_fpairs(Scene& s) {
+  counted(s);
   k_flag_active<<<152 * 4, 256, 0, s.stream>>>(s.st, s.acount.p, s.flagbuf.p);
+  counted(s);
   k_scan<<<1, 1024, 0, s.stream>>>(s.flagbuf.p, s.posbuf.p, &s.st->np, 0, &s.st->nfp, (long)s.fpairs.cap,
                                    ST_CAP_PAIRS, &s.st->need_misc, s.st);
+  counted(s);
   k_fpairs<<<152 * 4, 256, 0, s.stream>>>(s.st, s.P.p, s.flagbuf.p, s.posbuf.p, s.aoff.p, s.fpairs.p, s.fpoff.p);
 }
 
@@ -877,55 +893,81 @@ __global__ void k_negate(long n, const double* in, double* out) {
 }
 
 void launch_negate(Scene& s, const double* in, double* out, long n) {
+  counted(s);
   k_negate<<<blocks(n, 256), 256, 0, s.stream>>>(n, in, out);
 }
 
 void launch_assemble(Scene& s) {
+  counted(s);
+  ProfScope pa(s, PF_ASSEMBLE);
   k_assemble<<<152 * 8, 256, 0, s.stream>>>(s.st, s.P.p, s.aoff.p, s.term.p, s.termv.p, s.fpairs.p, s.fpoff.p,
                                             s.fterm.p, s.ftermv.p, s.vbody.p, s.xbar.p, s.pblk.p);
 }
 
 void launch_body_terms(Scene& s, const double* q, bool hess) {
+  counted(s);
+  ProfScope pb(s, PF_BODY);
   k_body_terms<<<blocks(s.nb, 64), 64, 0, s.stream>>>(s.nb, s.is_static.p, q, s.qtilde.p, s.mass10.p, s.vol.p,
                                                        s.kappa_b.p, s.prm.dt, hess, s.Db.p, s.gb.p, s.Eb.p);
 }
 
 void launch_gather(Scene& s) {
+  counted(s);
   k_gather<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.is_static.p, s.rowoff.p, s.in_off.p, s.in_list.p,
                                                           s.pblk.p, s.Db.p, s.gb.p, s.D.p, s.g.p, s.st);
 }
 
 void launch_precond(Scene& s) {
+  counted(s);
   k_precond<<<blocks(s.nb, 64), 64, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.Pinv.p, s.st);
 }
 
 // energies of the last evaluation into st->energy: bodies, barrier terms or
 // per-body-pair barrier energies (energy-only pass), friction terms
 void launch_energy_total(Scene& s, bool from_terms) {
+  counted(s);
   k_reduce<<<1, 1024, 0, s.stream>>>(s.Eb.p, 2, nullptr, s.nb, &s.st->energy[1]);
+  counted(s);
   k_reduce<<<1, 1024, 0, s.stream>>>(s.Eb.p + 1, 2, nullptr, s.nb, &s.st->energy[2]);
+  counted(s);
   if (from_terms) k_reduce<<<1, 1024, 0, s.stream>>>(s.term.p, kTermStride, &s.st->nact, 0, &s.st->energy[3]);
   else k_reduce<<<1, 1024, 0, s.stream>>>(s.Epair.p, 1, &s.st->np, 0, &s.st->energy[3]);
+  counted(s);
   k_reduce<<<1, 1024, 0, s.stream>>>(s.fterm.p, kTermStride, &s.st->nfr, 0, &s.st->energy[4]);
+  counted(s);
   k_energy_sum<<<1, 1, 0, s.stream>>>(s.st);
 }
 
 int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res) {
   const int nbk = blocks(s.nb, 128);
+  counted(s);
   k_pcg_init<<<nbk, 128, 0, s.stream>>>(s.nb, s.is_static.p, s.Pinv.p, rhs, xout, s.r.p, s.z.p, s.pv.p, s.part.p);
+  counted(s);
   k_pcg_start<<<1, 256, 0, s.stream>>>(s.part.p, nbk, s.st);
   const int sblocks = blocks(12L * s.nb, kPcgThreads);
   const double tol2 = rel_tol * rel_tol;
+  // algorithmic bytes of one product: every stored block once (diagonal and
+  // upper off-diagonal, 144 doubles each), the vector read once and the
+  // product written once, the pair list once
+  const double spmv_bytes = 8.0 * 144.0 * (s.nb + (double)s.last_np) + 2.0 * 8.0 * 12.0 * s.nb + 8.0 * s.last_np;
   int it = 0;
   const int chunk = 16;
   while (true) {
     for (int k = 0; k < chunk; ++k) {
-      k_spmv<<<sblocks, kPcgThreads, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.rowoff.p, s.in_off.p, s.in_list.p,
-                                                    s.P.p, s.pblk.p, s.pv.p, s.Ap.p, s.part.p, s.st);
+      counted(s);
+      {
+        ProfScope pv(s, PF_SPMV, spmv_bytes);
+        k_spmv<<<sblocks, kPcgThreads, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.rowoff.p, s.in_off.p,
+                                                      s.in_list.p, s.P.p, s.pblk.p, s.pv.p, s.Ap.p, s.part.p, s.st);
+      }
+      counted(s);
       k_pcg_alpha<<<1, 256, 0, s.stream>>>(s.part.p, sblocks, s.st);
+      counted(s);
       k_pcg_update<<<nbk, 128, 0, s.stream>>>(s.nb, s.is_static.p, s.Pinv.p, s.pv.p, s.Ap.p, xout, s.r.p, s.z.p,
                                               s.part.p, s.st);
+      counted(s);
       k_pcg_beta<<<1, 256, 0, s.stream>>>(s.part.p, nbk, tol2, s.st);
+      counted(s);
       k_pcg_dir<<<blocks(12L * s.nb, 256), 256, 0, s.stream>>>(12L * s.nb, s.z.p, s.pv.p, s.st);
     }
     it += chunk;
@@ -942,14 +984,17 @@ int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_
 }
 
 void launch_max_step(Scene& s) {
+  counted(s);
   k_max_step<<<blocks(s.nv, 256), 256, 0, s.stream>>>(s.nv, s.vbody.p, s.is_static.p, s.dx.p, s.st);
 }
 
 void launch_trial(Scene& s, double alpha) {
+  counted(s);
   k_trial<<<blocks(12L * s.nb, 256), 256, 0, s.stream>>>(12 * s.nb, s.q.p, s.dq.p, alpha, s.qtrial.p);
 }
 
 void launch_finish_step(Scene& s) {
+  counted(s);
   k_finish<<<blocks(s.nb, 128), 128, 0, s.stream>>>(s.nb, s.is_static.p, s.q.p, s.prm.dt, s.qt.p, s.qdot.p);
   launch_predictor(s);
 }
