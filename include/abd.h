@@ -200,6 +200,28 @@ ABD_API abd_status abd_step(abd_scene* s, int nsteps, abd_step_stats* stats);
 ABD_API abd_status abd_set_profiling(abd_scene* s, int on);
 ABD_API abd_status abd_get_profile(abd_scene* s, abd_kernel_profile* out, int cap, int* n);
 
+/* Minimum additive-CCD time of impact over a caller-given list of pairs,
+ * allocating nothing.  The paper has no counterpart: this serves callers
+ * that cannot allocate device memory when they need a step bound (a fixed
+ * memory pool owned elsewhere, allocation-free real-time loops).
+ *   x_dev, dx_dev  nv*3 doubles (device): start positions and the linear
+ *                  displacement of each vertex over the step
+ *   verts_dev      npairs*4 ints (device): the pair's vertices, ordered as in
+ *                  abd_get_pairs (point then triangle, or edge then edge)
+ *   kind_dev       npairs bytes (device): 0 point-triangle, 1 edge-edge
+ *   ccd_s, ccd_max ACCD gap fraction and iteration cap (as abd_params)
+ *   toi_host       receives min over pairs of the time of impact in (0, 1]
+ * Scratch is a file-scope device array of 262,144 pair slots (2 MiB) that
+ * every GPU loading the library holds until exit; npairs beyond that returns
+ * ABD_ERR_CAPACITY, an out-of-range vertex or kind ABD_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU (other streams, other threads) race.  The
+ * call synchronises `stream` (a cudaStream_t, NULL = legacy default). */
+ABD_API abd_status abd_ccd_toi_pairs_noalloc(const double* x_dev, const double* dx_dev, int nv, const int* verts_dev,
+                                             const unsigned char* kind_dev, long npairs, double ccd_s, int ccd_max,
+                                             void* stream, double* toi_host);
+
 /* Message of the last error on the scene (empty string if none). */
 ABD_API const char* abd_last_error(const abd_scene* s);
 

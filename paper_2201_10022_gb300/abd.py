@@ -72,7 +72,7 @@ def _as_dict(st):
 _lib = None
 EXPORTS = ["abd_default_params", "abd_create_scene", "abd_destroy", "abd_set_state", "abd_get_state",
            "abd_energy_grad_hess", "abd_get_hessian", "abd_get_pairs", "abd_solve", "abd_ccd_toi", "abd_step",
-           "abd_set_profiling", "abd_get_profile", "abd_last_error"]
+           "abd_set_profiling", "abd_get_profile", "abd_ccd_toi_pairs_noalloc", "abd_last_error"]
 
 
 def lib_path() -> str:
@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True):
         "abd_step": (i, [vp, i, vp]),
         "abd_set_profiling": (i, [vp, i]),
         "abd_get_profile": (i, [vp, vp, i, vp]),
+        "abd_ccd_toi_pairs_noalloc": (i, [vp, vp, i, vp, vp, l, d, i, vp, vp]),
         "abd_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -178,6 +179,13 @@ def abd_set_profiling(h, on):
 
 def abd_get_profile(h, out, cap, n):
     return load().abd_get_profile(h, out, cap, n)
+
+
+def abd_ccd_toi_pairs_noalloc(x_ptr, dx_ptr, nv, verts_ptr, kind_ptr, npairs, ccd_s, ccd_max, stream, toi):
+    """Allocation-free CCD bound over caller-given pairs (see include/abd.h)."""
+    return load().abd_ccd_toi_pairs_noalloc(C.c_void_p(x_ptr), C.c_void_p(dx_ptr), int(nv), C.c_void_p(verts_ptr),
+                                            C.c_void_p(kind_ptr), int(npairs), float(ccd_s), int(ccd_max),
+                                            C.c_void_p(stream), toi)
 
 
 def abd_last_error(h) -> str:
