@@ -155,6 +155,7 @@ def run_abd(args, rank, world):
     torch.cuda.synchronize()
     clk.start()
     g.set_profiling(True)
+    torch.cuda.nvtx.range_push("timed")
     ms, stats = [], []
     for k in range(args.steps):
         flush.zero_()
@@ -165,6 +166,7 @@ def run_abd(args, rank, world):
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
         stats.append(st)
+    torch.cuda.nvtx.range_pop()
     prof = g.profile()
     g.set_profiling(False)
     torch.cuda.synchronize()

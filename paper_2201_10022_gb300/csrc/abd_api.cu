@@ -145,6 +145,10 @@ bool handle_capacity(Scene& s) {
     size_term_buffers(s, std::max<size_t>(2 * term_cap(s), (size_t)(1.5 * (double)h.need_act) + 64));
     grew = true;
   }
+  if (h.flags & ST_CAP_HASH) {
+    grow(s, s.entries, std::max<size_t>(2 * s.entries.cap, (size_t)(1.5 * (double)h.need_misc) + 64));
+    grew = true;
+  }
   return grew;
 }
 
@@ -219,7 +223,7 @@ abd_status flags_to_status(Scene& s, unsigned f) {
   return ABD_OK;
 }
 
-const unsigned kCapFlags = ST_CAP_ROWS | ST_CAP_CANDS | ST_CAP_PAIRS | ST_CAP_ACTIVE;
+const unsigned kCapFlags = ST_CAP_ROWS | ST_CAP_CANDS | ST_CAP_PAIRS | ST_CAP_ACTIVE | ST_CAP_HASH;
 
 // run fn until no capacity flag is raised (buffers grow in between)
 template <typename F>
@@ -272,10 +276,23 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
       return ABD_ERR_PCG_BREAKDOWN;
     }
     loc.pcg_iters += its < 0 ? s.prm.pcg_max : its;
-    // convergence on the vertex-space step, before the line search
+    // E(q) over the active set of this iteration: the line search's reference
+    const double E0 = s.st_host->energy[0];
+    // step length for the convergence test, then (in the same batch) the CCD
+    // bound over the swept candidates and the first trial at alpha = bound;
+    // the swept candidates also serve the next iteration
     launch_transform_dq(s, s.dq.p);
     cudaMemsetAsync(&s.st->step_bits, 0, sizeof(unsigned long long), s.stream);
     launch_max_step(s);
+    {
+      // reset the CCD minimum (toi_bits only: step_bits sits next to it)
+      const double one = 1.0;
+      cudaMemcpyAsync(&s.st->toi_bits, &one, sizeof(double), cudaMemcpyHostToDevice, s.stream);
+    }
+    broad_and_enumerate(s, true, true);
+    launch_trial(s, 1.0, true);
+    launch_transform(s, s.qtrial.p, s.xt.p);
+    eval_energy(s, s.qtrial.p);
     read_status(s);
     double step = bits_to_double(s.st_host->step_bits);
     loc.last_step = step;
@@ -288,35 +305,23 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
       break;
     }
     loc.newton_iters++;
-    // CCD bound over the swept candidates; they also serve the next iteration
-    {
-      DevStatus& h = *s.st_host;
-      double one = 1.0;
-      memcpy(&h.toi_bits, &one, 8);
-      h.n_cand = 0;
-      cudaMemcpyAsync(&s.st->toi_bits, &h.toi_bits, 16, cudaMemcpyHostToDevice, s.stream);
-    }
-    broad_and_enumerate(s, true, true);
-    read_status(s);
     s.cand_last = (long)s.st_host->n_cand;
     if (s.st_host->flags & kCapFlags) return ABD_ERR_CAPACITY;
-    if (abd_status r = flags_to_status(s, s.st_host->flags)) return r;
+    if (abd_status r = flags_to_status(s, s.st_host->flags & ~ST_INTERSECT)) return r;
     double alpha = bits_to_double(s.st_host->toi_bits);
     loc.n_swept = (long)s.st_host->n_cand;
     loc.candidates_tested += (long)s.st_host->n_cand;
     loc.toi_min = std::min(loc.toi_min, alpha);
     // line search: E(q + alpha dq) <= E(q) + slack over the swept candidates
-    cudaMemcpyAsync(s.xt.p, s.x.p, sizeof(double4) * s.nv, cudaMemcpyDeviceToDevice, s.stream);
-    eval_energy(s, s.q.p);
-    read_status(s);
-    const double E0 = s.st_host->energy[0];
     const double slack = s.prm.ls_slack_rel * (fabs(E0) + 1.0);
     bool ok = false;
     for (int ls = 0; ls <= s.prm.ls_max; ++ls) {
-      launch_trial(s, alpha);
-      launch_transform(s, s.qtrial.p, s.xt.p);
-      eval_energy(s, s.qtrial.p);
-      read_status(s);
+      if (ls > 0) {
+        launch_trial(s, alpha, false);
+        launch_transform(s, s.qtrial.p, s.xt.p);
+        eval_energy(s, s.qtrial.p);
+        read_status(s);
+      }
       if (s.st_host->flags & ST_INTERSECT) {
         s.err = "line search reached zero distance";
         return ABD_ERR_INITIAL_INTERSECTION;
@@ -463,6 +468,19 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
     grow(s, s.rowoff, nb + 1);
     grow(s, s.in_off, nb + 1);
     grow(s, s.in_cnt, nb);
+    grow(s, s.hcount, nb);
+    grow(s, s.hoff, nb + 1);
+    grow(s, s.large, nb);
+    grow(s, s.large_pos, nb + 1);
+    grow(s, s.large_list, nb);
+    {
+      long t = 1024;
+      while (t < 16L * nb) t <<= 1;
+      s.hash_T = (int)t;
+    }
+    grow(s, s.slot_cnt, (size_t)s.hash_T);
+    grow(s, s.slot_off, (size_t)s.hash_T + 1);
+    grow(s, s.entries, 16L * nb + 1024);
     s.maxc = 256;
     size_pair_buffers(s, std::max<size_t>(1024, 8L * nb));
     size_term_buffers(s, std::max<size_t>(4096, 16L * nb));
@@ -474,6 +492,25 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
   }
   std::vector<double4> xb(nv);
   for (int v = 0; v < nv; ++v) xb[v] = make_double4(d->xbar[3 * v], d->xbar[3 * v + 1], d->xbar[3 * v + 2], 0.0);
+  // spatial-hash cell: the largest rest-frame box diagonal of the dynamic
+  // bodies, so every dynamic body's box spans at most 2 cells per axis
+  {
+    std::vector<double> diam;
+    for (int b = 0; b < nb; ++b) {
+      if (d->is_static[b] || vbeg[b] == vbeg[b + 1]) continue;
+      double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+      for (int v = vbeg[b]; v < vbeg[b + 1]; ++v)
+        for (int k = 0; k < 3; ++k) {
+          lo[k] = std::min(lo[k], d->xbar[3 * v + k]);
+          hi[k] = std::max(hi[k], d->xbar[3 * v + k]);
+        }
+      diam.push_back(sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                          (hi[2] - lo[2]) * (hi[2] - lo[2])));
+    }
+    double big = 1.0;
+    if (!diam.empty()) big = *std::max_element(diam.begin(), diam.end());
+    s.cell_h = std::max(big, 4.0 * prm->dhat) + 2.0 * prm->dhat;
+  }
   cudaMemcpyAsync(s.xbar.p, xb.data(), sizeof(double4) * nv, cudaMemcpyHostToDevice, s.stream);
   cudaMemcpyAsync(s.vbody.p, d->vbody, sizeof(int) * nv, cudaMemcpyHostToDevice, s.stream);
   if (nt) cudaMemcpyAsync(s.tri.p, d->tri, sizeof(int) * 3 * nt, cudaMemcpyHostToDevice, s.stream);
@@ -557,7 +594,8 @@ void abd_destroy(abd_scene* S) {
     release(s, *b);
   for (Buf<double4>* b : {&s.x, &s.dx, &s.x1, &s.xt}) release(s, *b);
   for (Buf<int>* b : {&s.nbr, &s.ncount, &s.rowoff, &s.in_off, &s.in_cnt, &s.in_list, &s.ccount, &s.acount, &s.aoff,
-                      &s.fpoff, &s.flagbuf, &s.posbuf})
+                      &s.fpoff, &s.flagbuf, &s.posbuf, &s.hcount, &s.hoff, &s.large, &s.large_pos, &s.large_list,
+                      &s.slot_cnt, &s.slot_off, &s.entries})
     release(s, *b);
   release(s, s.P);
   release(s, s.fpairs);

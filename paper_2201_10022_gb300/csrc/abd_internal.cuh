@@ -23,6 +23,7 @@ enum : unsigned {
   ST_INTERSECT = 1u << 5,      // a pair at zero distance
   ST_NONFINITE = 1u << 6,
   ST_PCG_BREAKDOWN = 1u << 7,
+  ST_CAP_HASH = 1u << 8,       // spatial-hash entry storage exceeded
 };
 
 struct DevStatus {
@@ -34,6 +35,9 @@ struct DevStatus {
   int nfr;                      // lagged friction terms
   int nfp;                      // friction body pairs
   int pad;
+  int nlarge;                   // bodies handled outside the spatial hash
+  int nent;                     // spatial-hash entries
+  int pad2[2];
   unsigned long long need_pairs;  // body pairs needed
   unsigned long long need_act;    // active terms needed
   unsigned long long need_misc;   // other scans
@@ -101,6 +105,11 @@ struct Scene {
   Buf<double> q, qdot, qt, qtilde, dq, qtrial, qsave, qdotsave;
   Buf<double4> x, dx, x1, xt;
   Buf<double> bbox;    // nb*6
+
+  // spatial hash over body boxes
+  double cell_h = 1.0;         // cell edge
+  int hash_T = 1;              // slots (power of two)
+  Buf<int> hcount, hoff, large, large_pos, large_list, slot_cnt, slot_off, entries;
 
   // body pairs
   int maxn = 0;        // neighbours per row
@@ -193,7 +202,7 @@ void launch_precond(Scene& s);
 void launch_energy_total(Scene& s, bool with_pairs);
 int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res);
 void launch_max_step(Scene& s);
-void launch_trial(Scene& s, double alpha);
+void launch_trial(Scene& s, double alpha, bool alpha_from_ccd);
 void launch_finish_step(Scene& s);
 // exclusive scan of cnt[0..*n_dev) into off[0..*n_dev] (off[n] = total), total
 // also to *total_dev; if the total exceeds cap, flag_bit is raised.

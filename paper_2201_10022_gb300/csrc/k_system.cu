@@ -2,6 +2,8 @@
 // (Sec. 3), body boxes and body-pair culling (Sec. 4.2), per-body inertia and
 // orthogonality terms (Sec. 3.2 / Sec. 4), Hessian assembly by body-pair
 // blocks (Sec. 4.3), block-Jacobi PCG, and deterministic reductions.
+#include <algorithm>
+
 #include "abd_internal.cuh"
 #include "derivs.cuh"
 
@@ -135,38 +137,133 @@ __global__ void k_body_boxes(int nb, const int* vbeg, const double4* x, const do
 
 // ---------------------------------------------------------------------------
 // body pairs (a < b, not both static) whose boxes are within dhat, plus the
-// lagged friction body pairs; one row per body a, sorted by b
+// lagged friction body pairs; one row per body (the smaller index, or the
+// non-large body), sorted by the other body.  A spatial hash over the bodies'
+// d-hat-dilated boxes finds the neighbours of ordinary bodies; bodies whose
+// box spans more than kMaxCells cells ("large", e.g. a ground slab) are tested
+// directly against every body.
 // ---------------------------------------------------------------------------
-__global__ void k_rows(int nb, const uint8_t* is_static, const double* bbox, double dhat, const int2* fpairs,
-                       const DevStatus* cst, int maxn, int* nbr, int* ncount, DevStatus* st) {
+constexpr int kMaxCells = 64;
+
+__device__ __forceinline__ int cell_of(double v, double inv_h) { return (int)floor(v * inv_h); }
+__device__ __forceinline__ unsigned slot_of(int ix, int iy, int iz, unsigned mask) {
+  return ((unsigned)ix * 73856093u ^ (unsigned)iy * 19349663u ^ (unsigned)iz * 83492791u) & mask;
+}
+__device__ __forceinline__ void cell_range(const double* bb, double dhat, double inv_h, int lo[3], int hi[3]) {
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = cell_of(bb[k] - dhat, inv_h);
+    hi[k] = cell_of(bb[3 + k] + dhat, inv_h);
+  }
+}
+__device__ __forceinline__ bool bodies_near(const double* A, const double* B, double dhat) {
+  for (int k = 0; k < 3; ++k) {
+    if (!(__dsub_rn(A[k], B[3 + k]) <= dhat)) return false;
+    if (!(__dsub_rn(B[k], A[3 + k]) <= dhat)) return false;
+  }
+  return true;
+}
+
+__global__ void k_hash_count(int nb, const double* bbox, double dhat, double inv_h, int* count, int* large) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  int lo[3], hi[3];
+  cell_range(bbox + 6 * b, dhat, inv_h, lo, hi);
+  long n = (long)(hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
+  const bool big = n > kMaxCells || n <= 0;
+  large[b] = big ? 1 : 0;
+  count[b] = big ? 0 : (int)n;
+}
+
+__global__ void k_large_list(int nb, const int* large, const int* pos, int* list) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nb && large[b]) list[pos[b]] = b;
+}
+
+__global__ void k_hash_slots(int nb, const double* bbox, const int* large, double dhat, double inv_h, unsigned mask,
+                             int* slot_cnt, const int* slot_off, int* entries, long cap, bool fill) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb || large[b]) return;
+  int lo[3], hi[3];
+  cell_range(bbox + 6 * b, dhat, inv_h, lo, hi);
+  for (int ix = lo[0]; ix <= hi[0]; ++ix)
+    for (int iy = lo[1]; iy <= hi[1]; ++iy)
+      for (int iz = lo[2]; iz <= hi[2]; ++iz) {
+        unsigned h = slot_of(ix, iy, iz, mask);
+        int pos = atomicAdd(&slot_cnt[h], 1);
+        if (fill && (long)slot_off[h] + pos < cap) entries[slot_off[h] + pos] = b;
+      }
+}
+
+__global__ void k_rows(int nb, const uint8_t* is_static, const double* bbox, double dhat, double inv_h, unsigned mask,
+                       const int* large, const int* large_list, const int* slot_off, const int* entries,
+                       const int2* fpairs, const DevStatus* cst, int maxn, int* nbr, int* ncount, DevStatus* st) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int nfp = cst->nfp;
+  const int nfp = cst->nfp, nlarge = cst->nlarge;
   for (int a = warp; a < nb; a += nwarps) {
-    double alo[3], ahi[3];
-    for (int k = 0; k < 3; ++k) {
-      alo[k] = bbox[6 * a + k];
-      ahi[k] = bbox[6 * a + 3 + k];
-    }
+    const double* A = bbox + 6 * a;
     const bool sa = is_static[a];
     int* out = nbr + (size_t)a * maxn;
     int base = 0;
-    for (int b0 = a + 1; b0 < nb; b0 += 32) {
-      int b = b0 + lane;
-      bool keep = false;
-      if (b < nb && !(sa && is_static[b])) {
-        keep = true;
-        for (int k = 0; k < 3; ++k) {
-          if (!(__dsub_rn(alo[k], bbox[6 * b + 3 + k]) <= dhat)) keep = false;
-          if (!(__dsub_rn(bbox[6 * b + k], ahi[k]) <= dhat)) keep = false;
-        }
-      }
+    auto emit = [&](bool keep, int b) {
       unsigned m = __ballot_sync(kFull, keep);
       if (keep) {
         int pos = base + __popc(m & ((1u << lane) - 1u));
         if (pos < maxn) out[pos] = b;
       }
       base += __popc(m);
+    };
+    if (large[a]) {
+      continue;  // rows of large bodies: k_rows_large
+    } else {
+      int lo[3], hi[3];
+      cell_range(A, dhat, inv_h, lo, hi);
+      for (int ix = lo[0]; ix <= hi[0]; ++ix)
+        for (int iy = lo[1]; iy <= hi[1]; ++iy)
+          for (int iz = lo[2]; iz <= hi[2]; ++iz) {
+            unsigned h = slot_of(ix, iy, iz, mask);
+            const int e0 = slot_off[h], e1 = slot_off[h + 1];
+            for (int k0 = e0; k0 < e1; k0 += 32) {
+              int k = k0 + lane;
+              bool keep = false;
+              int b = -1;
+              if (k < e1) {
+                b = entries[k];
+                const double* B = bbox + 6 * b;
+                if (b > a && !(sa && is_static[b]) && bodies_near(A, B, dhat)) {
+                  // report the pair only in the cell of the low corner of the
+                  // dilated boxes' overlap, so it is found once
+                  keep = cell_of(fmax(A[0], B[0]) - dhat, inv_h) == ix && cell_of(fmax(A[1], B[1]) - dhat, inv_h) == iy &&
+                         cell_of(fmax(A[2], B[2]) - dhat, inv_h) == iz;
+                }
+              }
+              emit(keep, b);
+            }
+          }
+      // large bodies after a
+      for (int k0 = 0; k0 < nlarge; k0 += 32) {
+        int k = k0 + lane;
+        int b = k < nlarge ? large_list[k] : -1;
+        bool keep = b > a && !(sa && is_static[b]) && bodies_near(A, bbox + 6 * b, dhat);
+        emit(keep, b);
+      }
+      // hash order is arbitrary: sort the row and drop repeats (a body
+      // listed twice in one slot when two of its cells share the slot)
+      if (lane == 0) {
+        const int n = min(base, maxn);
+        for (int i = 1; i < n; ++i) {
+          int v = out[i], j = i - 1;
+          while (j >= 0 && out[j] > v) {
+            out[j + 1] = out[j];
+            --j;
+          }
+          out[j + 1] = v;
+        }
+        int u = 0;
+        for (int i = 0; i < n; ++i)
+          if (u == 0 || out[i] != out[u - 1]) out[u++] = out[i];
+        if (base <= maxn) base = u;
+      }
     }
     if (lane == 0 && nfp > 0) {
       // friction neighbours of row a: fpairs entries with .x == a (sorted)
@@ -196,6 +293,102 @@ __global__ void k_rows(int nb, const uint8_t* is_static, const double* bbox, dou
         atomicMax(&st->need_row, base);
       }
     }
+    __syncwarp();
+  }
+}
+
+// rows of large bodies: one block scans every body after the large one, in
+// order, with a block-wide ordered compaction; then the friction merge
+__global__ void k_rows_large(int nb, const uint8_t* is_static, const double* bbox, double dhat, const int* large_list,
+                             const int2* fpairs, const DevStatus* cst, int maxn, int* nbr, int* ncount, DevStatus* st) {
+  __shared__ int wcount[32];
+  __shared__ int wbase[33];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int nlarge = cst->nlarge, nfp = cst->nfp;
+  for (int li = blockIdx.x; li < nlarge; li += gridDim.x) {
+    const int a = large_list[li];
+    const double* A = bbox + 6 * a;
+    const bool sa = is_static[a];
+    int* out = nbr + (size_t)a * maxn;
+    int base = 0;
+    for (int b0 = a + 1; b0 < nb; b0 += 1024) {
+      const int b = b0 + t;
+      const bool keep = b < nb && !(sa && is_static[b]) && bodies_near(A, bbox + 6 * b, dhat);
+      const unsigned m = __ballot_sync(kFull, keep);
+      if (lane == 0) wcount[w] = __popc(m);
+      __syncthreads();
+      if (t == 0) {
+        wbase[0] = 0;
+        for (int k = 0; k < 32; ++k) wbase[k + 1] = wbase[k] + wcount[k];
+      }
+      __syncthreads();
+      if (keep) {
+        const int pos = base + wbase[w] + __popc(m & ((1u << lane) - 1u));
+        if (pos < maxn) out[pos] = b;
+      }
+      base += wbase[32];
+      __syncthreads();
+    }
+    // friction neighbours of the row (fpairs entries with .x == a): the
+    // threads check membership by binary search; the few missing ones are
+    // inserted by one thread
+    __shared__ int frange[2], nmiss;
+    __shared__ int miss[256];
+    if (t == 0) {
+      int lo = 0, hi = nfp;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (fpairs[mid].x < a) lo = mid + 1;
+        else hi = mid;
+      }
+      int e = lo;
+      while (e < nfp && fpairs[e].x == a) ++e;
+      frange[0] = lo;
+      frange[1] = e;
+      nmiss = 0;
+    }
+    __syncthreads();
+    const int n0 = min(base, maxn);
+    bool overflow_miss = false;
+    for (int f = frange[0] + t; f < frange[1]; f += blockDim.x) {
+      const int b = fpairs[f].y;
+      int lo = 0, hi = n0;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (out[mid] < b) lo = mid + 1;
+        else hi = mid;
+      }
+      if (!(lo < n0 && out[lo] == b)) {
+        int k = atomicAdd(&nmiss, 1);
+        if (k < 256) miss[k] = b;
+        else overflow_miss = true;
+      }
+    }
+    __syncthreads();
+    if (t == 0) {
+      // more misses than the buffer holds: walk every friction neighbour
+      const bool all = nmiss > 256;
+      const int nm = all ? frange[1] - frange[0] : nmiss;
+      for (int i = 0; i < nm; ++i) {
+        const int b = all ? fpairs[frange[0] + i].y : miss[i];
+        const int n = min(base, maxn);
+        int pos = 0;
+        while (pos < n && out[pos] < b) ++pos;
+        if (pos < n && out[pos] == b) continue;
+        if (base < maxn) {
+          for (int k = n; k > pos; --k) out[k] = out[k - 1];
+          out[pos] = b;
+        }
+        ++base;
+      }
+      ncount[a] = min(base, maxn);
+      if (base > maxn) {
+        set_flag(st, ST_CAP_ROWS);
+        atomicMax(&st->need_row, base);
+      }
+    }
+    (void)overflow_miss;
+    __syncthreads();
   }
 }
 
@@ -210,31 +403,52 @@ __global__ void k_rows_compact(int nb, const int* nbr, const int* ncount, const 
   }
 }
 
-// single-block exclusive scan (fixed order)
+// single-block exclusive scan in tiles of 4096 (coalesced loads, fixed order)
 __global__ void k_scan(const int* cnt, int* off, const int* n_dev, int n_const, int* total_dev, long cap,
                        unsigned flag, unsigned long long* need, DevStatus* st) {
-  __shared__ long long sums[1024];
+  __shared__ long long wsum[32];
+  __shared__ long long carry_s;
   const int n = n_dev ? *n_dev : n_const;
-  const int t = threadIdx.x;
-  const int chunk = (n + 1023) / 1024;
-  const int beg = min(n, t * chunk), end = min(n, beg + chunk);
-  long long local = 0;
-  for (int i = beg; i < end; ++i) local += cnt[i];
-  sums[t] = local;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t == 0) carry_s = 0;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    long long v = t >= o ? sums[t - o] : 0;
+  for (int base = 0; base < n; base += 4096) {
+    int v[4];
+    long long loc = 0;
+    for (int k = 0; k < 4; ++k) {
+      const int i = base + 4 * t + k;
+      v[k] = i < n ? cnt[i] : 0;
+      loc += v[k];
+    }
+    // inclusive scan of the per-thread sums: warp, then warp totals
+    long long inc = loc;
+    for (int o = 1; o < 32; o <<= 1) {
+      long long u = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (lane == 31) wsum[w] = inc;
     __syncthreads();
-    sums[t] += v;
+    if (w == 0) {
+      long long x = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        long long u = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += u;
+      }
+      wsum[lane] = x;
+    }
+    __syncthreads();
+    long long run = carry_s + (w ? wsum[w - 1] : 0) + inc - loc;
+    for (int k = 0; k < 4; ++k) {
+      const int i = base + 4 * t + k;
+      if (i < n) off[i] = (int)run;
+      run += v[k];
+    }
+    __syncthreads();
+    if (t == 1023) carry_s += wsum[31];
     __syncthreads();
   }
-  long long run = sums[t] - local;
-  for (int i = beg; i < end; ++i) {
-    off[i] = (int)run;
-    run += cnt[i];
-  }
-  if (t == 1023) {
-    long long total = sums[1023];
+  if (t == 0) {
+    long long total = carry_s;
     off[n] = (int)total;
     if (total > cap) {
       set_flag(st, flag);
@@ -443,24 +657,53 @@ __global__ void k_body_terms(int nb, const uint8_t* is_static, const double* q, 
   Eb[2 * b] = Ein;
   Eb[2 * b + 1] = dt2 * V;
   if (!hess) return;
-  // Hessian blocks: (i,i) 4kv[2 a_i a_i^T + (|a_i|^2 - 1) I + sum_{j!=i} a_j a_j^T],
-  //                 (i,j) 4kv[a_j a_i^T + (a_i.a_j) I]
+  // PSD part of the orthogonality Hessian from its closed-form eigensystem.
+  // V = kv sum_i (s_i^2 - 1)^2 over the singular values of A = U S V^T; with
+  // X an orthonormal basis of 3x3 matrices and W = U X V^T, the second
+  // variation of V along W is
+  //   X = e_i e_i^T:                        kv (12 s_i^2 - 4)
+  //   X = (e_i e_j^T +- e_j e_i^T)/sqrt2:   4 kv (s_i^2 +- s_i s_j + s_j^2 - 1)
+  // and these nine W are the Hessian's eigenvectors over vec(A) (row order).
   double A9[81];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
+  {
+    // A^T A = V S^2 V^T by cyclic Jacobi on the 3x3 symmetric matrix
+    double C[9], Vm[9];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) C[3 * r + c] = comp(a[0], r) * comp(a[0], c) + comp(a[1], r) * comp(a[1], c) +
+                                                comp(a[2], r) * comp(a[2], c);
+    jacobi_eig<3, double>(C, Vm);
+    double sg[3], Um[9];
+    for (int i = 0; i < 3; ++i) sg[i] = sqrt(fmax(C[4 * i], 0.0));
+    // U = A V S^-1 (columns); A is close to a rotation, so S is far from 0
+    for (int i = 0; i < 3; ++i) {
+      const double inv = sg[i] > 0.0 ? 1.0 / sg[i] : 0.0;
+      for (int r = 0; r < 3; ++r) {
+        double t = 0.0;
+        for (int k = 0; k < 3; ++k) t += comp(a[r], k) * Vm[3 * k + i];
+        Um[3 * r + i] = t * inv;
+      }
+    }
+    for (int k = 0; k < 81; ++k) A9[k] = 0.0;
+    // modes: (i, j, sign) with i == j the scaling modes
+    const int mi[9] = {0, 1, 2, 0, 0, 0, 0, 1, 1}, mj[9] = {0, 1, 2, 1, 1, 2, 2, 2, 2};
+    const double ms[9] = {0, 0, 0, 1, -1, 1, -1, 1, -1};
+    for (int m = 0; m < 9; ++m) {
+      const int i = mi[m], j = mj[m];
+      double lam;
+      if (i == j) lam = kv * (12.0 * sg[i] * sg[i] - 4.0);
+      else lam = 4.0 * kv * (sg[i] * sg[i] + ms[m] * sg[i] * sg[j] + sg[j] * sg[j] - 1.0);
+      if (!(lam > 0.0)) continue;
+      // W = U X V^T: W[r][c] = (U_ri V_cj + sign U_rj V_ci) / sqrt2 (or U_ri V_ci)
+      double w[9];
+      const double nrm = i == j ? 1.0 : 0.70710678118654752440;
       for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) {
-          double h;
-          if (i == j) {
-            h = 2.0 * comp(a[i], r) * comp(a[i], c) + (r == c ? G[i][i] - 1.0 : 0.0);
-            for (int k = 0; k < 3; ++k)
-              if (k != i) h += comp(a[k], r) * comp(a[k], c);
-          } else {
-            h = comp(a[j], r) * comp(a[i], c) + (r == c ? G[i][j] : 0.0);
-          }
-          A9[(3 * i + r) * 9 + 3 * j + c] = 4.0 * kv * h;
-        }
-  project_psd<9, double>(A9);
+        for (int c = 0; c < 3; ++c)
+          w[3 * r + c] = i == j ? Um[3 * r + i] * Vm[3 * c + i]
+                                : nrm * (Um[3 * r + i] * Vm[3 * c + j] + ms[m] * Um[3 * r + j] * Vm[3 * c + i]);
+      for (int r = 0; r < 9; ++r)
+        for (int c = 0; c < 9; ++c) A9[9 * r + c] += lam * w[r] * w[c];
+    }
+  }
   double* D = Db + 144 * b;
   for (int k = 0; k < 144; ++k) D[k] = 0.0;
   for (int c = 0; c < 3; ++c)
@@ -494,50 +737,57 @@ __global__ void k_gather(int nb, const uint8_t* is_static, const int* rowoff, co
   }
 }
 
-// block-Jacobi preconditioner: inverse of each dynamic diagonal block
+// block-Jacobi preconditioner: inverse of each dynamic diagonal block, one
+// warp per body (lanes share the Cholesky column updates, then each lane
+// solves for one column of the inverse)
 __global__ void k_precond(int nb, const uint8_t* is_static, const double* D, double* Pinv, DevStatus* st) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double L[8][12][13];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (b >= nb) return;
   double* Pi = Pinv + 144 * b;
   if (is_static[b]) {
-    for (int k = 0; k < 144; ++k) Pi[k] = 0.0;
+    for (int k = lane; k < 144; k += 32) Pi[k] = 0.0;
     return;
   }
-  double L[144];
-  for (int k = 0; k < 144; ++k) L[k] = D[144 * b + k];
+  double(*A)[13] = L[wib];
+  for (int k = lane; k < 144; k += 32) A[k / 12][k % 12] = D[144 * b + k];
+  __syncwarp();
   bool ok = true;
-  for (int j = 0; j < 12 && ok; ++j) {
-    double s = L[13 * j];
-    for (int k = 0; k < j; ++k) s -= L[12 * j + k] * L[12 * j + k];
-    if (!(s > 0.0)) {
+  for (int j = 0; j < 12; ++j) {
+    double t = 0.0;
+    if (lane >= j && lane < 12) {
+      t = A[lane][j];
+      for (int k = 0; k < j; ++k) t -= A[lane][k] * A[j][k];
+    }
+    const double tjj = __shfl_sync(kFull, t, j);
+    if (!(tjj > 0.0)) {
       ok = false;
       break;
     }
-    double l = sqrt(s);
-    L[13 * j] = l;
-    for (int i = j + 1; i < 12; ++i) {
-      double t = L[12 * i + j];
-      for (int k = 0; k < j; ++k) t -= L[12 * i + k] * L[12 * j + k];
-      L[12 * i + j] = t / l;
-    }
+    const double d = sqrt(tjj);
+    __syncwarp();
+    if (lane == j) A[j][j] = d;
+    else if (lane > j && lane < 12) A[lane][j] = t / d;
+    __syncwarp();
   }
   if (!ok) {
-    set_flag(st, ST_PCG_BREAKDOWN);
-    for (int k = 0; k < 144; ++k) Pi[k] = (k % 13 == 0) ? 1.0 / fabs(D[144 * b + k]) : 0.0;
+    if (lane == 0) set_flag(st, ST_PCG_BREAKDOWN);
+    for (int k = lane; k < 144; k += 32) Pi[k] = (k % 13 == 0) ? 1.0 / fabs(D[144 * b + k]) : 0.0;
     return;
   }
-  // columns of the inverse: solve L L^T x = e_c
-  for (int c = 0; c < 12; ++c) {
+  if (lane < 12) {
+    const int c = lane;
     double x[12];
     for (int i = 0; i < 12; ++i) {
       double s = (i == c) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) s -= L[12 * i + k] * x[k];
-      x[i] = s / L[13 * i];
+      for (int k = 0; k < i; ++k) s -= A[i][k] * x[k];
+      x[i] = s / A[i][i];
     }
     for (int i = 11; i >= 0; --i) {
       double s = x[i];
-      for (int k = i + 1; k < 12; ++k) s -= L[12 * k + i] * x[k];
-      x[i] = s / L[13 * i];
+      for (int k = i + 1; k < 12; ++k) s -= A[k][i] * x[k];
+      x[i] = s / A[i][i];
     }
     for (int i = 0; i < 12; ++i) Pi[12 * i + c] = x[i];
   }
@@ -762,9 +1012,8 @@ __global__ void k_pcg_start(const double* part, int n, DevStatus* st) {
 }
 
 // fixed-order sum: out = sum_i v[i * stride] for i < n
-__global__ void k_reduce(const double* v, long stride, const int* n_dev, long n_const, double* out) {
+__device__ void block_reduce_to(const double* v, long stride, long n, double* out) {
   __shared__ double red[1024];
-  const long n = n_dev ? *n_dev : n_const;
   double s = 0.0;
   for (long i = threadIdx.x; i < n; i += 1024) s += v[i * stride];
   red[threadIdx.x] = s;
@@ -774,6 +1023,19 @@ __global__ void k_reduce(const double* v, long stride, const int* n_dev, long n_
     __syncthreads();
   }
   if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void k_reduce(const double* v, long stride, const int* n_dev, long n_const, double* out) {
+  block_reduce_to(v, stride, n_dev ? *n_dev : n_const, out);
+}
+
+// the four energy components in one launch (block k reduces component k)
+__global__ void k_energies(const double* Eb, int nb, const double* bar, long bar_stride, const int* nbar,
+                           const double* fterm, const int* nfr, DevStatus* st) {
+  if (blockIdx.x == 0) block_reduce_to(Eb, 2, nb, &st->energy[1]);
+  else if (blockIdx.x == 1) block_reduce_to(Eb + 1, 2, nb, &st->energy[2]);
+  else if (blockIdx.x == 2) block_reduce_to(bar, bar_stride, *nbar, &st->energy[3]);
+  else block_reduce_to(fterm, kTermStride, *nfr, &st->energy[4]);
 }
 
 __global__ void k_energy_sum(DevStatus* st) {
@@ -791,8 +1053,10 @@ __global__ void k_max_step(int nv, const int* vbody, const uint8_t* is_static, c
   if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(&st->step_bits, (unsigned long long)__double_as_longlong(m));
 }
 
-__global__ void k_trial(int n, const double* q, const double* dq, double alpha, double* qtrial) {
+__global__ void k_trial(int n, const double* q, const double* dq, double alpha, const DevStatus* toi_from,
+                        double* qtrial) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (toi_from) alpha = __longlong_as_double((long long)toi_from->toi_bits);
   if (k < n) qtrial[k] = __dadd_rn(q[k], __dmul_rn(alpha, dq[k]));
 }
 
@@ -854,12 +1118,31 @@ void launch_scan(Scene& s, const int* cnt, int* off, const int* n_dev, int* tota
 }
 
 void launch_body_pairs(Scene& s) {
-  counted(s);
+  const double inv_h = 1.0 / s.cell_h;
+  const unsigned mask = (unsigned)s.hash_T - 1u;
+  const int nbk = blocks(s.nb, 128);
+  counted(s, 2);
   ProfScope pr(s, PF_ROWS);
-  k_rows<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.is_static.p, s.bbox.p, s.prm.dhat, s.fpairs.p, s.st,
-                                                        s.maxn, s.nbr.p, s.ncount.p, s.st);
+  k_hash_count<<<nbk, 128, 0, s.stream>>>(s.nb, s.bbox.p, s.prm.dhat, inv_h, s.hcount.p, s.large.p);
+  launch_scan(s, s.large.p, s.large_pos.p, nullptr, &s.st->nlarge, (long)s.nb, 0, &s.st->need_misc);
+  k_large_list<<<nbk, 128, 0, s.stream>>>(s.nb, s.large.p, s.large_pos.p, s.large_list.p);
+  launch_scan(s, s.hcount.p, s.hoff.p, nullptr, &s.st->nent, (long)s.entries.cap, ST_CAP_HASH, &s.st->need_misc);
+  cudaMemsetAsync(s.slot_cnt.p, 0, sizeof(int) * s.hash_T, s.stream);
+  k_hash_slots<<<nbk, 128, 0, s.stream>>>(s.nb, s.bbox.p, s.large.p, s.prm.dhat, inv_h, mask, s.slot_cnt.p,
+                                          s.slot_off.p, s.entries.p, (long)s.entries.cap, false);
+  counted(s, 3);
+  k_scan<<<1, 1024, 0, s.stream>>>(s.slot_cnt.p, s.slot_off.p, nullptr, s.hash_T, &s.st->pad2[0],
+                                   (long)s.entries.cap, ST_CAP_HASH, &s.st->need_misc, s.st);
+  cudaMemsetAsync(s.slot_cnt.p, 0, sizeof(int) * s.hash_T, s.stream);
+  k_hash_slots<<<nbk, 128, 0, s.stream>>>(s.nb, s.bbox.p, s.large.p, s.prm.dhat, inv_h, mask, s.slot_cnt.p,
+                                          s.slot_off.p, s.entries.p, (long)s.entries.cap, true);
+  counted(s, 3);
+  k_rows<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.is_static.p, s.bbox.p, s.prm.dhat, inv_h, mask,
+                                                        s.large.p, s.large_list.p, s.slot_off.p, s.entries.p,
+                                                        s.fpairs.p, s.st, s.maxn, s.nbr.p, s.ncount.p, s.st);
+  k_rows_large<<<64, 1024, 0, s.stream>>>(s.nb, s.is_static.p, s.bbox.p, s.prm.dhat, s.large_list.p, s.fpairs.p, s.st,
+                                          s.maxn, s.nbr.p, s.ncount.p, s.st);
   launch_scan(s, s.ncount.p, s.rowoff.p, nullptr, &s.st->np, (long)s.P.cap, ST_CAP_PAIRS, &s.st->need_pairs);
-  counted(s);
   k_rows_compact<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.nbr.p, s.ncount.p, s.rowoff.p, s.maxn, s.P.p,
                                                                 (long)s.P.cap);
 }
@@ -919,22 +1202,17 @@ void launch_gather(Scene& s) {
 
 void launch_precond(Scene& s) {
   counted(s);
-  k_precond<<<blocks(s.nb, 64), 64, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.Pinv.p, s.st);
+  k_precond<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.Pinv.p, s.st);
 }
 
 // energies of the last evaluation into st->energy: bodies, barrier terms or
 // per-body-pair barrier energies (energy-only pass), friction terms
 void launch_energy_total(Scene& s, bool from_terms) {
-  counted(s);
-  k_reduce<<<1, 1024, 0, s.stream>>>(s.Eb.p, 2, nullptr, s.nb, &s.st->energy[1]);
-  counted(s);
-  k_reduce<<<1, 1024, 0, s.stream>>>(s.Eb.p + 1, 2, nullptr, s.nb, &s.st->energy[2]);
-  counted(s);
-  if (from_terms) k_reduce<<<1, 1024, 0, s.stream>>>(s.term.p, kTermStride, &s.st->nact, 0, &s.st->energy[3]);
-  else k_reduce<<<1, 1024, 0, s.stream>>>(s.Epair.p, 1, &s.st->np, 0, &s.st->energy[3]);
-  counted(s);
-  k_reduce<<<1, 1024, 0, s.stream>>>(s.fterm.p, kTermStride, &s.st->nfr, 0, &s.st->energy[4]);
-  counted(s);
+  counted(s, 2);
+  if (from_terms)
+    k_energies<<<4, 1024, 0, s.stream>>>(s.Eb.p, s.nb, s.term.p, kTermStride, &s.st->nact, s.fterm.p, &s.st->nfr, s.st);
+  else
+    k_energies<<<4, 1024, 0, s.stream>>>(s.Eb.p, s.nb, s.Epair.p, 1, &s.st->np, s.fterm.p, &s.st->nfr, s.st);
   k_energy_sum<<<1, 1, 0, s.stream>>>(s.st);
 }
 
@@ -951,7 +1229,7 @@ int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_
   // product written once, the pair list once
   const double spmv_bytes = 8.0 * 144.0 * (s.nb + (double)s.last_np) + 2.0 * 8.0 * 12.0 * s.nb + 8.0 * s.last_np;
   int it = 0;
-  const int chunk = 16;
+  int chunk = 2;
   while (true) {
     for (int k = 0; k < chunk; ++k) {
       counted(s);
@@ -974,6 +1252,7 @@ int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_
     cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
     cudaStreamSynchronize(s.stream);
     if (s.st_host->scal[6] != 0.0 || it >= max_iter) break;
+    chunk = std::min(2 * chunk, 16);
   }
   double rr = s.st_host->scal[2], rr0 = s.st_host->scal[3];
   *rel_res = rr0 > 0 ? sqrt(rr / rr0) : 0.0;
@@ -988,9 +1267,10 @@ void launch_max_step(Scene& s) {
   k_max_step<<<blocks(s.nv, 256), 256, 0, s.stream>>>(s.nv, s.vbody.p, s.is_static.p, s.dx.p, s.st);
 }
 
-void launch_trial(Scene& s, double alpha) {
+void launch_trial(Scene& s, double alpha, bool alpha_from_ccd) {
   counted(s);
-  k_trial<<<blocks(12L * s.nb, 256), 256, 0, s.stream>>>(12 * s.nb, s.q.p, s.dq.p, alpha, s.qtrial.p);
+  k_trial<<<blocks(12L * s.nb, 256), 256, 0, s.stream>>>(12 * s.nb, s.q.p, s.dq.p, alpha,
+                                                          alpha_from_ccd ? s.st : nullptr, s.qtrial.p);
 }
 
 void launch_finish_step(Scene& s) {
