@@ -134,6 +134,7 @@ typedef struct {
   long launches;
   double total_ms;     /* sum of per-launch durations (CUDA events on the scene's stream) */
   double bytes;        /* algorithmic bytes of those launches (0 if not defined) */
+  double flops;        /* algorithmic FP64 operations of those launches (0 if not defined) */
 } abd_kernel_profile;
 
 /* Fill *p with the defaults used by the benchmarks: dt 0.01, d-hat 1e-3,

@@ -91,6 +91,8 @@ def lib():
             "orc_candidates": (l, [vp, vp, vp, i, vp, vp, vp, l]),
             "orc_energy_grad_hess": (i, [vp, vp, vp, vp, i]), "orc_energy": (d, [vp, vp]),
             "orc_hess_nblocks": (l, [vp]), "orc_hess_copy": (None, [vp, vp, vp, vp]),
+            "orc_active_pairs": (l, [vp, vp, vp, vp, vp, vp, vp, l]),
+            "orc_grad_rows": (i, [vp, vp, i, vp, vp]),
             "orc_pairs_count": (l, [vp, i]), "orc_pairs_copy": (None, [vp, i, vp, vp, vp, vp, vp]),
             "orc_solve": (i, [vp, vp, vp, vp]), "orc_ccd_toi": (i, [vp, vp, vp, vp]),
             "orc_step": (i, [vp, i, vp]),
@@ -299,6 +301,26 @@ class Oracle:
     def energy(self, q):
         q = _f64(q, 12 * self.nb)
         return lib().orc_energy(self.ctx, _p(q))
+
+    def active_pairs(self, q):
+        """active pairs at q by canonical distance (no derivatives)"""
+        q = _f64(q, 12 * self.nb)
+        L = lib()
+        n = L.orc_active_pairs(self.ctx, _p(q), None, None, None, None, None, 0)
+        m = max(n, 1)
+        kind, pi, pj, ty = (np.zeros(m, np.int32) for _ in range(4))
+        d2 = np.zeros(m)
+        L.orc_active_pairs(self.ctx, _p(q), _p(kind), _p(pi), _p(pj), _p(ty), _p(d2), n)
+        return dict(kind=kind[:n], i=pi[:n], j=pj[:n], type=ty[:n], val=d2[:n])
+
+    def grad_rows(self, q, bodies):
+        """gradient rows of the selected bodies (body terms + every contact
+        term touching them)"""
+        q = _f64(q, 12 * self.nb)
+        sel = np.ascontiguousarray(bodies, dtype=np.int32)
+        out = np.zeros((len(sel), 12))
+        st = lib().orc_grad_rows(self.ctx, _p(q), len(sel), _p(sel), _p(out))
+        return st, out
 
     def hessian(self):
         L = lib()

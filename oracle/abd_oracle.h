@@ -102,6 +102,8 @@ long orc_candidates(const orc_ctx* c, const double* x0, const double* x1, int br
  * the candidate / active pair lists in the context for the getters below. */
 int orc_energy_grad_hess(orc_ctx* c, const double* q, double* E, double* g, int project);
 double orc_energy(orc_ctx* c, const double* q);
+long orc_active_pairs(orc_ctx* c, const double* q, int* kind, int* pi, int* pj, int* type, double* d2, long cap);
+int orc_grad_rows(orc_ctx* c, const double* q, int nsel, const int* sel, double* grows);
 long orc_hess_nblocks(const orc_ctx* c);
 void orc_hess_copy(const orc_ctx* c, double* diag, int* bpairs, double* blocks);
 long orc_pairs_count(const orc_ctx* c, int which); /* 0 candidates, 1 active, 2 friction */

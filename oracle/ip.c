@@ -848,6 +848,24 @@ static void build_pattern(orc_ctx* c, const plist* act) {
   c->blocks = (double*)calloc(144 * (u ? u : 1), sizeof(double));
 }
 
+/* mu lambda f0(|P (sum gamma_v x_v - r)|), value only */
+static double friction_value(const double x[12], const fpair* F, double eps) {
+  double u[3], t = 0.0;
+  for (int cc = 0; cc < 3; ++cc) {
+    u[cc] = -F->r[cc];
+    for (int m = 0; m < 4; ++m) u[cc] += F->gamma[m] * x[3 * m + cc];
+    t += F->n[cc] * u[cc];
+  }
+  double y2 = 0.0;
+  for (int cc = 0; cc < 3; ++cc) {
+    double w = u[cc] - t * F->n[cc];
+    y2 += w * w;
+  }
+  double y = sqrt(y2);
+  double f0 = y >= eps ? y : -y * y2 / (3.0 * eps * eps) + y2 / eps + eps / 3.0;
+  return F->mu_lambda * f0;
+}
+
 /* energy (and optionally gradient / Hessian) over the pairs of `cand` */
 static int evaluate(orc_ctx* c, const double* q, const plist* cand, double* E, double* g, int hess, int project,
                     plist* act_out) {
@@ -884,12 +902,16 @@ static int evaluate(orc_ctx* c, const double* q, const plist* cand, double* E, d
   for (long k = 0; k < act.n; ++k) {
     int v[4];
     double xx[12], e;
+    if (act.d2[k] == 0.0) status = ORC_ERR_INTERSECT;
+    if (!g && !hess) { /* value only: kappa B(d) */
+      Eb += s->kappa * orc_barrier(sqrt(act.d2[k]), s->dhat);
+      continue;
+    }
     pair_verts(c, act.kind[k], act.i[k], act.j[k], v);
     gather12(x, v, xx);
-    if (act.d2[k] == 0.0) status = ORC_ERR_INTERSECT;
     orc_pair_barrier(act.kind[k], xx, s->dhat, s->kappa, project, &e, gx, Hx);
     Eb += e;
-    if (g || hess) add_pair_blocks(c, v, gx, Hx, g, hess);
+    add_pair_blocks(c, v, gx, Hx, g, hess);
   }
   double eps = s->eps_v * s->dt;
   for (long k = 0; k < c->nfr; ++k) {
@@ -898,8 +920,12 @@ static int evaluate(orc_ctx* c, const double* q, const plist* cand, double* E, d
     double xx[12];
     pair_verts(c, F->kind, F->i, F->j, v);
     gather12(x, v, xx);
+    if (!g && !hess) {
+      Ef += friction_value(xx, F, eps);
+      continue;
+    }
     Ef += orc_friction_pair(xx, F->gamma, F->n, F->r, F->mu_lambda, eps, gx, Hx);
-    if (g || hess) add_pair_blocks(c, v, gx, Hx, g, hess);
+    add_pair_blocks(c, v, gx, Hx, g, hess);
   }
   E[1] = Ein;
   E[2] = Eo;
@@ -938,6 +964,85 @@ double orc_energy(orc_ctx* c, const double* q) {
   evaluate(c, q, &L, E, NULL, 0, 0, NULL);
   pl_free(&L);
   return E[0];
+}
+
+/* active pairs (canonical d^2 < dhat^2) at q, no derivatives */
+long orc_active_pairs(orc_ctx* c, const double* q, int* kind, int* pi, int* pj, int* type, double* d2, long cap) {
+  const orc_scene* s = &c->sc;
+  double* x = (double*)malloc(sizeof(double) * 3 * (s->nv + 1));
+  orc_vertices(c, q, x);
+  plist L = {0};
+  collect(c, x, NULL, 0, &L);
+  long n = 0;
+  for (long k = 0; k < L.n; ++k) {
+    int v[4], ty;
+    double xx[12];
+    pair_verts(c, L.kind[k], L.i[k], L.j[k], v);
+    gather12(x, v, xx);
+    double dd = orc_pair_dist2(L.kind[k], xx, &ty);
+    if (!(dd < s->dhat * s->dhat)) continue;
+    if (n < cap) {
+      kind[n] = L.kind[k];
+      pi[n] = L.i[k];
+      pj[n] = L.j[k];
+      type[n] = ty;
+      d2[n] = dd;
+    }
+    ++n;
+  }
+  pl_free(&L);
+  free(x);
+  return n;
+}
+
+/* gradient rows (12 each) of the selected bodies at q: body terms, every
+ * active barrier term and every friction term touching them */
+int orc_grad_rows(orc_ctx* c, const double* q, int nsel, const int* sel, double* grows) {
+  const orc_scene* s = &c->sc;
+  double* g = (double*)calloc(12 * (size_t)s->nb, sizeof(double));
+  unsigned char* want = (unsigned char*)calloc(s->nb, 1);
+  for (int k = 0; k < nsel; ++k) want[sel[k]] = 1;
+  double* x = (double*)malloc(sizeof(double) * 3 * (s->nv + 1));
+  orc_vertices(c, q, x);
+  for (int k = 0; k < nsel; ++k) {
+    int b = sel[k];
+    if (s->is_static[b]) continue;
+    double eo;
+    body_terms(c, b, q + 12 * b, g + 12 * b, NULL, 0, &eo);
+  }
+  plist L = {0};
+  collect(c, x, NULL, 0, &L);
+  double gx[12], Hx[144], e;
+  int status = ORC_OK;
+  for (long k = 0; k < L.n; ++k) {
+    int v[4], ty;
+    double xx[12];
+    pair_verts(c, L.kind[k], L.i[k], L.j[k], v);
+    if (!(want[c->vbody[v[0]]] || want[c->vbody[v[3]]])) continue;
+    gather12(x, v, xx);
+    double dd = orc_pair_dist2(L.kind[k], xx, &ty);
+    if (!(dd < s->dhat * s->dhat)) continue;
+    if (dd == 0.0) status = ORC_ERR_INTERSECT;
+    orc_pair_barrier(L.kind[k], xx, s->dhat, s->kappa, 0, &e, gx, Hx);
+    add_pair_blocks(c, v, gx, Hx, g, 0);
+  }
+  double eps = s->eps_v * s->dt;
+  for (long k = 0; k < c->nfr; ++k) {
+    const fpair* F = &c->fr[k];
+    int v[4];
+    double xx[12];
+    pair_verts(c, F->kind, F->i, F->j, v);
+    if (!(want[c->vbody[v[0]]] || want[c->vbody[v[3]]])) continue;
+    gather12(x, v, xx);
+    orc_friction_pair(xx, F->gamma, F->n, F->r, F->mu_lambda, eps, gx, Hx);
+    add_pair_blocks(c, v, gx, Hx, g, 0);
+  }
+  for (int k = 0; k < nsel; ++k) memcpy(grows + 12 * k, g + 12 * sel[k], 12 * sizeof(double));
+  pl_free(&L);
+  free(x);
+  free(g);
+  free(want);
+  return status;
 }
 
 long orc_hess_nblocks(const orc_ctx* c) { return c->nblk; }

@@ -61,7 +61,8 @@ class abd_step_stats(C.Structure):
 
 
 class abd_kernel_profile(C.Structure):
-    _fields_ = [("name", C.c_char_p), ("launches", C.c_long), ("total_ms", C.c_double), ("bytes", C.c_double)]
+    _fields_ = [("name", C.c_char_p), ("launches", C.c_long), ("total_ms", C.c_double), ("bytes", C.c_double),
+                ("flops", C.c_double)]
 
 
 def _as_dict(st):
@@ -358,5 +359,6 @@ class AbdScene:
         arr = (abd_kernel_profile * 16)()
         n = C.c_int()
         self._check(abd_get_profile(self.h, arr, 16, C.byref(n)))
-        return {arr[k].name.decode(): dict(launches=arr[k].launches, total_ms=arr[k].total_ms, bytes=arr[k].bytes)
+        return {arr[k].name.decode(): dict(launches=arr[k].launches, total_ms=arr[k].total_ms, bytes=arr[k].bytes,
+                                           flops=arr[k].flops)
                 for k in range(min(n.value, 16))}

@@ -876,6 +876,8 @@ abd_status abd_set_profiling(abd_scene* S, int on) {
   s.prof.on = on != 0;
   s.prof.used = 0;
   for (auto& sl : s.prof.slot) sl = Prof::Slot();
+  read_status(s);
+  for (int m = 0; m < 4; ++m) s.prof.bar_terms0[m] = s.st_host->bar_terms[m];
   return check_cuda(s);
 }
 
@@ -883,6 +885,9 @@ abd_status abd_get_profile(abd_scene* S, abd_kernel_profile* out, int cap, int* 
   if (!S) return ABD_ERR_INVALID_ARG;
   Scene& s = S->s;
   cudaStreamSynchronize(s.stream);
+  read_status(s);
+  double bar_flops = 0.0;
+  for (int m = 1; m < 4; ++m) bar_flops += kBarrierFlops[m] * (double)(s.st_host->bar_terms[m] - s.prof.bar_terms0[m]);
   if (n) *n = PF_COUNT;
   for (int k = 0; k < PF_COUNT && k < cap && out; ++k) {
     double ms = 0.0;
@@ -895,6 +900,7 @@ abd_status abd_get_profile(abd_scene* S, abd_kernel_profile* out, int cap, int* 
     out[k].launches = s.prof.slot[k].launches;
     out[k].total_ms = ms;
     out[k].bytes = s.prof.slot[k].bytes;
+    out[k].flops = k == PF_BARRIER ? bar_flops : 0.0;
   }
   return check_cuda(s);
 }

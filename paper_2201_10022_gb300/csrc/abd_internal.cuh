@@ -44,6 +44,7 @@ struct DevStatus {
   unsigned long long toi_bits;  // min time of impact (bits of a positive double)
   unsigned long long step_bits; // max vertex step length (bits of a positive double)
   unsigned long long n_cand;    // candidates of the last enumeration
+  unsigned long long bar_terms[4];  // barrier terms evaluated, by reduced dimension m = 1, 2, 3
   double scal[8];               // PCG scalars: 0 rz, 1 pAp, 2 rr, 3 rr0, 4 alpha, 5 beta, 6 done
   double energy[8];             // 0 total, 1 inertia, 2 ortho, 3 barrier, 4 friction
 };
@@ -83,6 +84,7 @@ struct Prof {
     long launches = 0;
     double bytes = 0;  // algorithmic bytes of the recorded launches
   } slot[PF_COUNT];
+  unsigned long long bar_terms0[4] = {0, 0, 0, 0};  // counters when profiling started
 };
 
 // ---- scene ------------------------------------------------------------------
@@ -159,6 +161,11 @@ struct Scene {
 };
 
 constexpr int kTermStride = 91;
+
+// algorithmic FP64 operations of one barrier term by reduced dimension m:
+// derivatives, congruences with the Gram factor, Newton-Schulz step, basis
+// change, one FP64 Jacobi sweep, clamp and expansion to 12x12
+constexpr double kBarrierFlops[4] = {0.0, 850.0, 5800.0, 18400.0};
 
 // launch bookkeeping: count every kernel; with profiling on, bracket the
 // launches of a slot with events

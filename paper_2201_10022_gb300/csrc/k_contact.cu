@@ -284,7 +284,8 @@ struct BarrierShared {
 __global__ void __launch_bounds__(32 * kBarWarps) k_barrier(const DevStatus* __restrict__ cst, const int* aoff,
                                                             const int4* act, const int* tri, const int* edge,
                                                             const double4* x, double dhat, double kappa, int maxc,
-                                                            int project, long cap, double* term, int4* termv) {
+                                                            int project, long cap, double* term, int4* termv,
+                                                            DevStatus* st) {
   __shared__ BarrierShared sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / kGroupLanes, gl = lane - grp * kGroupLanes;
@@ -395,7 +396,7 @@ __global__ void __launch_bounds__(32 * kBarWarps) k_barrier(const DevStatus* __r
         for (int pp = 0; pp < n3 - 1; ++pp)
           for (int qq = pp + 1; qq < n3; ++qq) {
             const float apq = K32[pp * n3 + qq];
-            if (apq == 0.f) continue;
+            if (fabsf(apq) <= 1e-7f * sqrtf(fabsf(K32[pp * n3 + pp] * K32[qq * n3 + qq]))) continue;
             const float theta = (K32[qq * n3 + qq] - K32[pp * n3 + pp]) / (2.f * apq);
             const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
             const float c = rsqrtf(t * t + 1.f), sn = t * c;
@@ -489,7 +490,8 @@ __global__ void __launch_bounds__(32 * kBarWarps) k_barrier(const DevStatus* __r
         for (int pp = 0; pp < n3 - 1; ++pp)
           for (int qq = pp + 1; qq < n3; ++qq) {
             const double apq = K[pp * n3 + qq];
-            if (apq == 0.0) continue;
+            // negligible against its diagonal pair: no rotation
+            if (fabs(apq) <= 1e-16 * sqrt(fabs(K[pp * n3 + pp] * K[qq * n3 + qq]))) continue;
             const double theta = (K[qq * n3 + qq] - K[pp * n3 + pp]) / (2.0 * apq);
             const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
             const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
@@ -565,6 +567,7 @@ __global__ void __launch_bounds__(32 * kBarWarps) k_barrier(const DevStatus* __r
     if (gl == 0) {
       T[0] = sh.E[warp][grp];
       termv[f] = make_int4(v[0], v[1], v[2], v[3]);
+      atomicAdd(&st->bar_terms[m], 1ull);
     }
     __syncwarp(gmask);
   }
@@ -746,7 +749,7 @@ void launch_barrier(Scene& s, int project, long cap) {
   counted(s);
   ProfScope ps(s, PF_BARRIER);
   k_barrier<<<152 * 8, 32 * kBarWarps, 0, s.stream>>>(s.st, s.aoff.p, s.act.p, s.tri.p, s.edge.p, s.x.p, s.prm.dhat,
-                                          s.prm.kappa, s.maxc, project, cap, s.term.p, s.termv.p);
+                                          s.prm.kappa, s.maxc, project, cap, s.term.p, s.termv.p, s.st);
 }
 
 void launch_friction_lag(Scene& s) {

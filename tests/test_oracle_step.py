@@ -151,3 +151,22 @@ def test_friction_decelerates_sliding_cube_by_mu_g():
     # the lagged normal forces carry the weight: sum mu lambda = mu m g dt^2
     mass = o.mass_matrix(1)[0, 0]
     assert o.pairs(2)["val"].sum() == pytest.approx(mu * mass * g * dt * dt, rel=5e-3)
+
+
+def test_sampled_entry_points_agree_with_full_evaluation():
+    """active set by distance alone, the value-only energy and gradient rows
+    of selected bodies equal the full evaluation's"""
+    s = scenes.packed_cubes(nx=3, ny=2, nz=2)
+    o = O.Oracle(s)
+    q = s.q0.reshape(-1)
+    st, E, g = o.energy_grad_hess(q, project=False)
+    act_full = o.pairs(1)
+    act = o.active_pairs(q)
+    key = lambda d: set(zip(d["kind"].tolist(), d["i"].tolist(), d["j"].tolist(), d["type"].tolist(),
+                            d["val"].tolist()))
+    assert len(act["kind"]) > 50 and key(act) == key(act_full)
+    assert o.energy(q) == pytest.approx(E[0], rel=1e-12)
+    sel = np.array([1, 4, 7, 11])
+    st, rows = o.grad_rows(q, sel)
+    assert st == 0
+    np.testing.assert_allclose(rows, g[sel], rtol=1e-12, atol=1e-12 * np.abs(g).max())
