@@ -84,7 +84,8 @@ def lib():
             "orc_d2_pt_plane": (d, [vp, vp, vp, vp]), "orc_d2_ee_line": (d, [vp, vp, vp, vp]),
             "orc_pt_dist2": (d, [vp, vp, vp, vp, vp]), "orc_ee_dist2": (d, [vp, vp, vp, vp, vp]),
             "orc_pair_dist2": (d, [i, vp, vp]), "orc_barrier": (d, [d, d]),
-            "orc_pair_barrier": (i, [i, vp, d, d, i, vp, vp, vp]),
+            "orc_pair_barrier": (i, [i, vp, d, d, d, i, vp, vp, vp]),
+            "orc_ee_cross2": (d, [vp]), "orc_ee_mollifier": (d, [d, d, vp, vp]),
             "orc_sym_eig": (None, [i, vp, vp, vp]), "orc_project_psd": (None, [i, vp]),
             "orc_accd": (i, [i, vp, vp, d, d, i, vp]),
             "orc_friction_pair": (d, [vp, vp, vp, vp, d, d, vp, vp]),
@@ -140,13 +141,25 @@ def barrier(d, dhat):
     return lib().orc_barrier(float(d), float(dhat))
 
 
-def pair_barrier(kind, x12, dhat, kappa, project=True):
+def pair_barrier(kind, x12, dhat, kappa, project=True, eps_x=0.0):
+    """kappa B(d) of one pair (times the edge-edge mollifier when eps_x > 0)"""
     x = _f64(x12, 12)
     E = np.zeros(1)
     g = np.zeros(12)
     H = np.zeros(144)
-    act = lib().orc_pair_barrier(kind, _p(x), dhat, kappa, int(project), _p(E), _p(g), _p(H))
+    act = lib().orc_pair_barrier(kind, _p(x), dhat, kappa, float(eps_x), int(project), _p(E), _p(g), _p(H))
     return bool(act), E[0], g, H.reshape(12, 12)
+
+
+def ee_cross2(x12):
+    return lib().orc_ee_cross2(_p(_f64(x12, 12)))
+
+
+def ee_mollifier(c, eps_x):
+    dm = C.c_double()
+    d2m = C.c_double()
+    m = lib().orc_ee_mollifier(float(c), float(eps_x), C.byref(dm), C.byref(d2m))
+    return m, dm.value, d2m.value
 
 
 def ortho(q12, kappa, vol):

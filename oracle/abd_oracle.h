@@ -81,8 +81,10 @@ double orc_pt_dist2(const double x0[3], const double x1[3], const double x2[3], 
 double orc_ee_dist2(const double x0[3], const double x1[3], const double x2[3], const double x3[3], int* type);
 double orc_pair_dist2(int kind, const double x[12], int* type);
 double orc_barrier(double d, double dhat);
-int orc_pair_barrier(int kind, const double x[12], double dhat, double kappa, int project, double* E,
-                     double g[12], double H[144]);
+double orc_ee_cross2(const double x[12]); /* |(x1 - x0) x (x3 - x2)|^2, canonical order */
+double orc_ee_mollifier(double c, double eps_x, double* dm, double* d2m);
+int orc_pair_barrier(int kind, const double x[12], double dhat, double kappa, double eps_x, int project,
+                     double* E, double g[12], double H[144]);
 void orc_sym_eig(int n, const double* A, double* w, double* V);
 void orc_project_psd(int n, double* A);
 int orc_accd(int kind, const double x[12], const double dx[12], double s, double tmax, int max_iter, double* toi);

@@ -275,12 +275,41 @@ double orc_barrier(double d, double dhat) {
   return -(t * t) * log(d / dhat);
 }
 
+/* ------------------------------------------------------------------------ */
+/* near-parallel edge-edge mollifier (IPC, Li et al. 2020): with              */
+/* c = |e0 x e1|^2 and eps_x = 1e-3 |rest e0|^2 |rest e1|^2, the edge-edge    */
+/* barrier is multiplied by m(c) = -c^2/eps_x^2 + 2c/eps_x for c < eps_x and  */
+/* by 1 otherwise, so that it fades out (C1) as the two edges turn parallel,  */
+/* where the line-line distance loses its conditioning.                       */
+/* ------------------------------------------------------------------------ */
+
+double orc_ee_cross2(const double x[12]) {
+  double e0[3], e1[3], n[3];
+  vsub(e0, x + 3, x);
+  vsub(e1, x + 9, x + 6);
+  vcross(n, e0, e1);
+  return vdot(n, n);
+}
+
+double orc_ee_mollifier(double c, double eps_x, double* dm, double* d2m) {
+  if (!(c < eps_x)) {
+    if (dm) *dm = 0.0;
+    if (d2m) *d2m = 0.0;
+    return 1.0;
+  }
+  double r = c / eps_x;
+  if (dm) *dm = (2.0 - 2.0 * r) / eps_x;
+  if (d2m) *d2m = -2.0 / (eps_x * eps_x);
+  return (2.0 - r) * r;
+}
+
 /* kappa * B(d(x)) with gradient and Hessian over the 12 coordinates, taken
  * by jets through d = sqrt(d^2) of the pair's distance type; the Hessian is
- * projected to the PSD cone when project != 0.  Returns 0 for an inactive
- * pair (d^2 >= dhat^2), 1 otherwise. */
-int orc_pair_barrier(int kind, const double x[12], double dhat, double kappa, int project, double* E,
-                     double g[12], double H[144]) {
+ * projected to the PSD cone when project != 0.  An edge-edge pair with
+ * eps_x > 0 and |e0 x e1|^2 < eps_x carries the mollifier factor m above.
+ * Returns 0 for an inactive pair (d^2 >= dhat^2), 1 otherwise. */
+int orc_pair_barrier(int kind, const double x[12], double dhat, double kappa, double eps_x, int project,
+                     double* E, double g[12], double H[144]) {
   int type;
   double d2 = orc_pair_dist2(kind, x, &type);
   *E = 0.0;
@@ -296,6 +325,24 @@ int orc_pair_barrier(int kind, const double x[12], double dhat, double kappa, in
   jet_log(&l, &l);
   jet_mul(&b, &t2, &l);
   jet_scale(&b, &b, -kappa);
+  if (kind == ORC_EE && eps_x > 0.0) {
+    double c = orc_ee_cross2(x);
+    if (c < eps_x) {
+      /* m(c(x)) as a jet: c = |(x1 - x0) x (x3 - x2)|^2 */
+      static jet3 v[4], e0, e1, n;
+      static jet cj, mj, bm;
+      for (int k = 0; k < 4; ++k) jet3_var(&v[k], x + 3 * k, 3 * k);
+      jet3_sub(&e0, &v[1], &v[0]);
+      jet3_sub(&e1, &v[3], &v[2]);
+      jet3_cross(&n, &e0, &e1);
+      jet3_dot(&cj, &n, &n);
+      double dm, d2m;
+      double mv = orc_ee_mollifier(cj.v, eps_x, &dm, &d2m);
+      jet_chain(&mj, &cj, mv, dm, d2m);
+      jet_mul(&bm, &b, &mj);
+      b = bm;
+    }
+  }
   *E = b.v;
   memcpy(g, b.g, 12 * sizeof(double));
   memcpy(H, b.h, 144 * sizeof(double));

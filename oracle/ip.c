@@ -79,6 +79,7 @@ struct orc_ctx {
   unsigned char* is_static;
   int *vbeg, *vend, *tbeg, *tend, *ebeg, *eend;
   double *vol, *m1, *S, *M; /* per body */
+  double* l2e;               /* squared rest length of every edge */
   double *qt, *qdot, *qtilde;
   fpair* fr;
   long nfr;
@@ -193,6 +194,13 @@ orc_ctx* orc_create(const orc_scene* s) {
     orc_body_moments(c, b, &c->vol[b], &c->m1[3 * b], &c->S[9 * b]);
     orc_mass_matrix(c, b, &c->M[144 * b]);
   }
+  c->l2e = (double*)calloc(s->ne ? s->ne : 1, sizeof(double));
+  for (int e = 0; e < s->ne; ++e) {
+    const double* a = c->xbar + 3 * c->edge[2 * e];
+    const double* b = c->xbar + 3 * c->edge[2 * e + 1];
+    double d0 = b[0] - a[0], d1 = b[1] - a[1], d2 = b[2] - a[2];
+    c->l2e[e] = fma(d2, d2, fma(d1, d1, d0 * d0));
+  }
   c->qt = (double*)calloc(12 * nb, sizeof(double));
   c->qdot = (double*)calloc(12 * nb, sizeof(double));
   c->qtilde = (double*)calloc(12 * nb, sizeof(double));
@@ -203,6 +211,7 @@ orc_ctx* orc_create(const orc_scene* s) {
 void orc_destroy(orc_ctx* c) {
   if (!c) return;
   free(c->xbar);
+  free(c->l2e);
   free(c->tri);
   free(c->edge);
   free(c->vbody);
@@ -548,6 +557,20 @@ static void pair_verts(const orc_ctx* c, int kind, int i, int j, int v[4]) {
   }
 }
 
+/* mollifier threshold of an edge-edge pair from the rest lengths (0 for a
+ * point-triangle pair): eps_x = 1e-3 |rest e_i|^2 |rest e_j|^2 */
+static double pair_eps_x(const orc_ctx* c, int kind, int i, int j) {
+  if (kind != ORC_EE) return 0.0;
+  return (1e-3 * c->l2e[i]) * c->l2e[j];
+}
+
+/* mollifier value of a pair at its vertex positions (1 unless a mollified
+ * edge-edge pair) */
+static double pair_mollifier(const orc_ctx* c, int kind, int i, int j, const double xx[12]) {
+  if (kind != ORC_EE) return 1.0;
+  return orc_ee_mollifier(orc_ee_cross2(xx), pair_eps_x(c, kind, i, j), NULL, NULL);
+}
+
 static void gather12(const double* x, const int v[4], double out[12]) {
   for (int k = 0; k < 4; ++k)
     for (int cc = 0; cc < 3; ++cc) out[3 * k + cc] = x[3 * v[k] + cc];
@@ -667,7 +690,8 @@ static void lag_friction(orc_ctx* c) {
     double d2 = orc_pair_dist2(L.kind[k], xx, &type);
     if (!(d2 < s->dhat * s->dhat)) continue;
     double d = sqrt(d2);
-    double lam = -s->kappa * barrier_d1(d, s->dhat);
+    /* normal force magnitude; a mollified edge-edge pair carries m(c) */
+    double lam = -s->kappa * barrier_d1(d, s->dhat) * pair_mollifier(c, L.kind[k], L.i[k], L.j[k], xx);
     if (!(lam > 0.0)) continue;
     fpair* F = &c->fr[c->nfr++];
     F->kind = L.kind[k];
@@ -903,13 +927,14 @@ static int evaluate(orc_ctx* c, const double* q, const plist* cand, double* E, d
     int v[4];
     double xx[12], e;
     if (act.d2[k] == 0.0) status = ORC_ERR_INTERSECT;
-    if (!g && !hess) { /* value only: kappa B(d) */
-      Eb += s->kappa * orc_barrier(sqrt(act.d2[k]), s->dhat);
-      continue;
-    }
     pair_verts(c, act.kind[k], act.i[k], act.j[k], v);
     gather12(x, v, xx);
-    orc_pair_barrier(act.kind[k], xx, s->dhat, s->kappa, project, &e, gx, Hx);
+    if (!g && !hess) { /* value only: kappa B(d) m(c) */
+      Eb += s->kappa * orc_barrier(sqrt(act.d2[k]), s->dhat) * pair_mollifier(c, act.kind[k], act.i[k], act.j[k], xx);
+      continue;
+    }
+    orc_pair_barrier(act.kind[k], xx, s->dhat, s->kappa, pair_eps_x(c, act.kind[k], act.i[k], act.j[k]), project, &e,
+                     gx, Hx);
     Eb += e;
     add_pair_blocks(c, v, gx, Hx, g, hess);
   }
@@ -1023,7 +1048,7 @@ int orc_grad_rows(orc_ctx* c, const double* q, int nsel, const int* sel, double*
     double dd = orc_pair_dist2(L.kind[k], xx, &ty);
     if (!(dd < s->dhat * s->dhat)) continue;
     if (dd == 0.0) status = ORC_ERR_INTERSECT;
-    orc_pair_barrier(L.kind[k], xx, s->dhat, s->kappa, 0, &e, gx, Hx);
+    orc_pair_barrier(L.kind[k], xx, s->dhat, s->kappa, pair_eps_x(c, L.kind[k], L.i[k], L.j[k]), 0, &e, gx, Hx);
     add_pair_blocks(c, v, gx, Hx, g, 0);
   }
   double eps = s->eps_v * s->dt;

@@ -446,6 +446,7 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
     grow(s, s.vbody, nv);
     grow(s, s.tri, 3L * nt + 1);
     grow(s, s.edge, 2L * ne + 1);
+    grow(s, s.l2e, ne + 1L);
     grow(s, s.vbeg, nb + 1);
     grow(s, s.tbeg, nb + 1);
     grow(s, s.ebeg, nb + 1);
@@ -526,6 +527,7 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
   *s.st_host = z;
   cudaMemcpyAsync(s.st, s.st_host, sizeof(DevStatus), cudaMemcpyHostToDevice, s.stream);
   launch_mass_moments(s);
+  launch_edge_rest(s);
   s.ndyn = 0;
   for (int b = 0; b < nb; ++b) s.ndyn += d->is_static[b] ? 0 : 1;
   // Newton tolerance (the paper states none): IPC's rule |dx|_inf <= 1e-5 l dt,
@@ -577,6 +579,7 @@ void abd_destroy(abd_scene* S) {
   Scene& s = S->s;
   if (s.stream || s.st) cudaStreamSynchronize(s.stream);
   release(s, s.xbar);
+  release(s, s.l2e);
   release(s, s.vbody);
   release(s, s.tri);
   release(s, s.edge);

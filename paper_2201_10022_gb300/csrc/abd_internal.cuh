@@ -98,6 +98,7 @@ struct Scene {
 
   // topology and body constants
   Buf<double4> xbar;   // nv (w unused)
+  Buf<double> l2e;     // ne: squared rest length of every edge (edge-edge mollifier)
   Buf<int> vbody, tri, edge, vbeg, tbeg, ebeg;
   Buf<uint8_t> is_static;
   Buf<double> mass10;  // nb*10: rho*vol, rho*m1[3], rho*S[xx,xy,xz,yy,yz,zz]
@@ -196,6 +197,7 @@ constexpr int kBlkStride = 3 * 144 + 24 + 2;
 
 // ---- launchers (k_system.cu) -----------------------------------------------
 void launch_mass_moments(Scene& s);
+void launch_edge_rest(Scene& s);
 void launch_predictor(Scene& s);
 void launch_transform(Scene& s, const double* q, double4* x);
 void launch_transform_dq(Scene& s, const double* dq);   // dx = J dq, x1 = x + dx

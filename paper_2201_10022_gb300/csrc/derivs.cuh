@@ -72,22 +72,6 @@ ABD_HD void jacobi_eig(T* A, T* V) {
   }
 }
 
-// in-place PSD projection of a symmetric N x N matrix
-template <int N, typename T>
-ABD_HD void project_psd(T* A) {
-  T V[N * N];
-  jacobi_eig<N, T>(A, V);
-  T w[N];
-  for (int i = 0; i < N; ++i) w[i] = A[i * N + i] > T(0) ? A[i * N + i] : T(0);
-  for (int i = 0; i < N; ++i)
-    for (int j = i; j < N; ++j) {
-      T s = 0;
-      for (int k = 0; k < N; ++k) s += V[i * N + k] * w[k] * V[j * N + k];
-      A[i * N + j] = s;
-      A[j * N + i] = s;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // reduced coordinates of each distance type
 // ---------------------------------------------------------------------------
@@ -271,95 +255,67 @@ ABD_HD double reduced_dist2(const Reduced& R, double* gs, double* Hs) {
 }
 
 // ---------------------------------------------------------------------------
-// barrier term: energy, vertex gradient g12 and projected Hessian (packed)
+// mollified edge-edge barrier kappa B(d) m(c) in the line-line coordinates
+// y = (w, e0, e1) = (x2 - x0, x1 - x0, x3 - x2), the reduced coordinates of
+// edge-edge type 8 whatever the pair's distance type: every type's difference
+// vectors are integer combinations of y (a column c of C gives coefficients
+// (c2 + c3, c1, c3)), and c = |e0 x e1|^2 depends on e0 and e1 only.
+// Writes the gradient g9 and the (unprojected) Hessian H9 (9x9 row-major) of
+// the product and returns its value.
 // ---------------------------------------------------------------------------
-ABD_HD double barrier_term(int kind, int type, const v3* x, double dhat, double kappa, int project, double* g12,
-                           double* H78) {
-  Reduced R;
-  reduce(kind, type, x, R);
-  const int m = R.m, n3 = 3 * m;
-  double gs[9], Hr[81];
-  double s = reduced_dist2(R, gs, Hr);
-  double d = sqrt(s);
+ABD_HD double mollified_ee_term(int type, const v3* x, double dhat, double kappa, double c, double eps, double* g9,
+                                double* H9) {
+  Reduced Rt;
+  reduce(1, type, x, Rt);
+  const int mt = Rt.m, nt = 3 * mt;
+  double gs[9], Hs[81];
+  const double s = reduced_dist2(Rt, gs, Hs);
+  const double d = sqrt(s);
   double B, B1, B2;
   barrier_derivs(d, dhat, B, B1, B2);
-  // grad B = B'/(2d) grad s; hess B = (B''/(4s) - B'/(4 d s)) grad s grad s^T + B'/(2d) hess s
-  double cg = kappa * B1 / (2.0 * d);
-  double ca = kappa * (B2 / (4.0 * s) - B1 / (4.0 * d * s));
-  for (int i = 0; i < n3; ++i)
-    for (int j = 0; j < n3; ++j) Hr[i * n3 + j] = ca * gs[i] * gs[j] + cg * Hr[i * n3 + j];
-  double gr[9];
-  for (int i = 0; i < n3; ++i) gr[i] = cg * gs[i];
-  if (project) {
-    // Gram G = C^T C = R^T R (R upper), K = (R (x) I) Hr (R^T (x) I)
-    double G[3][3], Rm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, Ri[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    for (int a = 0; a < m; ++a)
-      for (int b = 0; b < m; ++b) {
-        double t = 0.0;
-        for (int k = 0; k < 4; ++k) t += R.C[k][a] * R.C[k][b];
-        G[a][b] = t;
-      }
-    for (int j = 0; j < m; ++j) {  // Cholesky G = L L^T, Rm = L^T
-      double t = G[j][j];
-      for (int k = 0; k < j; ++k) t -= Rm[k][j] * Rm[k][j];
-      Rm[j][j] = sqrt(t);
-      for (int i = j + 1; i < m; ++i) {
-        double u = G[j][i];
-        for (int k = 0; k < j; ++k) u -= Rm[k][j] * Rm[k][i];
-        Rm[j][i] = u / Rm[j][j];
-      }
-    }
-    for (int i = m - 1; i >= 0; --i) {  // inverse of the upper factor
-      Ri[i][i] = 1.0 / Rm[i][i];
-      for (int j = i + 1; j < m; ++j) {
-        double t = 0.0;
-        for (int k = i + 1; k <= j; ++k) t += Rm[i][k] * Ri[k][j];
-        Ri[i][j] = -t / Rm[i][i];
-      }
-    }
-    double K[81];
-    for (int a = 0; a < m; ++a)
-      for (int b = 0; b < m; ++b)
-        for (int i = 0; i < 3; ++i)
-          for (int j = 0; j < 3; ++j) {
-            double t = 0.0;
-            for (int c = 0; c < m; ++c)
-              for (int e = 0; e < m; ++e) t += Rm[a][c] * Hr[(3 * c + i) * n3 + 3 * e + j] * Rm[b][e];
-            K[(3 * a + i) * n3 + 3 * b + j] = t;
-          }
-    if (m == 3) project_psd<9, double>(K);
-    else if (m == 2) project_psd<6, double>(K);
-    else project_psd<3, double>(K);
-    for (int a = 0; a < m; ++a)
-      for (int b = 0; b < m; ++b)
-        for (int i = 0; i < 3; ++i)
-          for (int j = 0; j < 3; ++j) {
-            double t = 0.0;
-            for (int c = 0; c < m; ++c)
-              for (int e = 0; e < m; ++e) t += Ri[a][c] * K[(3 * c + i) * n3 + 3 * e + j] * Ri[b][e];
-            Hr[(3 * a + i) * n3 + 3 * b + j] = t;
-          }
+  const double cg = kappa * B1 / (2.0 * d);
+  const double ca = kappa * (B2 / (4.0 * s) - B1 / (4.0 * d * s));
+  double A[3][3];
+  for (int w = 0; w < mt; ++w) {
+    A[w][0] = Rt.C[2][w] + Rt.C[3][w];
+    A[w][1] = Rt.C[1][w];
+    A[w][2] = Rt.C[3][w];
   }
-  // expand to vertex space: g12[k] = sum_v C[k][v] gr[v]; H12 = T Hr T^T
-  for (int k = 0; k < 4; ++k)
+  // kappa B and its derivatives pulled back to y
+  double gb[9];
+  for (int J = 0; J < 3; ++J)
     for (int i = 0; i < 3; ++i) {
       double t = 0.0;
-      for (int v = 0; v < m; ++v) t += R.C[k][v] * gr[3 * v + i];
-      g12[3 * k + i] = t;
+      for (int w = 0; w < mt; ++w) t += A[w][J] * gs[3 * w + i];
+      gb[3 * J + i] = cg * t;
     }
-  for (int k = 0; k < 4; ++k)
-    for (int l = k; l < 4; ++l)
+  for (int J = 0; J < 3; ++J)
+    for (int L = 0; L < 3; ++L)
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-          if (k == l && j < i) continue;
           double t = 0.0;
-          for (int v = 0; v < m; ++v) {
-            if (R.C[k][v] == 0.0) continue;
-            for (int w = 0; w < m; ++w) t += R.C[k][v] * R.C[l][w] * Hr[(3 * v + i) * n3 + 3 * w + j];
+          for (int w = 0; w < mt; ++w) {
+            if (A[w][J] == 0.0) continue;
+            for (int v = 0; v < mt; ++v)
+              t += A[w][J] * A[v][L] * (ca * gs[3 * w + i] * gs[3 * v + j] + cg * Hs[(3 * w + i) * nt + 3 * v + j]);
           }
-          H78[up12(3 * k + i, 3 * l + j)] = t;
+          H9[(3 * J + i) * 9 + 3 * L + j] = t;
         }
-  return kappa * B;
+  // c = |e0 x e1|^2 (Lagrange identity) in slots e0 = 1, e1 = 2
+  double gc[9], Hc[81];
+  for (int i = 0; i < 9; ++i) gc[i] = 0.0;
+  for (int i = 0; i < 81; ++i) Hc[i] = 0.0;
+  lagrange_derivs(x[1] - x[0], x[3] - x[2], 1, 2, 9, 1.0, 1.0, gc, Hc);
+  double dm, d2m;
+  const double mv = ee_mollifier(c, eps, dm, d2m);
+  const double Eb = kappa * B;
+  // product rule: H = m Hb + Eb (m'' gc gc^T + m' Hc) + m' (gc gb^T + gb gc^T)
+  for (int a = 0; a < 9; ++a)
+    for (int b = 0; b < 9; ++b)
+      H9[a * 9 + b] = mv * H9[a * 9 + b] + Eb * (d2m * gc[a] * gc[b] + dm * Hc[a * 9 + b]) +
+                      dm * (gc[a] * gb[b] + gb[a] * gc[b]);
+  for (int a = 0; a < 9; ++a) g9[a] = mv * gb[a] + Eb * dm * gc[a];
+  return Eb * mv;
 }
 
 // ---------------------------------------------------------------------------

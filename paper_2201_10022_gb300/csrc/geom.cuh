@@ -244,4 +244,29 @@ ABD_HD void barrier_derivs(double d, double dhat, double& B, double& B1, double&
   B2 = -2.0 * l - 4.0 * t / d + (t * t) / (d * d);
 }
 
+// ---------------------------------------------------------------------------
+// near-parallel edge-edge mollifier (IPC, Li et al. 2020): an edge-edge
+// barrier is multiplied by m(c) = (2 - c/eps) c/eps while c = |e0 x e1|^2 is
+// below eps = 1e-3 |rest e0|^2 |rest e1|^2, so that it fades out (C1) as the
+// edges turn parallel and the line-line distance loses its conditioning.
+// c and eps are formed in canonical order: the choice of branch matches the
+// CPU reference bit for bit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double ee_cross2(const v3* x) {
+  v3 n = ccross(csub(x[1], x[0]), csub(x[3], x[2]));
+  return cdot(n, n);
+}
+__device__ __forceinline__ double ee_eps(double l2i, double l2j) { return __dmul_rn(__dmul_rn(1e-3, l2i), l2j); }
+// m(c) with its first and second derivatives (1, 0, 0 at and above eps)
+ABD_HD double ee_mollifier(double c, double eps, double& dm, double& d2m) {
+  if (!(c < eps)) {
+    dm = d2m = 0.0;
+    return 1.0;
+  }
+  double r = c / eps;
+  dm = (2.0 - 2.0 * r) / eps;
+  d2m = -2.0 / (eps * eps);
+  return (2.0 - r) * r;
+}
+
 }  // namespace abd

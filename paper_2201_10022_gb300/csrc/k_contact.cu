@@ -283,9 +283,9 @@ struct BarrierShared {
 
 __global__ void __launch_bounds__(32 * kBarWarps) k_barrier(const DevStatus* __restrict__ cst, const int* aoff,
                                                             const int4* act, const int* tri, const int* edge,
-                                                            const double4* x, double dhat, double kappa, int maxc,
-                                                            int project, long cap, double* term, int4* termv,
-                                                            DevStatus* st) {
+                                                            const double4* x, const double* l2e, double dhat,
+                                                            double kappa, int maxc, int project, long cap,
+                                                            double* term, int4* termv, DevStatus* st) {
   __shared__ BarrierShared sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / kGroupLanes, gl = lane - grp * kGroupLanes;
@@ -305,10 +305,20 @@ __global__ void __launch_bounds__(32 * kBarWarps) k_barrier(const DevStatus* __r
     pair_vertices(kind, i, r.y, tri, edge, v);
     v3 xs[4];
     for (int m = 0; m < 4; ++m) xs[m] = mk(x[v[m]]);
+    // a mollified edge-edge pair is worked in the line-line coordinates
+    double c = 0.0, eps = 0.0;
+    bool moll = false;
+    if (kind == 1) {
+      c = ee_cross2(xs);
+      eps = ee_eps(l2e[i], l2e[r.y]);
+      moll = c < eps;
+    }
     Reduced R;
-    reduce(kind, r.z, xs, R);
+    reduce(kind, moll ? 8 : r.z, xs, R);
     const int m = R.m, n3 = 3 * m;
-    if (gl == 0) {
+    if (gl == 0 && moll) {
+      sh.E[warp][grp] = mollified_ee_term(r.z, xs, dhat, kappa, c, eps, sh.g[warp][grp], H);
+    } else if (gl == 0) {
       double gs[9], Hs[81];
       const double s = reduced_dist2(R, gs, Hs);
       const double d = sqrt(s);
@@ -630,7 +640,8 @@ __device__ void closest_weights(int kind, int type, const v3* x, double* g) {
 // (lambda = -kappa B'(d), closest-point weights, normal, lagged offset)
 __global__ void k_friction_lag(DevStatus* cst, const int2* P, const int* aoff, const int4* act,
                                const double* act_d2, const int* tri, const int* edge, const int* vbody,
-                               const double4* x, double dhat, double kappa, double mu, int maxc, FricRec* fr) {
+                               const double4* x, const double* l2e, double dhat, double kappa, double mu, int maxc,
+                               FricRec* fr) {
   const int np = cst->np, nact = cst->nact;
   if (blockIdx.x == 0 && threadIdx.x == 0) cst->nfr = nact;
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nact; f += gridDim.x * blockDim.x) {
@@ -645,7 +656,13 @@ __global__ void k_friction_lag(DevStatus* cst, const int2* P, const int* aoff, c
     double d = sqrt(act_d2[(size_t)p * maxc + k]);
     double B, B1, B2;
     barrier_derivs(d, dhat, B, B1, B2);
-    R.mu_lambda = mu * (-kappa * B1);
+    // normal force magnitude; a mollified edge-edge pair carries m(c)
+    double mv = 1.0;
+    if (kind == 1) {
+      double dm, d2m;
+      mv = ee_mollifier(ee_cross2(xs), ee_eps(l2e[i], l2e[r.y]), dm, d2m);
+    }
+    R.mu_lambda = mu * (-kappa * B1 * mv);
     closest_weights(kind, r.z, xs, R.gam);
     v3 w = (R.gam[0] * xs[0] + R.gam[1] * xs[1]) + (R.gam[2] * xs[2] + R.gam[3] * xs[3]);
     double nn = sqrt(dot(w, w));
@@ -688,8 +705,8 @@ __global__ void k_friction_eval(const DevStatus* __restrict__ cst, const FricRec
 // energy of the barrier over the stored candidates at positions x: one value
 // per body pair, summed in slot order (energy-only pass of the line search)
 __global__ void k_pair_energy(const DevStatus* __restrict__ cst, const int2* cand, const int* ccount,
-                              const int* tri, const int* edge, const double4* x, double dhat, double kappa, int maxc,
-                              double* Ep, DevStatus* st) {
+                              const int* tri, const int* edge, const double4* x, const double* l2e, double dhat,
+                              double kappa, int maxc, double* Ep, DevStatus* st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int np = cst->np;
@@ -710,7 +727,12 @@ __global__ void k_pair_energy(const DevStatus* __restrict__ cst, const int2* can
         if (d2 == 0.0) set_flag(st, ST_INTERSECT);
         double B, B1, B2;
         barrier_derivs(sqrt(d2), dhat, B, B1, B2);
-        e += kappa * B;
+        double mv = 1.0;
+        if (kind == 1) {
+          double dm, d2m;
+          mv = ee_mollifier(ee_cross2(xs), ee_eps(l2e[i], l2e[c.y]), dm, d2m);
+        }
+        e += kappa * B * mv;
       }
     }
     for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(kFull, e, o);
@@ -748,14 +770,15 @@ void launch_active(Scene& s, const double4* x) {
 void launch_barrier(Scene& s, int project, long cap) {
   counted(s);
   ProfScope ps(s, PF_BARRIER);
-  k_barrier<<<152 * 8, 32 * kBarWarps, 0, s.stream>>>(s.st, s.aoff.p, s.act.p, s.tri.p, s.edge.p, s.x.p, s.prm.dhat,
-                                          s.prm.kappa, s.maxc, project, cap, s.term.p, s.termv.p, s.st);
+  k_barrier<<<152 * 8, 32 * kBarWarps, 0, s.stream>>>(s.st, s.aoff.p, s.act.p, s.tri.p, s.edge.p, s.x.p, s.l2e.p,
+                                          s.prm.dhat, s.prm.kappa, s.maxc, project, cap, s.term.p, s.termv.p, s.st);
 }
 
 void launch_friction_lag(Scene& s) {
   counted(s);
   k_friction_lag<<<152 * 4, 128, 0, s.stream>>>(s.st, s.P.p, s.aoff.p, s.act.p, s.act_d2.p, s.tri.p, s.edge.p,
-                                               s.vbody.p, s.x.p, s.prm.dhat, s.prm.kappa, s.prm.mu, s.maxc, s.fric.p);
+                                               s.vbody.p, s.x.p, s.l2e.p, s.prm.dhat, s.prm.kappa, s.prm.mu, s.maxc,
+                                               s.fric.p);
 }
 
 void launch_friction_eval(Scene& s, const double4* x, bool derivs) {
@@ -768,8 +791,8 @@ void launch_friction_eval(Scene& s, const double4* x, bool derivs) {
 void launch_pair_energy(Scene& s, const double4* x) {
   int grid = grid_for(s.last_np > 0 ? s.last_np : s.nb, 8, 152 * 16);
   counted(s);
-  k_pair_energy<<<grid, 256, 0, s.stream>>>(s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.prm.dhat,
-                                            s.prm.kappa, s.maxc, s.Epair.p, s.st);
+  k_pair_energy<<<grid, 256, 0, s.stream>>>(s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.l2e.p,
+                                            s.prm.dhat, s.prm.kappa, s.maxc, s.Epair.p, s.st);
 }
 
 }  // namespace abd

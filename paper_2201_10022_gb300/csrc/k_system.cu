@@ -31,6 +31,15 @@ __device__ __forceinline__ void inv_dof(int i, int& u, int& c) {
 // Sec. 3.1: volume, first and second moments by signed tetrahedra (0, v0, v1,
 // v2) of the closed surface; M = rho [[vol I, I (x) m1^T], [I (x) m1, I (x) S]]
 // ---------------------------------------------------------------------------
+// squared rest length of every edge, canonical order (edge-edge mollifier
+// threshold eps = 1e-3 |rest e_i|^2 |rest e_j|^2)
+__global__ void k_edge_rest(int ne, const int* edge, const double4* xbar, double* l2e) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+    v3 d = csub(mk(xbar[edge[2 * e + 1]]), mk(xbar[edge[2 * e]]));
+    l2e[e] = cdot(d, d);
+  }
+}
+
 __global__ void k_mass_moments(int nb, const int* tbeg, const int* tri, const double4* xbar, const double* density,
                                const uint8_t* is_static, double* mass10, double* vol) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -737,59 +746,74 @@ __global__ void k_gather(int nb, const uint8_t* is_static, const int* rowoff, co
   }
 }
 
-// block-Jacobi preconditioner: inverse of each dynamic diagonal block, one
-// warp per body (lanes share the Cholesky column updates, then each lane
-// solves for one column of the inverse)
-__global__ void k_precond(int nb, const uint8_t* is_static, const double* D, double* Pinv, DevStatus* st) {
-  __shared__ double L[8][12][13];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (b >= nb) return;
-  double* Pi = Pinv + 144 * b;
-  if (is_static[b]) {
-    for (int k = lane; k < 144; k += 32) Pi[k] = 0.0;
-    return;
+// block-Jacobi preconditioner: inverse of each dynamic diagonal block.
+// Twelve threads per body (one matrix row each), sixteen bodies per block:
+// the blocks are staged through shared memory with coalesced loads and
+// stores, factored by a left-looking Cholesky (one column per step, the
+// reciprocal of its diagonal formed once), and thread c then solves
+// L L^T x = e_c for column c of the inverse with the triangular loops fully
+// unrolled so the solution stays in registers.
+constexpr int kPreBodies = 16, kPreThreads = 12 * kPreBodies;
+
+__global__ void __launch_bounds__(kPreThreads) k_precond(int nb, const uint8_t* is_static, const double* D,
+                                                         double* Pinv, DevStatus* st) {
+  __shared__ double A[kPreBodies][12][13];
+  __shared__ double rd[kPreBodies][12];
+  __shared__ int bad[kPreBodies];
+  const int bl = threadIdx.x / 12, r = threadIdx.x - 12 * (threadIdx.x / 12);
+  const int b = blockIdx.x * kPreBodies + bl;
+  const long base = (long)blockIdx.x * kPreBodies * 144, lim = 144L * nb;
+  for (int k = threadIdx.x; k < kPreBodies * 144; k += kPreThreads) {
+    const int bb = k / 144, e = k - 144 * (k / 144);
+    A[bb][e / 12][e % 12] = base + k < lim ? D[base + k] : 0.0;
   }
-  double(*A)[13] = L[wib];
-  for (int k = lane; k < 144; k += 32) A[k / 12][k % 12] = D[144 * b + k];
-  __syncwarp();
-  bool ok = true;
+  if (r == 0) bad[bl] = 0;
+  __syncthreads();
   for (int j = 0; j < 12; ++j) {
     double t = 0.0;
-    if (lane >= j && lane < 12) {
-      t = A[lane][j];
-      for (int k = 0; k < j; ++k) t -= A[lane][k] * A[j][k];
+    if (r >= j) {
+      t = A[bl][r][j];
+      for (int k = 0; k < j; ++k) t -= A[bl][r][k] * A[bl][j][k];
     }
-    const double tjj = __shfl_sync(kFull, t, j);
-    if (!(tjj > 0.0)) {
-      ok = false;
-      break;
+    if (r == j) {
+      if (!(t > 0.0)) bad[bl] = 1;  // not positive definite: diagonal fallback below
+      const double d = sqrt(t);
+      A[bl][j][j] = d;
+      rd[bl][j] = 1.0 / d;
     }
-    const double d = sqrt(tjj);
-    __syncwarp();
-    if (lane == j) A[j][j] = d;
-    else if (lane > j && lane < 12) A[lane][j] = t / d;
-    __syncwarp();
+    __syncthreads();
+    if (r > j) A[bl][r][j] = t * rd[bl][j];
+    __syncthreads();
   }
-  if (!ok) {
-    if (lane == 0) set_flag(st, ST_PCG_BREAKDOWN);
-    for (int k = lane; k < 144; k += 32) Pi[k] = (k % 13 == 0) ? 1.0 / fabs(D[144 * b + k]) : 0.0;
-    return;
+  // column c = r of (L L^T)^-1: forward L y = e_c (y_i = 0 for i < c), then
+  // back L^T x = y
+  const int c = r;
+  double y[12], x[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    double t = (i == c) ? 1.0 : 0.0;
+#pragma unroll
+    for (int k = 0; k < i; ++k) t -= A[bl][i][k] * y[k];
+    y[i] = (i < c) ? 0.0 : t * rd[bl][i];
   }
-  if (lane < 12) {
-    const int c = lane;
-    double x[12];
-    for (int i = 0; i < 12; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) s -= A[i][k] * x[k];
-      x[i] = s / A[i][i];
-    }
-    for (int i = 11; i >= 0; --i) {
-      double s = x[i];
-      for (int k = i + 1; k < 12; ++k) s -= A[k][i] * x[k];
-      x[i] = s / A[i][i];
-    }
-    for (int i = 0; i < 12; ++i) Pi[12 * i + c] = x[i];
+#pragma unroll
+  for (int i = 11; i >= 0; --i) {
+    double t = y[i];
+#pragma unroll
+    for (int k = i + 1; k < 12; ++k) t -= A[bl][k][i] * x[k];
+    x[i] = t * rd[bl][i];
+  }
+  __syncthreads();  // every solve has read L
+  const bool live = b < nb && !is_static[b];
+  const bool fallback = live && bad[bl];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) A[bl][i][c] = !live ? 0.0 : (fallback ? 0.0 : x[i]);
+  if (fallback) A[bl][c][c] = 1.0 / fabs(D[144L * b + 13 * c]);
+  if (fallback && c == 0) set_flag(st, ST_PCG_BREAKDOWN);
+  __syncthreads();
+  for (int k = threadIdx.x; k < kPreBodies * 144; k += kPreThreads) {
+    const int bb = k / 144, e = k - 144 * (k / 144);
+    if (base + k < lim) Pinv[base + k] = A[bb][e / 12][e % 12];
   }
 }
 
@@ -1088,6 +1112,12 @@ void launch_mass_moments(Scene& s) {
                                                                  s.vol.p);
 }
 
+void launch_edge_rest(Scene& s) {
+  if (s.ne == 0) return;
+  counted(s);
+  k_edge_rest<<<blocks(s.ne, 256), 256, 0, s.stream>>>(s.ne, s.edge.p, s.xbar.p, s.l2e.p);
+}
+
 void launch_predictor(Scene& s) {
   counted(s);
   k_predictor<<<blocks(s.nb, 128), 128, 0, s.stream>>>(s.nb, s.is_static.p, s.qt.p, s.qdot.p, s.prm.dt,
@@ -1202,7 +1232,7 @@ void launch_gather(Scene& s) {
 
 void launch_precond(Scene& s) {
   counted(s);
-  k_precond<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.Pinv.p, s.st);
+  k_precond<<<blocks(s.nb, kPreBodies), kPreThreads, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.Pinv.p, s.st);
 }
 
 // energies of the last evaluation into st->energy: bodies, barrier terms or

@@ -203,3 +203,111 @@ def test_projected_barrier_hessian_is_psd():
             act, E, g, H = O.pair_barrier(kind, x, DHAT, 1e8, True)
             w = np.linalg.eigvalsh(H)
             assert w.min() >= -1e-12 * np.abs(w).max()
+
+
+# --- near-parallel edge-edge mollifier ---------------------------------------
+
+def _ee_family(theta, mode, d=0.5 * DHAT, L0=1.0, L1=0.8):
+    """edge 0 along x at z=0, edge 1 at height d turned by theta about z.
+    mode "line": edge 1 crosses edge 0 at mid-span (line-line type);
+    "pe": edge 1 starts above the middle of edge 0, off to one side, so that
+    the lines' crossing lies behind it (its end against edge 0);
+    "pp": the same just past the end of edge 0 (end against end).  Each
+    configuration sits strictly inside its distance type's region."""
+    c, s = np.cos(theta), np.sin(theta)
+    x0, x1 = np.array([0.0, 0.0, 0.0]), np.array([L0, 0.0, 0.0])
+    u = L1 * np.array([c, s, 0.0])
+    if mode == "line":
+        x2 = np.array([0.5 * L0, 0.0, d]) - 0.5 * u
+    elif mode == "pe":
+        x2 = np.array([0.5 * L0, 0.3 * DHAT, d])
+    else:
+        x2 = np.array([L0 + 0.3 * DHAT, 0.3 * DHAT, d])
+    return np.concatenate([x0, x1, x2, x2 + u])
+
+
+def test_mollifier_polynomial_joins():
+    """m is 0 with slope 2/eps at c = 0 and joins 1 with zero slope at eps (C1)"""
+    for eps in (1e-3, 0.37, 5.0):
+        m0, dm0, _ = O.ee_mollifier(0.0, eps)
+        assert m0 == 0.0 and dm0 == pytest.approx(2.0 / eps, rel=1e-15)
+        m1, dm1, _ = O.ee_mollifier(eps * (1 - 1e-12), eps)
+        assert m1 == pytest.approx(1.0, abs=1e-11) and abs(dm1) < 1e-10 / eps
+        assert O.ee_mollifier(eps, eps)[:2] == (1.0, 0.0)
+        # monotone increasing on [0, eps): a fade-in, never above 1
+        cs = np.linspace(0, eps, 50, endpoint=False)
+        ms = [O.ee_mollifier(c, eps)[0] for c in cs]
+        assert np.all(np.diff(ms) > 0) and max(ms) < 1.0
+        # second derivative by differences of the first
+        c = 0.3 * eps
+        h = 1e-6 * eps
+        fd = (O.ee_mollifier(c + h, eps)[1] - O.ee_mollifier(c - h, eps)[1]) / (2 * h)
+        assert fd == pytest.approx(O.ee_mollifier(c, eps)[2], rel=1e-7)
+
+
+def test_ee_cross2_against_numpy():
+    rng = np.random.default_rng(31)
+    for _ in range(20):
+        x = rng.normal(size=12)
+        n = np.cross(x[3:6] - x[0:3], x[9:12] - x[6:9])
+        assert O.ee_cross2(x) == pytest.approx(n @ n, rel=1e-13)
+
+
+def test_parallel_edges_carry_no_barrier():
+    """exactly parallel edges within d-hat: c = 0, so energy and gradient vanish
+    (the contact is left to the point-triangle pairs)"""
+    eps = 1e-3 * 1.0 * 0.64
+    for mode in ("line", "pe", "pp"):  # parallel: the type is a tie-break
+        x = _ee_family(0.0, mode)
+        d2, ty = O.pair_dist2(1, x)
+        assert d2 < DHAT ** 2
+        act, E, g, H = O.pair_barrier(1, x, DHAT, 1e8, False, eps_x=eps)
+        assert act and E == 0.0 and np.all(g == 0.0)
+        assert np.linalg.eigvalsh(H).min() >= -1e-9 * np.abs(H).max()
+        act0, E0, _, _ = O.pair_barrier(1, x, DHAT, 1e8, False)
+        assert E0 > 0.0
+
+
+@pytest.mark.parametrize("mode,want", [("line", 8), ("pe", 6), ("pp", 2)])
+def test_mollified_barrier_finite_differences(mode, want):
+    eps = 1e-3 * 1.0 * 0.64
+    for theta in (2e-4, 1e-3, 2.5e-2):
+        x = _ee_family(theta, mode)
+        c = O.ee_cross2(x)
+        assert c < eps and O.pair_dist2(1, x)[1] == want
+        act, E, g, H = O.pair_barrier(1, x, DHAT, 1.0, False, eps_x=eps)
+        act0, E0, g0, _ = O.pair_barrier(1, x, DHAT, 1.0, False)
+        assert act and E == pytest.approx(E0 * O.ee_mollifier(c, eps)[0], rel=1e-12)
+        h = 1e-9
+        f = lambda y: O.pair_barrier(1, y, DHAT, 1.0, False, eps_x=eps)[1]
+        np.testing.assert_allclose(g, _fd(f, x, h), rtol=1e-4, atol=1e-5 * np.abs(g).max())
+        gf = lambda y: O.pair_barrier(1, y, DHAT, 1.0, False, eps_x=eps)[2]
+        Hfd = np.array([(gf(x + h * np.eye(12)[i]) - gf(x - h * np.eye(12)[i])) / (2 * h) for i in range(12)])
+        np.testing.assert_allclose(H, Hfd, rtol=1e-4, atol=1e-5 * np.abs(H).max())
+        # the product-rule terms matter: the mollified gradient is not m * g0
+        assert np.abs(g - O.ee_mollifier(c, eps)[0] * g0).max() > 1e-6 * np.abs(g).max()
+
+
+def test_mollified_barrier_is_c1_across_threshold():
+    """energy and its derivative along the rotation are continuous where
+    |e0 x e1|^2 crosses eps_x, and nothing changes above it"""
+    eps = 1e-3 * 1.0 * 0.64
+    theta_c = np.arcsin(np.sqrt(eps / 0.64))  # |e0 x e1|^2 = 0.64 sin^2 theta
+    def E_and_slope(theta):
+        x = _ee_family(theta, "line")
+        dx = (_ee_family(theta + 1e-7, "line") - _ee_family(theta - 1e-7, "line")) / 2e-7
+        _, E, g, _ = O.pair_barrier(1, x, DHAT, 1.0, False, eps_x=eps)
+        return E, g @ dx
+    jumps = []
+    for delta in (1e-4, 1e-5, 1e-6):
+        Em, sm = E_and_slope(theta_c - delta)
+        Ep, sp = E_and_slope(theta_c + delta)
+        jumps.append((abs(Ep - Em), abs(sp - sm)))
+    # a jump in the value or the slope would not shrink with delta; for a C1
+    # join both go to zero (the slope linearly, the value quadratically)
+    for (e1, s1), (e2, s2) in zip(jumps, jumps[1:]):
+        assert s2 <= 0.15 * s1 and e2 <= 0.02 * e1 + 1e-22
+    x = _ee_family(2 * theta_c, "line")
+    a = O.pair_barrier(1, x, DHAT, 1.0, True, eps_x=eps)
+    b = O.pair_barrier(1, x, DHAT, 1.0, True)
+    assert a[1] == b[1] and np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])

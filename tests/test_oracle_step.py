@@ -170,3 +170,39 @@ def test_sampled_entry_points_agree_with_full_evaluation():
     st, rows = o.grad_rows(q, sel)
     assert st == 0
     np.testing.assert_allclose(rows, g[sel], rtol=1e-12, atol=1e-12 * np.abs(g).max())
+
+
+def test_scene_barrier_uses_rest_length_mollifier():
+    """In a scene the edge-edge terms carry the mollifier with eps_x from the
+    edges' rest lengths: the barrier energy of a packed pair of cubes (tiny
+    rotations, so every edge-edge pair is near-parallel) equals the sum of the
+    per-pair terms with eps_x = 1e-3 |rest e_i|^2 |rest e_j|^2 computed here,
+    and stays so after the bodies are scaled (eps_x is not recomputed)."""
+    s = scenes.packed_cubes(nx=2, ny=1, nz=1)
+    o = O.Oracle(s)
+    q = s.q0.reshape(-1).copy()
+    rest_l2 = {}
+    for e, (a, b) in enumerate(s.edge):
+        d = s.xbar[b] - s.xbar[a]
+        rest_l2[e] = d @ d
+    for scale in (1.0, 1.0 + 2e-4):
+        qs = q.copy()
+        for b in range(s.nb):
+            if not s.is_static[b]:
+                qs[12 * b + 3:12 * b + 12] *= scale  # A -> scale * A (about each body's origin)
+        st, E, g = o.energy_grad_hess(qs)
+        assert st == 0 and E[3] > 0
+        P = o.pairs(1)
+        x = o.vertices(qs).reshape(-1, 3)
+        total, n_moll = 0.0, 0
+        for kind, i, j in zip(P["kind"], P["i"], P["j"]):
+            if kind == 0:
+                v = [i, *s.tri[j]]
+                eps = 0.0
+            else:
+                v = [*s.edge[i], *s.edge[j]]
+                eps = 1e-3 * rest_l2[i] * rest_l2[j]
+                n_moll += O.ee_cross2(x[v].ravel()) < eps
+            total += O.pair_barrier(kind, x[v].ravel(), s.params["dhat"], s.params["kappa"], False, eps_x=eps)[1]
+        assert n_moll > 0
+        assert E[3] == pytest.approx(total, rel=1e-12)
