@@ -206,10 +206,11 @@ def run_abd(args, rank, world):
     act = sum(st["active_evaluated"] for st in stats)
     launches = sum(st["kernel_launches"] for st in stats)
     pk, src = peaks()
-    # roofline of the kernel class that took the most device time
-    top = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
-    name, p = top
+    # roofline of the kernel class with an algorithmic flop or byte model
+    # that took the most device time
+    modelled = [kv for kv in prof.items() if kv[1]["flops"] > 0 or kv[1]["bytes"] > 0]
     roof = None
+    name, p = max(modelled or prof.items(), key=lambda kv: kv[1]["total_ms"])
     if p["launches"] and p["total_ms"] > 0:
         t_s = p["total_ms"] * 1e-3
         if p["flops"] > 0:

@@ -81,6 +81,9 @@ void size_pair_buffers(Scene& s, size_t pcap) {
 void size_term_buffers(Scene& s, size_t tcap) {
   grow(s, s.term, tcap * kTermStride);
   grow(s, s.termv, tcap);
+  grow(s, s.tmeta, tcap);
+  grow(s, s.teps, tcap);
+  grow(s, s.tlist, 3 * tcap);
   grow(s, s.fric, tcap);
   grow(s, s.fterm, tcap * kTermStride);
   grow(s, s.ftermv, tcap);
@@ -605,6 +608,9 @@ void abd_destroy(abd_scene* S) {
   release(s, s.cand);
   release(s, s.act);
   release(s, s.termv);
+  release(s, s.tmeta);
+  release(s, s.teps);
+  release(s, s.tlist);
   release(s, s.ftermv);
   release(s, s.fric);
   for (cudaEvent_t e : s.prof.pool) cudaEventDestroy(e);

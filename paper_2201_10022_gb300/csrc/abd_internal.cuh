@@ -47,7 +47,39 @@ struct DevStatus {
   unsigned long long bar_terms[4];  // barrier terms evaluated, by reduced dimension m = 1, 2, 3
   double scal[8];               // PCG scalars: 0 rz, 1 pAp, 2 rr, 3 rr0, 4 alpha, 5 beta, 6 done
   double energy[8];             // 0 total, 1 inertia, 2 ortho, 3 barrier, 4 friction
+  int bar_cnt[4];               // active terms by working dimension 3, 6, 9 (classification pass)
 };
+
+// ---- small device helpers shared by the kernel files -----------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ void set_flag(DevStatus* st, unsigned f) { atomicOr(&st->flags, f); }
+
+// vertices of a pair: point-triangle (vertex i, triangle j) or edge-edge
+__device__ __forceinline__ void pair_vertices(int kind, int i, int j, const int* tri, const int* edge, int v[4]) {
+  if (kind == 0) {
+    v[0] = i;
+    v[1] = tri[3 * j];
+    v[2] = tri[3 * j + 1];
+    v[3] = tri[3 * j + 2];
+  } else {
+    v[0] = edge[2 * i];
+    v[1] = edge[2 * i + 1];
+    v[2] = edge[2 * j];
+    v[3] = edge[2 * j + 1];
+  }
+}
+
+// largest p with off[p] <= f (off has n+1 entries, nondecreasing)
+__device__ __forceinline__ int owner(const int* off, int n, int f) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (off[mid] <= f) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+#endif
 
 // ---- allocation -------------------------------------------------------------
 struct Alloc {
@@ -132,6 +164,9 @@ struct Scene {
   // the term's four vertices
   Buf<double> term;    // barrier terms
   Buf<int4> termv;
+  Buf<int> tmeta;      // barrier terms: kind | type << 1 | mollified << 5
+  Buf<double> teps;    // barrier terms: edge-edge mollifier threshold
+  Buf<int> tlist;      // barrier terms bucketed by working dimension 3, 6, 9 (3 x capacity)
   Buf<double> fterm;   // friction terms
   Buf<int4> ftermv;
   Buf<double> Epair;   // energy-only pass: barrier energy per body pair
@@ -163,10 +198,13 @@ struct Scene {
 
 constexpr int kTermStride = 91;
 
-// algorithmic FP64 operations of one barrier term by reduced dimension m:
-// derivatives, congruences with the Gram factor, Newton-Schulz step, basis
-// change, one FP64 Jacobi sweep, clamp and expansion to 12x12
-constexpr double kBarrierFlops[4] = {0.0, 850.0, 5800.0, 18400.0};
+// algorithmic FP64 operations of one barrier term by reduced dimension m.
+// m = 1: derivatives, closed-form clamp, 91 outputs.  m = 2, 3: the n x n
+// Hessian entries, the Gram congruence, the Newton-Schulz step, the basis
+// change V^T K V, one FP64 round-robin Jacobi sweep, the clamped
+// reconstruction, the inverse congruence and the expansion to 12x12 (the
+// FP32 eigenbasis is not counted)
+constexpr double kBarrierFlops[4] = {0.0, 380.0, 7500.0, 25300.0};
 
 // launch bookkeeping: count every kernel; with profiling on, bracket the
 // launches of a slot with events

@@ -57,22 +57,6 @@ __device__ __forceinline__ void prim_box(int t, int id, const int* tri, const in
   }
 }
 
-__device__ __forceinline__ void pair_vertices(int kind, int i, int j, const int* tri, const int* edge, int v[4]) {
-  if (kind == 0) {
-    v[0] = i;
-    v[1] = tri[3 * j];
-    v[2] = tri[3 * j + 1];
-    v[3] = tri[3 * j + 2];
-  } else {
-    v[0] = edge[2 * i];
-    v[1] = edge[2 * i + 1];
-    v[2] = edge[2 * j];
-    v[3] = edge[2 * j + 1];
-  }
-}
-
-__device__ __forceinline__ void set_flag(DevStatus* st, unsigned f) { atomicOr(&st->flags, f); }
-
 struct WarpLists {
   int pid[kChunk], qid[kChunk];
   double pb[kChunk][6], qb[kChunk][6];
@@ -246,340 +230,6 @@ __global__ void k_active(const int2* __restrict__ P, const DevStatus* __restrict
       base += __popc(m);
     }
     if (lane == 0) acount[p] = base;
-  }
-}
-
-__device__ __forceinline__ int owner(const int* off, int n, int f) {
-  // largest p with off[p] <= f (off has n+1 entries, nondecreasing)
-  int lo = 0, hi = n;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (off[mid] <= f) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
-// barrier terms: energy, vertex gradient and projected vertex Hessian.
-// Nine lanes work on one pair (three pairs per warp): lane 0 forms the
-// Hessian in the type's reduced coordinates, then the lanes share the
-// congruence with the Gram factor, the Jacobi rotations of the 9x9 (6x6, 3x3)
-// eigenproblem (one matrix row per lane), the eigenvalue clamp and the
-// expansion to the 12x12 vertex Hessian.
-constexpr int kBarWarps = 4;
-constexpr int kGroups = 3, kGroupLanes = 9;
-
-struct BarrierShared {
-  double H[kBarWarps][kGroups][81];
-  double K[kBarWarps][kGroups][81];
-  double V[kBarWarps][kGroups][81];
-  float K32[kBarWarps][kGroups][81];
-  float V32[kBarWarps][kGroups][81];
-  double lam[kBarWarps][kGroups][9];
-  double g[kBarWarps][kGroups][9];
-  double red[kBarWarps][kGroups][2 * kGroupLanes];
-  double E[kBarWarps][kGroups];
-};
-
-__global__ void __launch_bounds__(32 * kBarWarps) k_barrier(const DevStatus* __restrict__ cst, const int* aoff,
-                                                            const int4* act, const int* tri, const int* edge,
-                                                            const double4* x, const double* l2e, double dhat,
-                                                            double kappa, int maxc, int project, long cap,
-                                                            double* term, int4* termv, DevStatus* st) {
-  __shared__ BarrierShared sh;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int grp = lane / kGroupLanes, gl = lane - grp * kGroupLanes;
-  if (grp >= kGroups) return;  // lanes 27..31 idle
-  const unsigned gmask = 0x1FFu << (kGroupLanes * grp);
-  const int np = cst->np, nact = (int)min((long)cst->nact, cap);
-  double* H = sh.H[warp][grp];
-  double* K = sh.K[warp][grp];
-  double* V = sh.V[warp][grp];
-  double* red = sh.red[warp][grp];
-  const long stride = (long)gridDim.x * kBarWarps * kGroups;
-  for (long f = ((long)blockIdx.x * kBarWarps + warp) * kGroups + grp; f < nact; f += stride) {
-    const int p = owner(aoff, np, (int)f);
-    const int4 r = act[(size_t)p * maxc + (f - aoff[p])];
-    const int kind = (unsigned)r.x >> 31, i = r.x & 0x7fffffff;
-    int v[4];
-    pair_vertices(kind, i, r.y, tri, edge, v);
-    v3 xs[4];
-    for (int m = 0; m < 4; ++m) xs[m] = mk(x[v[m]]);
-    // a mollified edge-edge pair is worked in the line-line coordinates
-    double c = 0.0, eps = 0.0;
-    bool moll = false;
-    if (kind == 1) {
-      c = ee_cross2(xs);
-      eps = ee_eps(l2e[i], l2e[r.y]);
-      moll = c < eps;
-    }
-    Reduced R;
-    reduce(kind, moll ? 8 : r.z, xs, R);
-    const int m = R.m, n3 = 3 * m;
-    if (gl == 0 && moll) {
-      sh.E[warp][grp] = mollified_ee_term(r.z, xs, dhat, kappa, c, eps, sh.g[warp][grp], H);
-    } else if (gl == 0) {
-      double gs[9], Hs[81];
-      const double s = reduced_dist2(R, gs, Hs);
-      const double d = sqrt(s);
-      double B, B1, B2;
-      barrier_derivs(d, dhat, B, B1, B2);
-      const double cg = kappa * B1 / (2.0 * d);
-      const double ca = kappa * (B2 / (4.0 * s) - B1 / (4.0 * d * s));
-      for (int a = 0; a < n3; ++a) {
-        sh.g[warp][grp][a] = cg * gs[a];
-        for (int b = 0; b < n3; ++b) H[a * n3 + b] = ca * gs[a] * gs[b] + cg * Hs[a * n3 + b];
-      }
-      sh.E[warp][grp] = kappa * B;
-    }
-    __syncwarp(gmask);
-    // Gram factor of the difference map: C^T C = Rm^T Rm (Rm upper), Ri = Rm^-1
-    double Rm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, Ri[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    if (project) {
-      double G[3][3];
-      for (int a = 0; a < m; ++a)
-        for (int b = 0; b < m; ++b) {
-          double t = 0.0;
-          for (int k = 0; k < 4; ++k) t += R.C[k][a] * R.C[k][b];
-          G[a][b] = t;
-        }
-      for (int j = 0; j < m; ++j) {
-        double t = G[j][j];
-        for (int k = 0; k < j; ++k) t -= Rm[k][j] * Rm[k][j];
-        Rm[j][j] = sqrt(t);
-        for (int ii = j + 1; ii < m; ++ii) {
-          double u = G[j][ii];
-          for (int k = 0; k < j; ++k) u -= Rm[k][j] * Rm[k][ii];
-          Rm[j][ii] = u / Rm[j][j];
-        }
-      }
-      for (int ii = m - 1; ii >= 0; --ii) {
-        Ri[ii][ii] = 1.0 / Rm[ii][ii];
-        for (int j = ii + 1; j < m; ++j) {
-          double t = 0.0;
-          for (int k = ii + 1; k <= j; ++k) t += Rm[ii][k] * Ri[k][j];
-          Ri[ii][j] = -t / Rm[ii][ii];
-        }
-      }
-      // K = (Rm x I) H (Rm^T x I): lane gl forms row gl
-      if (gl < n3) {
-        const int a = gl / 3, ci = gl % 3;
-        for (int col = 0; col < n3; ++col) {
-          const int b = col / 3, cj = col % 3;
-          double t = 0.0;
-          for (int c = a; c < m; ++c)
-            for (int e = b; e < m; ++e) t += Rm[a][c] * H[(3 * c + ci) * n3 + 3 * e + cj] * Rm[b][e];
-          K[gl * n3 + col] = t;
-          V[gl * n3 + col] = gl == col ? 1.0 : 0.0;
-        }
-      }
-      __syncwarp(gmask);
-      // eigenvectors: cyclic Jacobi in FP32 first (one row per lane; FP32
-      // rotations are cheap), then refined to FP64 accuracy below
-      float* K32 = sh.K32[warp][grp];
-      float* V32 = sh.V32[warp][grp];
-      if (gl < n3)
-        for (int c = 0; c < n3; ++c) {
-          K32[gl * n3 + c] = (float)K[gl * n3 + c];
-          V32[gl * n3 + c] = gl == c ? 1.0f : 0.0f;
-        }
-      __syncwarp(gmask);
-      for (int sweep = 0; sweep < 20; ++sweep) {
-        float off = 0.f, tot = 0.f;
-        if (gl < n3)
-          for (int c = 0; c < n3; ++c) {
-            const float a2 = K32[gl * n3 + c] * K32[gl * n3 + c];
-            tot += a2;
-            if (c != gl) off += a2;
-          }
-        red[2 * gl] = off;
-        red[2 * gl + 1] = tot;
-        __syncwarp(gmask);
-        off = 0.f;
-        tot = 0.f;
-        for (int k = 0; k < n3; ++k) {
-          off += (float)red[2 * k];
-          tot += (float)red[2 * k + 1];
-        }
-        __syncwarp(gmask);
-        if (!(off > 1e-12f * tot)) break;
-        for (int pp = 0; pp < n3 - 1; ++pp)
-          for (int qq = pp + 1; qq < n3; ++qq) {
-            const float apq = K32[pp * n3 + qq];
-            if (fabsf(apq) <= 1e-7f * sqrtf(fabsf(K32[pp * n3 + pp] * K32[qq * n3 + qq]))) continue;
-            const float theta = (K32[qq * n3 + qq] - K32[pp * n3 + pp]) / (2.f * apq);
-            const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
-            const float c = rsqrtf(t * t + 1.f), sn = t * c;
-            __syncwarp(gmask);
-            if (gl < n3) {
-              const float kp = K32[gl * n3 + pp], kq = K32[gl * n3 + qq];
-              K32[gl * n3 + pp] = c * kp - sn * kq;
-              K32[gl * n3 + qq] = sn * kp + c * kq;
-              const float vp = V32[gl * n3 + pp], vq = V32[gl * n3 + qq];
-              V32[gl * n3 + pp] = c * vp - sn * vq;
-              V32[gl * n3 + qq] = sn * vp + c * vq;
-            }
-            __syncwarp(gmask);
-            if (gl < n3) {
-              const float kp = K32[pp * n3 + gl], kq = K32[qq * n3 + gl];
-              K32[pp * n3 + gl] = c * kp - sn * kq;
-              K32[qq * n3 + gl] = sn * kp + c * kq;
-            }
-            __syncwarp(gmask);
-          }
-      }
-      // FP64 refinement: orthonormalise the FP32 basis by one Newton-Schulz
-      // step V (3I - V^T V) / 2, rotate K into it (nearly diagonal), finish
-      // with FP64 Jacobi sweeps (quadratic convergence from FP32 accuracy)
-      if (gl < n3)
-        for (int c = 0; c < n3; ++c) V[gl * n3 + c] = (double)V32[gl * n3 + c];
-      __syncwarp(gmask);
-      if (gl < n3)  // S = V^T V, row gl into H
-        for (int c = 0; c < n3; ++c) {
-          double t = 0.0;
-          for (int k = 0; k < n3; ++k) t += V[k * n3 + gl] * V[k * n3 + c];
-          H[gl * n3 + c] = t;
-        }
-      __syncwarp(gmask);
-      double vrow[9];
-      if (gl < n3)
-        for (int c = 0; c < n3; ++c) {
-          double t = 0.0;
-          for (int k = 0; k < n3; ++k) t += V[gl * n3 + k] * ((k == c ? 1.5 : 0.0) - 0.5 * H[k * n3 + c]);
-          vrow[c] = t;
-        }
-      __syncwarp(gmask);
-      if (gl < n3)
-        for (int c = 0; c < n3; ++c) V[gl * n3 + c] = vrow[c];
-      __syncwarp(gmask);
-      if (gl < n3)  // T = K V, row gl into H
-        for (int c = 0; c < n3; ++c) {
-          double t = 0.0;
-          for (int k = 0; k < n3; ++k) t += K[gl * n3 + k] * V[k * n3 + c];
-          H[gl * n3 + c] = t;
-        }
-      __syncwarp(gmask);
-      double krow[9];
-      if (gl < n3)  // K' = V^T T, row gl
-        for (int c = 0; c < n3; ++c) {
-          double t = 0.0;
-          for (int k = 0; k < n3; ++k) t += V[k * n3 + gl] * H[k * n3 + c];
-          krow[c] = t;
-        }
-      __syncwarp(gmask);
-      if (gl < n3)
-        for (int c = 0; c < n3; ++c) K[gl * n3 + c] = krow[c];
-      __syncwarp(gmask);
-      // symmetrise (K' is symmetric up to rounding)
-      if (gl < n3)
-        for (int c = gl + 1; c < n3; ++c) {
-          const double a = 0.5 * (K[gl * n3 + c] + K[c * n3 + gl]);
-          K[gl * n3 + c] = a;
-          K[c * n3 + gl] = a;
-        }
-      __syncwarp(gmask);
-      for (int sweep = 0; sweep < 20; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        if (gl < n3)
-          for (int c = 0; c < n3; ++c) {
-            const double a2 = K[gl * n3 + c] * K[gl * n3 + c];
-            tot += a2;
-            if (c != gl) off += a2;
-          }
-        red[2 * gl] = off;
-        red[2 * gl + 1] = tot;
-        __syncwarp(gmask);
-        off = 0.0;
-        tot = 0.0;
-        for (int k = 0; k < n3; ++k) {
-          off += red[2 * k];
-          tot += red[2 * k + 1];
-        }
-        __syncwarp(gmask);
-        if (!(off > 1e-28 * tot)) break;
-        for (int pp = 0; pp < n3 - 1; ++pp)
-          for (int qq = pp + 1; qq < n3; ++qq) {
-            const double apq = K[pp * n3 + qq];
-            // negligible against its diagonal pair: no rotation
-            if (fabs(apq) <= 1e-16 * sqrt(fabs(K[pp * n3 + pp] * K[qq * n3 + qq]))) continue;
-            const double theta = (K[qq * n3 + qq] - K[pp * n3 + pp]) / (2.0 * apq);
-            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
-            __syncwarp(gmask);
-            if (gl < n3) {
-              const double kp = K[gl * n3 + pp], kq = K[gl * n3 + qq];
-              K[gl * n3 + pp] = c * kp - sn * kq;
-              K[gl * n3 + qq] = sn * kp + c * kq;
-              const double vp = V[gl * n3 + pp], vq = V[gl * n3 + qq];
-              V[gl * n3 + pp] = c * vp - sn * vq;
-              V[gl * n3 + qq] = sn * vp + c * vq;
-            }
-            __syncwarp(gmask);
-            if (gl < n3) {
-              const double kp = K[pp * n3 + gl], kq = K[qq * n3 + gl];
-              K[pp * n3 + gl] = c * kp - sn * kq;
-              K[qq * n3 + gl] = sn * kp + c * kq;
-            }
-            __syncwarp(gmask);
-          }
-      }
-      if (gl < n3) sh.lam[warp][grp][gl] = K[gl * n3 + gl];
-      __syncwarp(gmask);
-      // Proj(K) = sum_k max(lambda_k, 0) v_k v_k^T, row gl into H
-      if (gl < n3)
-        for (int col = 0; col < n3; ++col) {
-          double t = 0.0;
-          for (int k = 0; k < n3; ++k) {
-            const double lam = sh.lam[warp][grp][k];
-            if (lam > 0.0) t += V[gl * n3 + k] * lam * V[col * n3 + k];
-          }
-          H[gl * n3 + col] = t;
-        }
-      __syncwarp(gmask);
-      // back to the difference coordinates: (Ri x I) Proj(K) (Ri^T x I), row gl into K
-      if (gl < n3) {
-        const int a = gl / 3, ci = gl % 3;
-        for (int col = 0; col < n3; ++col) {
-          const int b = col / 3, cj = col % 3;
-          double t = 0.0;
-          for (int c = a; c < m; ++c)
-            for (int e = b; e < m; ++e) t += Ri[a][c] * H[(3 * c + ci) * n3 + 3 * e + cj] * Ri[b][e];
-          K[gl * n3 + col] = t;
-        }
-      }
-      __syncwarp(gmask);
-    }
-    const double* Hr = project ? K : H;
-    double* T = term + (size_t)f * kTermStride;
-    // vertex gradient and packed upper vertex Hessian: H12 = T Hr T^T
-    for (int o = gl; o < 12; o += kGroupLanes) {
-      const int k = o / 3, ci = o % 3;
-      double t = 0.0;
-      for (int w = 0; w < m; ++w) t += R.C[k][w] * sh.g[warp][grp][3 * w + ci];
-      T[1 + o] = t;
-    }
-    for (int e = gl; e < 78; e += kGroupLanes) {
-      // packed index e -> (row, col), row <= col
-      int row = 0, rem = e;
-      while (rem >= 12 - row) {
-        rem -= 12 - row;
-        ++row;
-      }
-      const int col = row + rem;
-      const int k = row / 3, ci = row % 3, l = col / 3, cj = col % 3;
-      double t = 0.0;
-      for (int vv = 0; vv < m; ++vv) {
-        if (R.C[k][vv] == 0.0) continue;
-        for (int w = 0; w < m; ++w) t += R.C[k][vv] * R.C[l][w] * Hr[(3 * vv + ci) * n3 + 3 * w + cj];
-      }
-      T[13 + e] = t;
-    }
-    if (gl == 0) {
-      T[0] = sh.E[warp][grp];
-      termv[f] = make_int4(v[0], v[1], v[2], v[3]);
-      atomicAdd(&st->bar_terms[m], 1ull);
-    }
-    __syncwarp(gmask);
   }
 }
 
@@ -765,13 +415,6 @@ void launch_active(Scene& s, const double4* x) {
   ProfScope ps(s, PF_ACTIVE);
   k_active<<<grid, 256, 0, s.stream>>>(s.P.p, s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.prm.dhat, s.maxc,
                                        s.act.p, s.act_d2.p, s.acount.p, s.st);
-}
-
-void launch_barrier(Scene& s, int project, long cap) {
-  counted(s);
-  ProfScope ps(s, PF_BARRIER);
-  k_barrier<<<152 * 8, 32 * kBarWarps, 0, s.stream>>>(s.st, s.aoff.p, s.act.p, s.tri.p, s.edge.p, s.x.p, s.l2e.p,
-                                          s.prm.dhat, s.prm.kappa, s.maxc, project, cap, s.term.p, s.termv.p, s.st);
 }
 
 void launch_friction_lag(Scene& s) {

@@ -13,7 +13,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ void set_flag(DevStatus* st, unsigned f) { atomicOr(&st->flags, f); }
 
 // DOF of the coefficient multiplying w_u = (1, xbar)_u in x_c
 __host__ __device__ __forceinline__ int dof(int u, int c) { return u == 0 ? c : 3 + 3 * c + (u - 1); }

@@ -21,17 +21,26 @@ def main():
     ap.add_argument("dims", type=int, nargs=3)
     ap.add_argument("--evals", type=int, default=1)
     ap.add_argument("--steps", type=int, default=0)
+    ap.add_argument("--prof", action="store_true", help="print per-slot kernel times (CUDA events)")
     a = ap.parse_args()
     nx, ny, nz = a.dims
     s = scenes.packed_cubes(nx=nx, ny=ny, nz=nz) if a.scene == "packed" else scenes.lattice_pile(nx=nx, ny=ny, nz=nz)
     g = AbdScene(s)
     q = torch.tensor(s.q0)
+    E, grad, cnt = g.energy_grad_hess(q)  # warm-up (buffer growth)
+    if a.prof:
+        g.set_profiling(True)
     for _ in range(a.evals):
         E, grad, cnt = g.energy_grad_hess(q)
     if a.steps:
         g.step(a.steps)
     torch.cuda.synchronize()
-    print({"bodies": s.nb, "active": cnt["n_active"], "candidates": cnt["n_candidates"], "energy": float(E[0])})
+    out = {"bodies": s.nb, "active": cnt["n_active"], "candidates": cnt["n_candidates"], "energy": float(E[0])}
+    if a.prof:
+        out["kernels"] = {k: {"launches": v["launches"], "ms": round(v["total_ms"], 4),
+                              "tflops": round(v["flops"] / (v["total_ms"] * 1e-3) / 1e12, 4) if v["total_ms"] > 0 and v["flops"] else None}
+                          for k, v in g.profile().items() if v["launches"]}
+    print(out)
 
 
 if __name__ == "__main__":
