@@ -154,7 +154,6 @@ def run_abd(args, rank, world):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk.start()
-    g.set_profiling(True)
     torch.cuda.nvtx.range_push("timed")
     ms, stats = [], []
     for k in range(args.steps):
@@ -167,12 +166,22 @@ def run_abd(args, rank, world):
         ms.append(e0.elapsed_time(e1))
         stats.append(st)
     torch.cuda.nvtx.range_pop()
-    prof = g.profile()
-    g.set_profiling(False)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = clk.stop()
+
+    # ---- per-kernel-class device times: the same steps again from the same
+    # state with the library's event profiling on (kept out of the timed run)
+    g.set_state(q0, qd0)
+    g.set_profiling(True)
+    for k in range(args.steps):
+        flush.zero_()
+        g.step(1)
+    torch.cuda.synchronize()
+    prof = g.profile()
+    g.set_profiling(False)
+    cnt = g.counters()
     total_ms = sum(ms)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -246,6 +255,7 @@ def run_abd(args, rank, world):
         "gpu_launches": launches,
         "roofline": roof,
         "kernel_ms": {k: round(v["total_ms"], 3) for k, v in prof.items()},
+        "barrier_counters": cnt,
         "clocks": clocks,
     }
     return out

@@ -201,6 +201,17 @@ ABD_API abd_status abd_step(abd_scene* s, int nsteps, abd_step_stats* stats);
 ABD_API abd_status abd_set_profiling(abd_scene* s, int on);
 ABD_API abd_status abd_get_profile(abd_scene* s, abd_kernel_profile* out, int cap, int* n);
 
+/* Work counters of the barrier-term kernel, cumulative since the scene was
+ * created (diagnostics of the eigen-projection's cost; no effect on
+ * results).  Synchronises the scene's stream. */
+typedef struct {
+  unsigned long long barrier_terms[4]; /* terms evaluated, by reduced dimension m = 1, 2, 3 (index m) */
+  unsigned long long sweeps_fp32;      /* FP32 Jacobi sweeps over all 6- and 9-dimensional terms */
+  unsigned long long sweeps_fp64;      /* FP64 refinement sweeps over the same terms */
+  unsigned long long capped_fp64;      /* terms whose FP64 sweeps reached the sweep cap */
+} abd_counters;
+ABD_API abd_status abd_get_counters(abd_scene* s, abd_counters* out);
+
 /* Minimum additive-CCD time of impact over a caller-given list of pairs,
  * allocating nothing.  The paper has no counterpart: this serves callers
  * that cannot allocate device memory when they need a step bound (a fixed

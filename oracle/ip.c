@@ -382,18 +382,18 @@ static double body_terms(orc_ctx* c, int b, const double* q, double* g, double* 
   double dt2 = c->sc.dt * c->sc.dt;
   double gv[12], Hv[144];
   double V = orc_ortho(q, c->kappa_body[b], c->vol[b], gv, Hv);
-  if (project) {
-    double A9[81];
-    for (int i = 0; i < 9; ++i)
-      for (int j = 0; j < 9; ++j) A9[9 * i + j] = Hv[12 * (3 + i) + 3 + j];
-    orc_project_psd(9, A9);
-    for (int i = 0; i < 9; ++i)
-      for (int j = 0; j < 9; ++j) Hv[12 * (3 + i) + 3 + j] = A9[9 * i + j];
-  }
   if (g)
     for (int k = 0; k < 12; ++k) g[k] = Mdq[k] + dt2 * gv[k];
-  if (H)
+  if (H) {
+    /* the whole body block M + dt^2 hess V; projected to the PSD cone only
+     * when it is not positive definite (Cholesky fails) */
     for (int k = 0; k < 144; ++k) H[k] = M[k] + dt2 * Hv[k];
+    if (project) {
+      double L[144];
+      memcpy(L, H, sizeof(L));
+      if (chol(12, L)) orc_project_psd(12, H);
+    }
+  }
   *Eo = dt2 * V;
   return Ei;
 }

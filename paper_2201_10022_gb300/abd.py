@@ -65,6 +65,11 @@ class abd_kernel_profile(C.Structure):
                 ("flops", C.c_double)]
 
 
+class abd_counters(C.Structure):
+    _fields_ = [("barrier_terms", C.c_ulonglong * 4), ("sweeps_fp32", C.c_ulonglong),
+                ("sweeps_fp64", C.c_ulonglong), ("capped_fp64", C.c_ulonglong)]
+
+
 def _as_dict(st):
     return {k: (list(getattr(st, k)) if isinstance(getattr(st, k), C.Array) else getattr(st, k))
             for k, _ in st._fields_}
@@ -73,7 +78,8 @@ def _as_dict(st):
 _lib = None
 EXPORTS = ["abd_default_params", "abd_create_scene", "abd_destroy", "abd_set_state", "abd_get_state",
            "abd_energy_grad_hess", "abd_get_hessian", "abd_get_pairs", "abd_solve", "abd_ccd_toi", "abd_step",
-           "abd_set_profiling", "abd_get_profile", "abd_ccd_toi_pairs_noalloc", "abd_last_error"]
+           "abd_set_profiling", "abd_get_profile", "abd_get_counters", "abd_ccd_toi_pairs_noalloc",
+           "abd_last_error"]
 
 
 def lib_path() -> str:
@@ -104,6 +110,7 @@ def load(build_if_missing: bool = True):
         "abd_step": (i, [vp, i, vp]),
         "abd_set_profiling": (i, [vp, i]),
         "abd_get_profile": (i, [vp, vp, i, vp]),
+        "abd_get_counters": (i, [vp, vp]),
         "abd_ccd_toi_pairs_noalloc": (i, [vp, vp, i, vp, vp, l, d, i, vp, vp]),
         "abd_last_error": (C.c_char_p, [vp]),
     }
@@ -180,6 +187,10 @@ def abd_set_profiling(h, on):
 
 def abd_get_profile(h, out, cap, n):
     return load().abd_get_profile(h, out, cap, n)
+
+
+def abd_get_counters(h, out):
+    return load().abd_get_counters(h, out)
 
 
 def abd_ccd_toi_pairs_noalloc(x_ptr, dx_ptr, nv, verts_ptr, kind_ptr, npairs, ccd_s, ccd_max, stream, toi):
@@ -362,3 +373,8 @@ class AbdScene:
         return {arr[k].name.decode(): dict(launches=arr[k].launches, total_ms=arr[k].total_ms, bytes=arr[k].bytes,
                                            flops=arr[k].flops)
                 for k in range(min(n.value, 16))}
+
+    def counters(self):
+        c = abd_counters()
+        self._check(abd_get_counters(self.h, C.byref(c)))
+        return _as_dict(c)

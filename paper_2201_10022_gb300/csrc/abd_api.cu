@@ -72,7 +72,7 @@ void size_pair_buffers(Scene& s, size_t pcap) {
   grow(s, s.fpoff, pcap + 1);
   grow(s, s.flagbuf, pcap);
   grow(s, s.posbuf, pcap + 1);
-  grow(s, s.Epair, pcap);
+  grow(s, s.Epair, pcap * (size_t)energy_chunks(s));
   grow(s, s.cand, pcap * (size_t)s.maxc);
   grow(s, s.act, pcap * (size_t)s.maxc);
   grow(s, s.act_d2, pcap * (size_t)s.maxc);
@@ -258,29 +258,32 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
   broad_and_enumerate(s, false, false);
   read_status(s);
   s.cand_last = (long)s.st_host->n_cand;
+  s.last_np = s.st_host->np;
   abd_status status = ABD_ERR_NEWTON_MAXITER;
   for (int it = 0; it < s.prm.newton_max; ++it) {
     launch_transform(s, s.q.p, s.x.p);
     eval_system(s, s.q.p, 1);
-    read_status(s);
+    // Newton direction: H dq = -g, enqueued behind the system without a host
+    // round trip; the status word the solver reads back also carries the
+    // system's flags and energies, checked before its result is used (every
+    // kernel bounds its work by the clamped counts, so an overflowed system
+    // is only discarded)
+    launch_negate(s, s.g.p, s.qsave.p, 12L * s.nb);
+    double rel;
+    int its = run_pcg(s, s.qsave.p, s.dq.p, s.prm.pcg_max, s.prm.pcg_rel_tol, &rel);
     if (s.st_host->flags & kCapFlags) return ABD_ERR_CAPACITY;
     if (abd_status r = flags_to_status(s, s.st_host->flags)) return r;
-    s.last_np = s.st_host->np;
     loc.n_active = s.st_host->nact;
     loc.candidates_tested += cand_total(s);
     loc.active_evaluated += s.st_host->nact;
     loc.n_candidates = cand_total(s);
-    // Newton direction: H dq = -g
-    launch_negate(s, s.g.p, s.qsave.p, 12L * s.nb);
-    double rel;
-    int its = run_pcg(s, s.qsave.p, s.dq.p, s.prm.pcg_max, s.prm.pcg_rel_tol, &rel);
     if (its == -2) {
       s.err = "PCG breakdown";
       return ABD_ERR_PCG_BREAKDOWN;
     }
     loc.pcg_iters += its < 0 ? s.prm.pcg_max : its;
     // E(q) over the active set of this iteration: the line search's reference
-    const double E0 = s.st_host->energy[0];
+    const double E0 = s.st_host->energy[5];
     // step length for the convergence test, then (in the same batch) the CCD
     // bound over the swept candidates and the first trial at alpha = bound;
     // the swept candidates also serve the next iteration
@@ -309,6 +312,7 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
     }
     loc.newton_iters++;
     s.cand_last = (long)s.st_host->n_cand;
+    s.last_np = s.st_host->np;
     if (s.st_host->flags & kCapFlags) return ABD_ERR_CAPACITY;
     if (abd_status r = flags_to_status(s, s.st_host->flags & ~ST_INTERSECT)) return r;
     double alpha = bits_to_double(s.st_host->toi_bits);
@@ -483,6 +487,7 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
       s.hash_T = (int)t;
     }
     grow(s, s.slot_cnt, (size_t)s.hash_T);
+    grow(s, s.scan_part, (size_t)s.hash_T / 4096 + 1);
     grow(s, s.slot_off, (size_t)s.hash_T + 1);
     grow(s, s.entries, 16L * nb + 1024);
     s.maxc = 256;
@@ -583,6 +588,7 @@ void abd_destroy(abd_scene* S) {
   if (s.stream || s.st) cudaStreamSynchronize(s.stream);
   release(s, s.xbar);
   release(s, s.l2e);
+  release(s, s.scan_part);
   release(s, s.vbody);
   release(s, s.tri);
   release(s, s.edge);
@@ -911,6 +917,17 @@ abd_status abd_get_profile(abd_scene* S, abd_kernel_profile* out, int cap, int* 
     out[k].bytes = s.prof.slot[k].bytes;
     out[k].flops = k == PF_BARRIER ? bar_flops : 0.0;
   }
+  return check_cuda(s);
+}
+
+abd_status abd_get_counters(abd_scene* S, abd_counters* out) {
+  if (!S || !out) return ABD_ERR_INVALID_ARG;
+  Scene& s = S->s;
+  read_status(s);
+  for (int m = 0; m < 4; ++m) out->barrier_terms[m] = s.st_host->bar_terms[m];
+  out->sweeps_fp32 = s.st_host->jac[0];
+  out->sweeps_fp64 = s.st_host->jac[1];
+  out->capped_fp64 = s.st_host->jac[2];
   return check_cuda(s);
 }
 

@@ -48,6 +48,7 @@ struct DevStatus {
   double scal[8];               // PCG scalars: 0 rz, 1 pAp, 2 rr, 3 rr0, 4 alpha, 5 beta, 6 done
   double energy[8];             // 0 total, 1 inertia, 2 ortho, 3 barrier, 4 friction
   int bar_cnt[4];               // active terms by working dimension 3, 6, 9 (classification pass)
+  unsigned long long jac[3];    // Jacobi sweeps FP32, FP64, terms at the FP64 sweep cap (cumulative)
 };
 
 // ---- small device helpers shared by the kernel files -----------------------
@@ -169,7 +170,7 @@ struct Scene {
   Buf<int> tlist;      // barrier terms bucketed by working dimension 3, 6, 9 (3 x capacity)
   Buf<double> fterm;   // friction terms
   Buf<int4> ftermv;
-  Buf<double> Epair;   // energy-only pass: barrier energy per body pair
+  Buf<double> Epair;   // energy-only pass: barrier energy per (body pair, chunk of 32 candidates)
 
   // friction
   Buf<FricRec> fric;
@@ -182,6 +183,7 @@ struct Scene {
   Buf<double> Db, gb, Eb;   // body terms
   Buf<double> D, g, Pinv;   // assembled diagonal, gradient, preconditioner
   Buf<double> red;     // reduction scratch
+  Buf<long long> scan_part;  // tile sums of the two-phase scan
 
   // PCG
   Buf<double> r, z, pv, Ap, part;
@@ -210,6 +212,9 @@ constexpr double kBarrierFlops[4] = {0.0, 380.0, 7500.0, 25300.0};
 // launches of a slot with events
 cudaEvent_t prof_event(Scene& s);
 inline void counted(Scene& s, int n = 1) { s.nlaunch += n; }
+
+// chunks of 32 candidate slots per body pair (energy-only pass partial sums)
+inline int energy_chunks(const Scene& s) { return (s.maxc + 31) / 32; }
 struct ProfScope {
   Scene& s;
   int slot;

@@ -21,8 +21,8 @@
 //     Jacobi in FP32 with round-robin ordering (n/2 disjoint rotations per
 //     round), then refine it in FP64: one Newton-Schulz step V (3I - V^T V)/2,
 //     K' = V^T K V, and FP64 round-robin Jacobi sweeps on the nearly diagonal
-//     K' until its off-diagonal mass is below 1e-12 of the total (squares
-//     below 1e-24).  Negative eigenvalues are clamped to zero.
+//     K' until its off-diagonal mass is below 1e-11 of the total (squares
+//     below 1e-22).  Negative eigenvalues are clamped to zero.
 // A mollified edge-edge pair (near-parallel edges) is worked in the line-line
 // coordinates (n = 9) whatever its distance type.
 #include <math.h>
@@ -279,7 +279,8 @@ __device__ __forceinline__ void rot32(float app, float aqq, float apq, float& c,
   s = t * c;
 }
 
-__device__ __forceinline__ void rot64(double app, double aqq, double apq, double& c, double& s) {
+// FP64 rotation; sc scales the entries into FP32 range (1 / max |K|)
+__device__ __forceinline__ void rot64(double app, double aqq, double apq, double sc, double& c, double& s) {
   if (apq == 0.0 || apq * apq <= 1e-36 * fabs(app * aqq)) {  // negligible against its diagonal pair
     c = 1.0;
     s = 0.0;
@@ -287,9 +288,11 @@ __device__ __forceinline__ void rot64(double app, double aqq, double apq, double
   }
   const double dd = aqq - app;
   if (fabs(dd) > 2e4 * fabs(apq)) {
-    // |theta| > 1e4: t = 1/(2 theta) (1 - 1/(4 theta^2)), c = 1 - t^2/2, both
-    // exact to a relative 1e-17
-    const double u = apq / dd;
+    // |theta| > 1e4: t = 1/(2 theta) (1 - 1/(4 theta^2)).  The quotient is
+    // taken in FP32: the rotation stays orthogonal to FP64 rounding
+    // (c = 1 - t^2/2 is exact to a relative 1e-17 here) and annihilates
+    // K_pq up to a relative 1e-7, which the next sweep squares away.
+    const double u = (double)(__fdividef((float)(apq * sc), (float)(dd * sc)));
     const double t = u * (1.0 - u * u);
     c = 1.0 - 0.5 * t * t;
     s = t * c;
@@ -305,7 +308,8 @@ __device__ __forceinline__ void rot64(double app, double aqq, double apq, double
 // chosen to annihilate K_pq, applied as K <- J^T K J, V <- V J into the
 // other buffers.  rc[i] = J_ii, rs[i] = J_{partner(i), i}.
 template <int N, typename T>
-__device__ __forceinline__ void jacobi_round(int r, int lane, const T* Kc, T* Kn, const T* Vc, T* Vn, T* rc, T* rs) {
+__device__ __forceinline__ void jacobi_round(int r, int lane, const T* Kc, T* Kn, const T* Vc, T* Vn, T* rc, T* rs,
+                                             double sc) {
   constexpr int NP = N + (N & 1), last = NP - 1;
   if (lane < NP / 2) {
     int p = lane == 0 ? r : (r + lane) % last;
@@ -318,7 +322,7 @@ __device__ __forceinline__ void jacobi_round(int r, int lane, const T* Kc, T* Kn
     if (q < N) {
       T c, s;
       if constexpr (sizeof(T) == 4) rot32(Kc[p * N + p], Kc[q * N + q], Kc[p * N + q], c, s);
-      else rot64(Kc[p * N + p], Kc[q * N + q], Kc[p * N + q], c, s);
+      else rot64(Kc[p * N + p], Kc[q * N + q], Kc[p * N + q], sc, c, s);
       rc[p] = c;
       rc[q] = c;
       rs[p] = -s;
@@ -503,15 +507,18 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
       }
       __syncwarp();
       constexpr int NP = N + (N & 1);
-      int cur = 0;
+      int cur = 0, n32 = 0, n64 = 0, capped = 0;
       float prev = INFINITY;
       for (int sweep = 0; sweep < 12; ++sweep) {
         float off, tot;
         off_tot<N>(W.K32[cur], lane, off, tot);
-        if (!(off > 1e-13f * tot) || off > 0.25f * prev) break;  // converged, or at FP32 rounding
+        if (!(off > 1e-13f * tot)) break;
+        if (off < 1e-9f * tot && off > 0.25f * prev) break;  // at the FP32 rounding floor
         prev = off;
+        ++n32;
         for (int r = 0; r < NP - 1; ++r) {
-          jacobi_round<N, float>(r, lane, W.K32[cur], W.K32[cur ^ 1], W.V32[cur], W.V32[cur ^ 1], W.rc32, W.rs32);
+          jacobi_round<N, float>(r, lane, W.K32[cur], W.K32[cur ^ 1], W.V32[cur], W.V32[cur ^ 1], W.rc32, W.rs32,
+                                 1.0);
           cur ^= 1;
         }
       }
@@ -557,14 +564,24 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
       double* Vb[2] = {W.Vd[1], W.Vd[0]};
       int c64 = 0;
       __syncwarp();
-      for (int sweep = 0; sweep < 8; ++sweep) {
+      for (int sweep = 0; sweep <= 8; ++sweep) {
         double off, tot;
         off_tot<N>(Kb[c64], lane, off, tot);
-        if (!(off > 1e-24 * tot)) break;
+        if (!(off > 1e-22 * tot)) break;
+        if (sweep == 8) {  // cap reached: keep the last basis
+          capped = 1;
+          break;
+        }
+        ++n64;
         for (int r = 0; r < NP - 1; ++r) {
-          jacobi_round<N, double>(r, lane, Kb[c64], Kb[c64 ^ 1], Vb[c64], Vb[c64 ^ 1], W.rc, W.rs);
+          jacobi_round<N, double>(r, lane, Kb[c64], Kb[c64 ^ 1], Vb[c64], Vb[c64 ^ 1], W.rc, W.rs, inv);
           c64 ^= 1;
         }
+      }
+      if (lane == 0) {
+        atomicAdd(&st->jac[0], (unsigned long long)n32);
+        atomicAdd(&st->jac[1], (unsigned long long)n64);
+        if (capped) atomicAdd(&st->jac[2], 1ull);
       }
       // Proj = V diag(max(lambda, 0)) V^T
       const double* Kf = Kb[c64];

@@ -354,21 +354,27 @@ __global__ void k_friction_eval(const DevStatus* __restrict__ cst, const FricRec
 
 // energy of the barrier over the stored candidates at positions x: one value
 // per body pair, summed in slot order (energy-only pass of the line search)
+// energy-only barrier sum over the stored candidates: one warp per (body
+// pair, chunk of 32 candidates) so that a body pair with many candidates is
+// spread over several warps; each warp writes its partial sum to its own
+// slot (np x nch, summed later in a fixed order)
 __global__ void k_pair_energy(const DevStatus* __restrict__ cst, const int2* cand, const int* ccount,
                               const int* tri, const int* edge, const double4* x, const double* l2e, double dhat,
-                              double kappa, int maxc, double* Ep, DevStatus* st) {
+                              double kappa, int maxc, int nch, double* Ep, DevStatus* st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  const int np = cst->np;
+  const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+  const long nw = (long)cst->np * nch;
   const double dh2 = __dmul_rn(dhat, dhat);
-  for (int p = blockIdx.x * (blockDim.x >> 5) + warp; p < np; p += nwarps) {
+  for (long w = (long)blockIdx.x * (blockDim.x >> 5) + warp; w < nw; w += nwarps) {
+    const int p = (int)(w / nch), c = (int)(w - (long)p * nch);
     const int n = min(ccount[p], maxc);
+    const int k = c * 32 + lane;
     double e = 0.0;
-    for (int k = lane; k < n; k += 32) {
-      int2 c = cand[(size_t)p * maxc + k];
-      int kind = (unsigned)c.x >> 31, i = c.x & 0x7fffffff;
+    if (k < n) {
+      int2 cc = cand[(size_t)p * maxc + k];
+      int kind = (unsigned)cc.x >> 31, i = cc.x & 0x7fffffff;
       int v[4];
-      pair_vertices(kind, i, c.y, tri, edge, v);
+      pair_vertices(kind, i, cc.y, tri, edge, v);
       v3 xs[4];
       for (int m = 0; m < 4; ++m) xs[m] = mk(x[v[m]]);
       int type;
@@ -380,13 +386,14 @@ __global__ void k_pair_energy(const DevStatus* __restrict__ cst, const int2* can
         double mv = 1.0;
         if (kind == 1) {
           double dm, d2m;
-          mv = ee_mollifier(ee_cross2(xs), ee_eps(l2e[i], l2e[c.y]), dm, d2m);
+          mv = ee_mollifier(ee_cross2(xs), ee_eps(l2e[i], l2e[cc.y]), dm, d2m);
         }
-        e += kappa * B * mv;
+        e = kappa * B * mv;
       }
     }
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(kFull, e, o);
-    if (lane == 0) Ep[p] = e;
+    if (c * 32 < n)
+      for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(kFull, e, o);
+    if (lane == 0) Ep[w] = e;
   }
 }
 
@@ -432,10 +439,11 @@ void launch_friction_eval(Scene& s, const double4* x, bool derivs) {
 }
 
 void launch_pair_energy(Scene& s, const double4* x) {
-  int grid = grid_for(s.last_np > 0 ? s.last_np : s.nb, 8, 152 * 16);
+  const int nch = energy_chunks(s);
+  int grid = grid_for((long)(s.last_np > 0 ? s.last_np : s.nb) * nch, 8, 152 * 32);
   counted(s);
   k_pair_energy<<<grid, 256, 0, s.stream>>>(s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.l2e.p,
-                                            s.prm.dhat, s.prm.kappa, s.maxc, s.Epair.p, s.st);
+                                            s.prm.dhat, s.prm.kappa, s.maxc, nch, s.Epair.p, s.st);
 }
 
 }  // namespace abd

@@ -468,6 +468,84 @@ __global__ void k_scan(const int* cnt, int* off, const int* n_dev, int n_const, 
   }
 }
 
+// two-phase exclusive scan for long arrays: tile sums (4096 entries a block),
+// then every block scans its tile from the sum of the tiles before it; the
+// last block writes off[n] and the clamped total
+constexpr int kScanTile = 4096;
+
+__global__ void k_scan_tiles(const int* cnt, int n, long long* part) {
+  __shared__ long long ws[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int base = blockIdx.x * kScanTile;
+  long long loc = 0;
+  for (int k = 0; k < 4; ++k) {
+    const int i = base + 4 * t + k;
+    if (i < n) loc += cnt[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) loc += __shfl_xor_sync(kFull, loc, o);
+  if (lane == 0) ws[w] = loc;
+  __syncthreads();
+  if (w == 0) {
+    long long x = ws[lane];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    if (lane == 0) part[blockIdx.x] = x;
+  }
+}
+
+__global__ void k_scan_apply(const int* cnt, int* off, int n, const long long* part, int* total_dev, long cap,
+                             unsigned flag, unsigned long long* need, DevStatus* st) {
+  __shared__ long long wsum[32];
+  __shared__ long long carry_s;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int b = blockIdx.x, base = b * kScanTile;
+  if (w == 0) {  // sum of the earlier tiles, in a fixed order
+    long long c = 0;
+    for (int k = lane; k < b; k += 32) c += part[k];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if (lane == 0) carry_s = c;
+  }
+  int v[4];
+  long long loc = 0;
+  for (int k = 0; k < 4; ++k) {
+    const int i = base + 4 * t + k;
+    v[k] = i < n ? cnt[i] : 0;
+    loc += v[k];
+  }
+  long long inc = loc;
+  for (int o = 1; o < 32; o <<= 1) {
+    long long u = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    long long x = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      long long u = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += u;
+    }
+    wsum[lane] = x;
+  }
+  __syncthreads();
+  long long run = carry_s + (w ? wsum[w - 1] : 0) + inc - loc;
+  for (int k = 0; k < 4; ++k) {
+    const int i = base + 4 * t + k;
+    if (i < n) off[i] = (int)run;
+    run += v[k];
+  }
+  if (b == gridDim.x - 1 && t == 1023) {
+    const long long total = run;  // thread 1023 of the last tile ends past n
+    off[n] = (int)total;
+    if (total > cap) {
+      set_flag(st, flag);
+      atomicMax(need, (unsigned long long)total);
+      *total_dev = (int)cap;
+    } else {
+      *total_dev = (int)total;
+    }
+  }
+}
+
 // incoming lists: body pairs whose second body is b, sorted by pair index
 __global__ void k_in_count(const DevStatus* cst, const int2* P, int* cnt) {
   const int np = cst->np;
@@ -607,16 +685,15 @@ __global__ void k_assemble(const DevStatus* __restrict__ cst, const int2* P, con
 }
 
 // ---------------------------------------------------------------------------
-// per-body inertia and orthogonality terms (Sec. 3.2, Sec. 4)
+// per-body inertia and orthogonality energies and gradients (Sec. 3.2,
+// Sec. 4); the Hessian block is formed by k_body_hess
 // ---------------------------------------------------------------------------
 __global__ void k_body_terms(int nb, const uint8_t* is_static, const double* q, const double* qtilde,
-                             const double* mass10, const double* vol, const double* kappa_b, double dt, bool hess,
-                             double* Db, double* gb, double* Eb) {
+                             const double* mass10, const double* vol, const double* kappa_b, double dt, double* gb,
+                             double* Eb) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nb) return;
   if (is_static[b]) {
-    if (hess)
-      for (int k = 0; k < 144; ++k) Db[144 * b + k] = (k % 13 == 0) ? 1.0 : 0.0;
     for (int k = 0; k < 12; ++k) gb[12 * b + k] = 0.0;
     Eb[2 * b] = Eb[2 * b + 1] = 0.0;
     return;
@@ -664,61 +741,105 @@ __global__ void k_body_terms(int nb, const uint8_t* is_static, const double* q, 
   for (int k = 0; k < 12; ++k) gb[12 * b + k] = Md[k] + dt2 * gv[k];
   Eb[2 * b] = Ein;
   Eb[2 * b + 1] = dt2 * V;
-  if (!hess) return;
-  // PSD part of the orthogonality Hessian from its closed-form eigensystem.
-  // V = kv sum_i (s_i^2 - 1)^2 over the singular values of A = U S V^T; with
-  // X an orthonormal basis of 3x3 matrices and W = U X V^T, the second
-  // variation of V along W is
-  //   X = e_i e_i^T:                        kv (12 s_i^2 - 4)
-  //   X = (e_i e_j^T +- e_j e_i^T)/sqrt2:   4 kv (s_i^2 +- s_i s_j + s_j^2 - 1)
-  // and these nine W are the Hessian's eigenvectors over vec(A) (row order).
-  double A9[81];
+
+}
+
+// Hessian block of the body terms (Sec. 3.2, Sec. 4): B = M + dt^2 hess V_ortho
+// over q = (p, rows a_i of A), with the closed form
+//   d2 V / da_k da_l = 4 kappa nu [(a_k.a_l - delta_kl) I + delta_kl A^T A + a_l a_k^T],
+// used as it is when it is positive definite (a Cholesky factorisation
+// succeeds) and replaced by its PSD projection otherwise.  Twelve threads per
+// body (one row each), sixteen bodies per block; static bodies get I.
+constexpr int kHessBodies = 16, kHessThreads = 12 * kHessBodies;
+
+__global__ void __launch_bounds__(kHessThreads) k_body_hess(int nb, const uint8_t* is_static, const double* q,
+                                                            const double* mass10, const double* vol,
+                                                            const double* kappa_b, double dt, double* Db) {
+  __shared__ double Bs[kHessBodies][12][13];
+  __shared__ double L[kHessBodies][12][13];
+  __shared__ double rd[kHessBodies][12];
+  __shared__ int bad[kHessBodies];
+  const int bl = threadIdx.x / 12, r = threadIdx.x - 12 * (threadIdx.x / 12);
+  const int b = blockIdx.x * kHessBodies + bl;
+  const bool live = b < nb && !is_static[b];
+  if (r == 0) bad[bl] = 0;
+  // row r of B
   {
-    // A^T A = V S^2 V^T by cyclic Jacobi on the 3x3 symmetric matrix
-    double C[9], Vm[9];
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) C[3 * r + c] = comp(a[0], r) * comp(a[0], c) + comp(a[1], r) * comp(a[1], c) +
-                                                comp(a[2], r) * comp(a[2], c);
-    jacobi_eig<3, double>(C, Vm);
-    double sg[3], Um[9];
-    for (int i = 0; i < 3; ++i) sg[i] = sqrt(fmax(C[4 * i], 0.0));
-    // U = A V S^-1 (columns); A is close to a rotation, so S is far from 0
-    for (int i = 0; i < 3; ++i) {
-      const double inv = sg[i] > 0.0 ? 1.0 / sg[i] : 0.0;
-      for (int r = 0; r < 3; ++r) {
-        double t = 0.0;
-        for (int k = 0; k < 3; ++k) t += comp(a[r], k) * Vm[3 * k + i];
-        Um[3 * r + i] = t * inv;
+    double row[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) row[j] = (j == r) ? 1.0 : 0.0;
+    if (live) {
+      const double* m = mass10 + 10 * b;
+      const double W[4][4] = {{m[0], m[1], m[2], m[3]}, {m[1], m[4], m[5], m[6]}, {m[2], m[5], m[7], m[8]},
+                              {m[3], m[6], m[8], m[9]}};
+      double A[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A[i][c] = q[12 * b + 3 + 3 * i + c];
+      const double kv4 = 4.0 * kappa_b[b] * vol[b], dt2 = dt * dt;
+      // q index j: translation component j (< 3), else A[(j-3)/3][(j-3)%3]
+      const int cr = r < 3 ? r : (r - 3) / 3, ur = r < 3 ? 0 : 1 + (r - 3) % 3;
+#pragma unroll
+      for (int j = 0; j < 12; ++j) {
+        const int cj = j < 3 ? j : (j - 3) / 3, uj = j < 3 ? 0 : 1 + (j - 3) % 3;
+        double v = cr == cj ? W[ur][uj] : 0.0;
+        if (r >= 3 && j >= 3) {
+          const int k = cr, ck = ur - 1, l = cj, cl = uj - 1;
+          double h = A[l][ck] * A[k][cl];
+          if (ck == cl) h += A[k][0] * A[l][0] + A[k][1] * A[l][1] + A[k][2] * A[l][2] - (k == l ? 1.0 : 0.0);
+          if (k == l) h += A[0][ck] * A[0][cl] + A[1][ck] * A[1][cl] + A[2][ck] * A[2][cl];
+          v += dt2 * kv4 * h;
+        }
+        row[j] = v;
       }
     }
-    for (int k = 0; k < 81; ++k) A9[k] = 0.0;
-    // modes: (i, j, sign) with i == j the scaling modes
-    const int mi[9] = {0, 1, 2, 0, 0, 0, 0, 1, 1}, mj[9] = {0, 1, 2, 1, 1, 2, 2, 2, 2};
-    const double ms[9] = {0, 0, 0, 1, -1, 1, -1, 1, -1};
-    for (int m = 0; m < 9; ++m) {
-      const int i = mi[m], j = mj[m];
-      double lam;
-      if (i == j) lam = kv * (12.0 * sg[i] * sg[i] - 4.0);
-      else lam = 4.0 * kv * (sg[i] * sg[i] + ms[m] * sg[i] * sg[j] + sg[j] * sg[j] - 1.0);
-      if (!(lam > 0.0)) continue;
-      // W = U X V^T: W[r][c] = (U_ri V_cj + sign U_rj V_ci) / sqrt2 (or U_ri V_ci)
-      double w[9];
-      const double nrm = i == j ? 1.0 : 0.70710678118654752440;
-      for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c)
-          w[3 * r + c] = i == j ? Um[3 * r + i] * Vm[3 * c + i]
-                                : nrm * (Um[3 * r + i] * Vm[3 * c + j] + ms[m] * Um[3 * r + j] * Vm[3 * c + i]);
-      for (int r = 0; r < 9; ++r)
-        for (int c = 0; c < 9; ++c) A9[9 * r + c] += lam * w[r] * w[c];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      Bs[bl][r][j] = row[j];
+      L[bl][r][j] = row[j];
     }
   }
-  double* D = Db + 144 * b;
-  for (int k = 0; k < 144; ++k) D[k] = 0.0;
-  for (int c = 0; c < 3; ++c)
-    for (int u = 0; u < 4; ++u)
-      for (int v = 0; v < 4; ++v) D[12 * dof(u, c) + dof(v, c)] = W[u][v];
-  for (int i = 0; i < 9; ++i)
-    for (int j = 0; j < 9; ++j) D[12 * (3 + i) + 3 + j] += dt2 * A9[9 * i + j];
+  __syncthreads();
+  // Cholesky test (left-looking, one column per step)
+  for (int j = 0; j < 12; ++j) {
+    double t = 0.0;
+    if (r >= j) {
+      t = L[bl][r][j];
+      for (int k = 0; k < j; ++k) t -= L[bl][r][k] * L[bl][j][k];
+    }
+    if (r == j) {
+      if (!(t > 0.0)) bad[bl] = 1;
+      const double ri = rsqrt(t);
+      L[bl][j][j] = t * ri;
+      rd[bl][j] = ri;
+    }
+    __syncthreads();
+    if (r > j) L[bl][r][j] = t * rd[bl][j];
+    __syncthreads();
+  }
+  if (live && bad[bl] && r == 0) {
+    // not positive definite: PSD projection of the whole block (rare)
+    double Ab[144], V[144];
+    for (int i = 0; i < 12; ++i)
+      for (int j = 0; j < 12; ++j) Ab[12 * i + j] = Bs[bl][i][j];
+    jacobi_eig<12, double>(Ab, V);
+    for (int i = 0; i < 12; ++i)
+      for (int j = 0; j < 12; ++j) {
+        double t = 0.0;
+        for (int k = 0; k < 12; ++k) {
+          const double lam = Ab[13 * k];
+          if (lam > 0.0) t += V[12 * i + k] * lam * V[12 * j + k];
+        }
+        Bs[bl][i][j] = t;
+      }
+  }
+  __syncthreads();
+  const long base = (long)blockIdx.x * kHessBodies * 144, lim = 144L * nb;
+  for (int k = threadIdx.x; k < kHessBodies * 144; k += kHessThreads) {
+    const int bb = k / 144, e = k - 144 * (k / 144);
+    if (base + k < lim) Db[base + k] = Bs[bb][e / 12][e % 12];
+  }
 }
 
 // diagonal blocks and gradient: body terms plus the body's share of each of
@@ -745,13 +866,14 @@ __global__ void k_gather(int nb, const uint8_t* is_static, const int* rowoff, co
   }
 }
 
-// block-Jacobi preconditioner: inverse of each dynamic diagonal block.
-// Twelve threads per body (one matrix row each), sixteen bodies per block:
-// the blocks are staged through shared memory with coalesced loads and
-// stores, factored by a left-looking Cholesky (one column per step, the
-// reciprocal of its diagonal formed once), and thread c then solves
-// L L^T x = e_c for column c of the inverse with the triangular loops fully
-// unrolled so the solution stays in registers.
+// block-Jacobi preconditioner: Cholesky factor L of each dynamic diagonal
+// block, stored per body as 144 doubles with L below the diagonal (row-major)
+// and 1 / L_ii on it; the solver applies (L L^T)^-1 by forward and back
+// substitution (chol_apply).  Twelve threads per body (one matrix row each),
+// sixteen bodies per block, staged through shared memory with coalesced loads
+// and stores; left-looking, one column per step.  A block that is not
+// positive definite falls back to its diagonal (flagged).  Static bodies get
+// a zero factor (their rows stay zero).
 constexpr int kPreBodies = 16, kPreThreads = 12 * kPreBodies;
 
 __global__ void __launch_bounds__(kPreThreads) k_precond(int nb, const uint8_t* is_static, const double* D,
@@ -775,44 +897,49 @@ __global__ void __launch_bounds__(kPreThreads) k_precond(int nb, const uint8_t* 
       for (int k = 0; k < j; ++k) t -= A[bl][r][k] * A[bl][j][k];
     }
     if (r == j) {
-      if (!(t > 0.0)) bad[bl] = 1;  // not positive definite: diagonal fallback below
-      const double d = sqrt(t);
-      A[bl][j][j] = d;
-      rd[bl][j] = 1.0 / d;
+      if (!(t > 0.0)) bad[bl] = 1;  // not positive definite
+      const double ri = rsqrt(t);
+      A[bl][j][j] = t * ri;
+      rd[bl][j] = ri;
     }
     __syncthreads();
     if (r > j) A[bl][r][j] = t * rd[bl][j];
     __syncthreads();
   }
-  // column c = r of (L L^T)^-1: forward L y = e_c (y_i = 0 for i < c), then
-  // back L^T x = y
-  const int c = r;
-  double y[12], x[12];
+  const bool live = b < nb && !is_static[b];
+  const bool fallback = live && bad[bl];
+  // row r of the stored factor
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    double v = 0.0;
+    if (live && !fallback) v = k < r ? A[bl][r][k] : (k == r ? rd[bl][r] : 0.0);
+    if (fallback && k == r) v = rsqrt(fabs(D[144L * b + 13 * r]));
+    A[bl][r][k] = v;  // each thread rewrites only its own row
+  }
+  if (fallback && r == 0) set_flag(st, ST_PCG_BREAKDOWN);
+  __syncthreads();
+  for (int k = threadIdx.x; k < kPreBodies * 144; k += kPreThreads) {
+    const int bb = k / 144, e = k - 144 * (k / 144);
+    if (base + k < lim) Pinv[base + k] = A[bb][e / 12][e % 12];
+  }
+}
+
+// z = (L L^T)^-1 r for one body from its stored factor F (see k_precond)
+__device__ __forceinline__ void chol_apply(const double* __restrict__ F, const double* rb, double* z) {
+  double y[12];
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
-    double t = (i == c) ? 1.0 : 0.0;
+    double t = rb[i];
 #pragma unroll
-    for (int k = 0; k < i; ++k) t -= A[bl][i][k] * y[k];
-    y[i] = (i < c) ? 0.0 : t * rd[bl][i];
+    for (int k = 0; k < i; ++k) t -= F[12 * i + k] * y[k];
+    y[i] = t * F[13 * i];
   }
 #pragma unroll
   for (int i = 11; i >= 0; --i) {
     double t = y[i];
 #pragma unroll
-    for (int k = i + 1; k < 12; ++k) t -= A[bl][k][i] * x[k];
-    x[i] = t * rd[bl][i];
-  }
-  __syncthreads();  // every solve has read L
-  const bool live = b < nb && !is_static[b];
-  const bool fallback = live && bad[bl];
-#pragma unroll
-  for (int i = 0; i < 12; ++i) A[bl][i][c] = !live ? 0.0 : (fallback ? 0.0 : x[i]);
-  if (fallback) A[bl][c][c] = 1.0 / fabs(D[144L * b + 13 * c]);
-  if (fallback && c == 0) set_flag(st, ST_PCG_BREAKDOWN);
-  __syncthreads();
-  for (int k = threadIdx.x; k < kPreBodies * 144; k += kPreThreads) {
-    const int bb = k / 144, e = k - 144 * (k / 144);
-    if (base + k < lim) Pinv[base + k] = A[bb][e / 12][e % 12];
+    for (int k = i + 1; k < 12; ++k) t -= F[12 * k + i] * z[k];
+    z[i] = t * F[13 * i];
   }
 }
 
@@ -893,7 +1020,8 @@ __global__ void k_pcg_alpha(const double* part, int n, DevStatus* st) {
   }
 }
 
-// x += alpha p; r -= alpha Ap; z = Pinv r; partial sums of r.z and r.r
+// x += alpha p; r -= alpha Ap; z = (L L^T)^-1 r from the stored block factors;
+// partial sums of r.z and r.r
 __global__ void k_pcg_update(int nb, const uint8_t* is_static, const double* Pinv, const double* pv,
                              const double* Ap, double* x, double* r, double* z, double* part, const DevStatus* cst) {
   __shared__ double red[2][128];
@@ -909,12 +1037,12 @@ __global__ void k_pcg_update(int nb, const uint8_t* is_static, const double* Pin
       r[12 * b + k] = rb[k];
       rr += rb[k] * rb[k];
     }
-    const double* Pi = Pinv + 144 * b;
+    double zb[12];
+    chol_apply(Pinv + 144 * b, rb, zb);
+#pragma unroll
     for (int i = 0; i < 12; ++i) {
-      double s = 0.0;
-      for (int j = 0; j < 12; ++j) s += Pi[12 * i + j] * rb[j];
-      z[12 * b + i] = s;
-      rz += rb[i] * s;
+      z[12 * b + i] = zb[i];
+      rz += rb[i] * zb[i];
     }
   }
   red[0][threadIdx.x] = rz;
@@ -968,7 +1096,7 @@ __global__ void k_pcg_dir(long n, const double* z, double* pv, const DevStatus* 
     pv[i] = z[i] + beta * pv[i];
 }
 
-// r = rhs (dynamic rows), x = 0, z = Pinv r, p = z; partials of r.z and r.r
+// r = rhs (dynamic rows), x = 0, z = (L L^T)^-1 r, p = z; partials of r.z and r.r
 __global__ void k_pcg_init(int nb, const uint8_t* is_static, const double* Pinv, const double* rhs, double* x,
                            double* r, double* z, double* pv, double* part) {
   __shared__ double red[2][128];
@@ -983,13 +1111,13 @@ __global__ void k_pcg_init(int nb, const uint8_t* is_static, const double* Pinv,
       x[12 * b + k] = 0.0;
       rr += rb[k] * rb[k];
     }
-    const double* Pi = Pinv + 144 * b;
+    double zb[12];
+    chol_apply(Pinv + 144 * b, rb, zb);
+#pragma unroll
     for (int i = 0; i < 12; ++i) {
-      double s = 0.0;
-      for (int j = 0; j < 12; ++j) s += Pi[12 * i + j] * rb[j];
-      z[12 * b + i] = s;
-      pv[12 * b + i] = s;
-      rz += rb[i] * s;
+      z[12 * b + i] = zb[i];
+      pv[12 * b + i] = zb[i];
+      rz += rb[i] * zb[i];
     }
   }
   red[0][threadIdx.x] = rz;
@@ -1054,15 +1182,18 @@ __global__ void k_reduce(const double* v, long stride, const int* n_dev, long n_
 
 // the four energy components in one launch (block k reduces component k)
 __global__ void k_energies(const double* Eb, int nb, const double* bar, long bar_stride, const int* nbar,
-                           const double* fterm, const int* nfr, DevStatus* st) {
+                           int nbar_mul, const double* fterm, const int* nfr, DevStatus* st) {
   if (blockIdx.x == 0) block_reduce_to(Eb, 2, nb, &st->energy[1]);
   else if (blockIdx.x == 1) block_reduce_to(Eb + 1, 2, nb, &st->energy[2]);
-  else if (blockIdx.x == 2) block_reduce_to(bar, bar_stride, *nbar, &st->energy[3]);
+  else if (blockIdx.x == 2) block_reduce_to(bar, bar_stride, (long)*nbar * nbar_mul, &st->energy[3]);
   else block_reduce_to(fterm, kTermStride, *nfr, &st->energy[4]);
 }
 
-__global__ void k_energy_sum(DevStatus* st) {
+// total energy; keep != 0 also stores it in energy[5] (the reference value of
+// the line search, which later energy-only passes do not overwrite)
+__global__ void k_energy_sum(DevStatus* st, int keep) {
   st->energy[0] = ((st->energy[1] + st->energy[2]) + st->energy[3]) + st->energy[4];
+  if (keep) st->energy[5] = st->energy[0];
 }
 
 __global__ void k_max_step(int nv, const int* vbody, const uint8_t* is_static, const double4* dx, DevStatus* st) {
@@ -1159,9 +1290,13 @@ void launch_body_pairs(Scene& s) {
   cudaMemsetAsync(s.slot_cnt.p, 0, sizeof(int) * s.hash_T, s.stream);
   k_hash_slots<<<nbk, 128, 0, s.stream>>>(s.nb, s.bbox.p, s.large.p, s.prm.dhat, inv_h, mask, s.slot_cnt.p,
                                           s.slot_off.p, s.entries.p, (long)s.entries.cap, false);
-  counted(s, 3);
-  k_scan<<<1, 1024, 0, s.stream>>>(s.slot_cnt.p, s.slot_off.p, nullptr, s.hash_T, &s.st->pad2[0],
-                                   (long)s.entries.cap, ST_CAP_HASH, &s.st->need_misc, s.st);
+  counted(s, 4);
+  {
+    const int tiles = (s.hash_T + kScanTile - 1) / kScanTile;
+    k_scan_tiles<<<tiles, 1024, 0, s.stream>>>(s.slot_cnt.p, s.hash_T, s.scan_part.p);
+    k_scan_apply<<<tiles, 1024, 0, s.stream>>>(s.slot_cnt.p, s.slot_off.p, s.hash_T, s.scan_part.p, &s.st->pad2[0],
+                                               (long)s.entries.cap, ST_CAP_HASH, &s.st->need_misc, s.st);
+  }
   cudaMemsetAsync(s.slot_cnt.p, 0, sizeof(int) * s.hash_T, s.stream);
   k_hash_slots<<<nbk, 128, 0, s.stream>>>(s.nb, s.bbox.p, s.large.p, s.prm.dhat, inv_h, mask, s.slot_cnt.p,
                                           s.slot_off.p, s.entries.p, (long)s.entries.cap, true);
@@ -1220,7 +1355,12 @@ void launch_body_terms(Scene& s, const double* q, bool hess) {
   counted(s);
   ProfScope pb(s, PF_BODY);
   k_body_terms<<<blocks(s.nb, 64), 64, 0, s.stream>>>(s.nb, s.is_static.p, q, s.qtilde.p, s.mass10.p, s.vol.p,
-                                                       s.kappa_b.p, s.prm.dt, hess, s.Db.p, s.gb.p, s.Eb.p);
+                                                       s.kappa_b.p, s.prm.dt, s.gb.p, s.Eb.p);
+  if (hess) {
+    counted(s);
+    k_body_hess<<<blocks(s.nb, kHessBodies), kHessThreads, 0, s.stream>>>(s.nb, s.is_static.p, q, s.mass10.p,
+                                                                          s.vol.p, s.kappa_b.p, s.prm.dt, s.Db.p);
+  }
 }
 
 void launch_gather(Scene& s) {
@@ -1239,10 +1379,12 @@ void launch_precond(Scene& s) {
 void launch_energy_total(Scene& s, bool from_terms) {
   counted(s, 2);
   if (from_terms)
-    k_energies<<<4, 1024, 0, s.stream>>>(s.Eb.p, s.nb, s.term.p, kTermStride, &s.st->nact, s.fterm.p, &s.st->nfr, s.st);
+    k_energies<<<4, 1024, 0, s.stream>>>(s.Eb.p, s.nb, s.term.p, kTermStride, &s.st->nact, 1, s.fterm.p, &s.st->nfr,
+                                         s.st);
   else
-    k_energies<<<4, 1024, 0, s.stream>>>(s.Eb.p, s.nb, s.Epair.p, 1, &s.st->np, s.fterm.p, &s.st->nfr, s.st);
-  k_energy_sum<<<1, 1, 0, s.stream>>>(s.st);
+    k_energies<<<4, 1024, 0, s.stream>>>(s.Eb.p, s.nb, s.Epair.p, 1, &s.st->np, energy_chunks(s), s.fterm.p,
+                                         &s.st->nfr, s.st);
+  k_energy_sum<<<1, 1, 0, s.stream>>>(s.st, from_terms ? 1 : 0);
 }
 
 int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res) {

@@ -40,6 +40,7 @@ def main():
         out["kernels"] = {k: {"launches": v["launches"], "ms": round(v["total_ms"], 4),
                               "tflops": round(v["flops"] / (v["total_ms"] * 1e-3) / 1e12, 4) if v["total_ms"] > 0 and v["flops"] else None}
                           for k, v in g.profile().items() if v["launches"]}
+        out["counters"] = g.counters()
     print(out)
 
 

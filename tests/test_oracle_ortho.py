@@ -82,3 +82,73 @@ def test_hessian_at_identity_has_six_zero_modes():
     assert w.min() > -1e-12
     w9 = np.linalg.eigvalsh(H[3:, 3:])
     assert (np.abs(w9) < 1e-12).sum() == 3
+
+
+def test_hessian_matches_hand_derived_closed_form():
+    """d2V/da_k da_l = 4 kappa nu [(a_k.a_l - delta_kl) I + delta_kl A^T A + a_l a_k^T],
+    derived by hand from V = kappa nu sum_ij (a_i.a_j - delta_ij)^2 (rows a_i of A),
+    against the oracle's jets"""
+    rng = np.random.default_rng(11)
+    for _ in range(10):
+        q = rng.normal(size=12)
+        kap, vol = 1e3 * rng.uniform(1, 2), rng.uniform(0.1, 1.0)
+        _, _, H = O.ortho(q, kap, vol)
+        A = q[3:].reshape(3, 3)
+        G, ATA = A @ A.T, A.T @ A
+        Hc = np.zeros((12, 12))
+        for k in range(3):
+            for l in range(3):
+                blk = (G[k, l] - (k == l)) * np.eye(3) + (k == l) * ATA + np.outer(A[l], A[k])
+                Hc[3 + 3 * k:6 + 3 * k, 3 + 3 * l:6 + 3 * l] = 4 * kap * vol * blk
+        np.testing.assert_allclose(H, Hc, rtol=0, atol=1e-13 * np.abs(H).max())
+
+
+def test_body_block_is_unprojected_when_positive_definite():
+    """the body block of the assembled Hessian is M + dt^2 hess V exactly when
+    that block is positive definite (it is projected only when Cholesky fails)"""
+    s = scenes.cube_stack(n=2)
+    o = O.Oracle(s)
+    q = s.q0.reshape(-1).copy()
+    for b in range(s.nb):
+        if not s.is_static[b]:
+            # slight compression: the rotation modes of hess V turn negative
+            # (4 kappa nu (s^2 - 1) < 0) while M still dominates them
+            q[12 * b + 3:12 * b + 12] *= 1.0 - 1e-5
+    st, E, g = o.energy_grad_hess(q)
+    diag, _, _ = o.hessian()
+    dt = s.params["dt"]
+    for b in range(s.nb):
+        if s.is_static[b]:
+            continue
+        vol = o.moments(b)[0]
+        _, _, Hv = O.ortho(q[12 * b:12 * b + 12], s.kappa_body[b], vol)
+        assert np.linalg.eigvalsh(Hv[3:, 3:]).min() < 0  # the 9x9 part alone is indefinite
+        B = o.mass_matrix(b) + dt * dt * Hv
+        assert np.linalg.eigvalsh(B).min() > 0
+        np.testing.assert_allclose(diag[b], B, rtol=0, atol=1e-12 * np.abs(B).max())
+
+
+def test_body_block_is_projected_when_indefinite():
+    """strong compression makes M + dt^2 hess V indefinite: the assembled body
+    block is then its eigenvalue clamp (numpy's eigh as the reference)"""
+    s = scenes.cube_stack(n=2)
+    o = O.Oracle(s)
+    q = s.q0.reshape(-1).copy()
+    for b in range(s.nb):
+        if not s.is_static[b]:
+            q[12 * b + 3:12 * b + 12] *= 0.95
+    o.energy_grad_hess(q)
+    diag, _, _ = o.hessian()
+    dt = s.params["dt"]
+    n_proj = 0
+    for b in range(s.nb):
+        if s.is_static[b]:
+            continue
+        _, _, Hv = O.ortho(q[12 * b:12 * b + 12], s.kappa_body[b], o.moments(b)[0])
+        B = o.mass_matrix(b) + dt * dt * Hv
+        w, V = np.linalg.eigh(B)
+        if w.min() > 0:
+            continue
+        n_proj += 1
+        np.testing.assert_allclose(diag[b], (V * np.maximum(w, 0)) @ V.T, rtol=0, atol=1e-10 * np.abs(B).max())
+    assert n_proj > 0
