@@ -393,16 +393,16 @@ def random_pair(seed: int, kinds=("cube", "ico1"), sep: float = 0.0005, **params
     return B.build(params)
 
 
-CONFIGS = {
-    0: lambda **kw: packed_cubes(**kw),
-    1: lambda **kw: cube_stack(**kw),
-    2: lambda **kw: ico_bowl(**kw),
-    3: lambda **kw: lattice_pile(**kw),
-    4: lambda **kw: throw_stack(**kw),
+RECIPES = {
+    "packed_cubes": packed_cubes,
+    "cube_stack": cube_stack,
+    "ico_bowl": ico_bowl,
+    "lattice_pile": lattice_pile,
+    "throw_stack": throw_stack,
 }
 
 
-def make_scene(config: int, **kw) -> Scene:
-    """Scene of workload ``config`` (1 cube stack, 2 icospheres in a bowl,
-    3 lattice pile, 4 throw into a stack); keyword arguments shrink it."""
-    return CONFIGS[config](**kw)
+def make_scene(name: str, **kw) -> Scene:
+    """Scene of the named recipe (packed_cubes, cube_stack, ico_bowl,
+    lattice_pile, throw_stack); keyword arguments shrink it."""
+    return RECIPES[name](**kw)
