@@ -122,6 +122,17 @@ def oracle_sample(start_step, warmup, steps, dims=(6, 6, 3)):
             "seconds": dt}
 
 
+def vertices(s, q):
+    """world vertex positions x = A xbar + p for body states q (nb, 12)"""
+    q = np.asarray(q).reshape(-1, 12)
+    A = q[s.vbody, 3:].reshape(-1, 3, 3)
+    return np.einsum("vij,vj->vi", A, s.xbar) + q[s.vbody, :3]
+
+
+def bbox_diag(x):
+    return float(np.linalg.norm(x.max(axis=0) - x.min(axis=0)))
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -208,6 +219,35 @@ def run_abd(args, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    # ---- mixed precision (precision = 1): the same steps from the same state;
+    # the end state is compared with the FP64 run's (the e2e pass above)
+    mixed = None
+    if not args.no_mixed:
+        gm = AbdScene(s, device=dev, precision=1)
+        gm.set_state(q0, qd0)
+        gm.step(1)  # buffer growth outside the timed steps
+        gm.set_state(q0, qd0)
+        torch.cuda.synchronize()
+        ms_m, st_m = [], []
+        for k in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st_m.append(gm.step(1))
+            e1.record()
+            torch.cuda.synchronize()
+            ms_m.append(e0.elapsed_time(e1))
+        qm, _ = gm.get_state()
+        xm = vertices(s, qm.cpu().numpy())
+        x64 = vertices(s, qh.numpy())
+        L = bbox_diag(vertices(s, q0.cpu().numpy()))
+        mixed = {"value": sum(ms_m) / len(ms_m), "unit": "ms/step",
+                 "newton_iters_per_step": sum(st["newton_iters"] for st in st_m) / len(st_m),
+                 "max_vertex_deviation_vs_fp64_over_lbbox": float(np.abs(xm - x64).max() / L),
+                 "precision": "FP32 eigenbasis for the barrier Hessian projection; distances, barrier, "
+                              "energies, gradients, CCD, Newton test and line search FP64"}
+        gm.close()
+
     steps_total = args.steps * world
     ms_per_step = total_ms / steps_total
     newton = sum(st["newton_iters"] for st in stats)
@@ -256,6 +296,7 @@ def run_abd(args, rank, world):
         "roofline": roof,
         "kernel_ms": {k: round(v["total_ms"], 3) for k, v in prof.items()},
         "barrier_counters": cnt,
+        "mixed": mixed,
         "clocks": clocks,
     }
     return out
@@ -269,6 +310,7 @@ def main():
     ap.add_argument("--start-step", type=int, default=20)
     ap.add_argument("--impl", default="abd", choices=["abd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision run")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

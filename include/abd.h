@@ -86,7 +86,14 @@ typedef struct {
   double ls_slack_rel;  /* line search accepts E <= E0 + ls_slack_rel (|E0| + 1) */
   double ccd_s;         /* ACCD gap fraction s (the step keeps >= s of each pair's distance) */
   int newton_max, pcg_max, ls_max, ccd_max;
-  int precision;        /* 0: FP64 */
+  int precision;        /* 0: FP64 throughout.  1: mixed - the PSD projection of the
+                           6- and 9-dimensional barrier Hessians is taken from an
+                           FP32 eigenbasis without FP64 refinement (distances,
+                           barrier values and logs, energies, gradients, CCD, the
+                           Newton test and the line search stay FP64); when a
+                           step passes the Newton test, the test is repeated at
+                           the same iterate with the FP64-refined projection, so
+                           both modes stop on the same criterion */
 } abd_params;
 
 /* Scene description (host arrays, copied).  Vertices, triangles and edges

@@ -318,6 +318,11 @@ int orc_pair_barrier(int kind, const double x[12], double dhat, double kappa, do
   if (!(d2 < dhat * dhat)) return 0;
   static jet s, d, t, t2, l, b;  /* large structs: static to keep the stack small */
   orc_jet_pair_d2(&s, kind, type, x);
+  /* the barrier is a function of the distance; its value is the canonical
+   * d^2 (the one that decides membership), its derivatives those of the
+   * type's formula (near d-hat, B ~ (d - dhat)^2 amplifies any difference in
+   * d by dhat / (dhat - d)) */
+  s.v = d2;
   jet_sqrt(&d, &s);
   jet_add_const(&t, &d, -dhat);
   jet_sq(&t2, &t);
@@ -336,6 +341,7 @@ int orc_pair_barrier(int kind, const double x[12], double dhat, double kappa, do
       jet3_sub(&e1, &v[3], &v[2]);
       jet3_cross(&n, &e0, &e1);
       jet3_dot(&cj, &n, &n);
+      cj.v = c; /* canonical value, as for d^2 */
       double dm, d2m;
       double mv = orc_ee_mollifier(cj.v, eps_x, &dm, &d2m);
       jet_chain(&mj, &cj, mv, dm, d2m);

@@ -83,6 +83,7 @@ void size_term_buffers(Scene& s, size_t tcap) {
   grow(s, s.termv, tcap);
   grow(s, s.tmeta, tcap);
   grow(s, s.teps, tcap);
+  grow(s, s.td2, tcap);
   grow(s, s.tlist, 3 * tcap);
   grow(s, s.fric, tcap);
   grow(s, s.fterm, tcap * kTermStride);
@@ -260,7 +261,12 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
   s.cand_last = (long)s.st_host->n_cand;
   s.last_np = s.st_host->np;
   abd_status status = ABD_ERR_NEWTON_MAXITER;
+  // mixed precision iterates with the FP32-basis projection; once its step
+  // passes the convergence test, the test is repeated with the FP64-refined
+  // projection at the same iterate, so both modes stop on the same criterion
+  bool hp = s.prm.precision == 0;
   for (int it = 0; it < s.prm.newton_max; ++it) {
+    s.fp32_proj = !hp;
     launch_transform(s, s.q.p, s.x.p);
     eval_system(s, s.q.p, 1);
     // Newton direction: H dq = -g, enqueued behind the system without a host
@@ -307,8 +313,14 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
       return ABD_ERR_NONFINITE;
     }
     if (step <= s.newton_tol) {
-      status = ABD_OK;
-      break;
+      if (hp) {
+        status = ABD_OK;
+        break;
+      }
+      hp = true;  // verify with the FP64-refined projection (the swept set covers x)
+      s.cand_last = (long)s.st_host->n_cand;
+      s.last_np = s.st_host->np;
+      continue;
     }
     loc.newton_iters++;
     s.cand_last = (long)s.st_host->n_cand;
@@ -412,7 +424,7 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
       (d->ne && !d->edge))
     return ABD_ERR_INVALID_ARG;
   if (!(prm->dt > 0) || !(prm->dhat > 0) || !(prm->kappa > 0) || prm->newton_max <= 0 || prm->pcg_max <= 0 ||
-      prm->ls_max < 0 || prm->ccd_max <= 0 || !(prm->ccd_s > 0 && prm->ccd_s < 1) || prm->precision != 0)
+      prm->ls_max < 0 || prm->ccd_max <= 0 || !(prm->ccd_s > 0 && prm->ccd_s < 1) || (prm->precision != 0 && prm->precision != 1))
     return ABD_ERR_INVALID_ARG;
   const int nb = d->nb, nv = d->nv, nt = d->nt, ne = d->ne;
   std::vector<int> vbeg, tbeg, ebeg, towner(nt), eowner(ne);
@@ -616,6 +628,7 @@ void abd_destroy(abd_scene* S) {
   release(s, s.termv);
   release(s, s.tmeta);
   release(s, s.teps);
+  release(s, s.td2);
   release(s, s.tlist);
   release(s, s.ftermv);
   release(s, s.fric);
@@ -662,6 +675,7 @@ abd_status abd_energy_grad_hess(abd_scene* S, const double* q_dev, double* E_hos
   abd_status r = with_capacity(s, [&]() {
     launch_transform(s, q_dev, s.x.p);
     broad_and_enumerate(s, false, false);
+    s.fp32_proj = s.prm.precision == 1;
     eval_system(s, q_dev, 1);
     return ABD_OK;
   });

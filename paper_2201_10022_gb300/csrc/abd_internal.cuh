@@ -125,6 +125,7 @@ struct Scene {
   abd_params prm{};
   int nb = 0, nv = 0, nt = 0, ne = 0, ndyn = 0;
   double newton_tol = 0;
+  bool fp32_proj = false;  // barrier projection from the FP32 eigenbasis (mixed precision)
   Alloc alloc;
   cudaStream_t stream = nullptr;
   std::string err;
@@ -167,6 +168,7 @@ struct Scene {
   Buf<int4> termv;
   Buf<int> tmeta;      // barrier terms: kind | type << 1 | mollified << 5
   Buf<double> teps;    // barrier terms: edge-edge mollifier threshold
+  Buf<double> td2;     // barrier terms: canonical squared distance
   Buf<int> tlist;      // barrier terms bucketed by working dimension 3, 6, 9 (3 x capacity)
   Buf<double> fterm;   // friction terms
   Buf<int4> ftermv;

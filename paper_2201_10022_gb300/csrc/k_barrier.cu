@@ -98,9 +98,10 @@ __device__ __forceinline__ int gram_class(int kind, int type, int moll) {
 // ---------------------------------------------------------------------------
 // classification: vertex ids, type / mollifier flag and bucket of every term
 // ---------------------------------------------------------------------------
-__global__ void k_bar_classify(const DevStatus* __restrict__ cst, const int* aoff, const int4* act, const int* tri,
-                               const int* edge, const double4* x, const double* l2e, int maxc, long cap, int4* termv,
-                               int* tmeta, double* teps, int* tlist, DevStatus* st) {
+__global__ void k_bar_classify(const DevStatus* __restrict__ cst, const int* aoff, const int4* act,
+                               const double* act_d2, const int* tri, const int* edge, const double4* x,
+                               const double* l2e, int maxc, long cap, int4* termv, int* tmeta, double* teps,
+                               double* td2, int* tlist, DevStatus* st) {
   const int lane = threadIdx.x & 31;
   const int np = cst->np;
   const long nact = min((long)cst->nact, cap);
@@ -110,7 +111,8 @@ __global__ void k_bar_classify(const DevStatus* __restrict__ cst, const int* aof
     int cls = -1;
     if (f < nact) {
       const int p = owner(aoff, np, (int)f);
-      const int4 r = act[(size_t)p * maxc + (f - aoff[p])];
+      const size_t slot = (size_t)p * maxc + (f - aoff[p]);
+      const int4 r = act[slot];
       const int kind = (unsigned)r.x >> 31, i = r.x & 0x7fffffff, type = r.z;
       int v[4];
       pair_vertices(kind, i, r.y, tri, edge, v);
@@ -127,6 +129,7 @@ __global__ void k_bar_classify(const DevStatus* __restrict__ cst, const int* aof
       termv[f] = make_int4(v[0], v[1], v[2], v[3]);
       tmeta[f] = kind | (type << 1) | (moll << 5);
       teps[f] = eps;
+      td2[f] = act_d2[slot];
     }
     for (int k = 0; k < 3; ++k) {
       const unsigned m = __ballot_sync(kAll, cls == k);
@@ -376,6 +379,7 @@ struct WarpScratch {
   float V32[2][81];
   double vec[6][9];  // gs, gD, gt, gr, gb, gc
   double Rm[9], Ri[9], C[12], A[9];
+  float Ri32[9];
   double rc[10], rs[10];
   float rc32[10], rs32[10];
 };
@@ -383,9 +387,9 @@ struct WarpScratch {
 // one 6- or 9-dimensional term by the whole warp
 template <int N>
 __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restrict__ termv,
-                          const int* __restrict__ tmeta, const double* __restrict__ teps, const double4* x,
-                          double dhat, double kappa, int project, const GramTables& gram, double* term,
-                          DevStatus* st) {
+                          const int* __restrict__ tmeta, const double* __restrict__ teps,
+                          const double* __restrict__ td2, const double4* x, double dhat, double kappa, int project,
+                          int mixed, const GramTables& gram, double* term, DevStatus* st) {
   constexpr int M = N / 3;
   const int4 vv = termv[f];
   const int meta = tmeta[f];
@@ -398,11 +402,14 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
   double *gs = W.vec[0], *gD = W.vec[1], *gt = W.vec[2], *gr = W.vec[3], *gb = W.vec[4], *gc = W.vec[5];
   TypeDist T;
   type_dist(Rt, T, gs, gD, gt, lane);
-  const double d = sqrt(T.s);
+  // the barrier's scalar factors at the canonical squared distance (the value
+  // that decides membership); the derivatives of s come from the type's form
+  const double sc = td2[f];
+  const double d = sqrt(sc);
   double B, B1, B2;
   barrier_derivs(d, dhat, B, B1, B2);
   const double cg = kappa * B1 / (2.0 * d);
-  const double ca = kappa * (B2 / (4.0 * T.s) - B1 / (4.0 * d * T.s));
+  const double ca = kappa * (B2 / (4.0 * sc) - B1 / (4.0 * d * sc));
   const double Eb = kappa * B;
   const int gcls = gram_class(kind, type, moll);
   if (lane == 0) {
@@ -414,6 +421,7 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
     for (int k = 0; k < 9; ++k) {
       W.Rm[k] = gcls == 1 ? gram.Rm[1][k] : (gcls == 2 ? gram.Rm[2][k] : gram.Rm[3][k]);
       W.Ri[k] = gcls == 1 ? gram.Ri[1][k] : (gcls == 2 ? gram.Ri[2][k] : gram.Ri[3][k]);
+      W.Ri32[k] = (float)W.Ri[k];
     }
   }
   __syncwarp();
@@ -522,6 +530,33 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
           cur ^= 1;
         }
       }
+      if (mixed) {
+        // mixed precision: the clamp from the FP32 eigenpairs and the
+        // back-transform in FP32, no FP64 refinement
+        const float* Kc = W.K32[cur];
+        const float* Vc = W.V32[cur];
+        float* Pf = W.K32[cur ^ 1];
+        for (int e = lane; e < N * N; e += 32) {
+          const int a = e / N, b = e - N * (e / N);
+          float t = 0.0f;
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const float lam = Kc[k * N + k];
+            if (lam > 0.0f) t += Vc[a * N + k] * lam * Vc[b * N + k];
+          }
+          Pf[e] = t;
+        }
+        __syncwarp();
+        for (int e = lane; e < N * N; e += 32) {
+          const int a = e / N, b = e - N * (e / N);
+          const int Ia = a / 3, i = a - 3 * Ia, Jb = b / 3, j = b - 3 * Jb;
+          float t = 0.0f;
+          for (int c = Ia; c < M; ++c)
+            for (int e2 = Jb; e2 < M; ++e2) t += W.Ri32[3 * Ia + c] * W.Ri32[3 * Jb + e2] * Pf[(3 * c + i) * N + 3 * e2 + j];
+          P[e] = (double)t * mx;
+        }
+        if (lane == 0) atomicAdd(&st->jac[0], (unsigned long long)n32);
+      } else {
       // FP64 refinement: V <- V (3I - V^T V) / 2, K' = V^T K V, FP64 sweeps
       double *V0 = W.Vd[0], *V1 = W.Vd[1], *S = W.H;
       for (int e = lane; e < N * N; e += 32) V0[e] = (double)W.V32[cur][e];
@@ -606,6 +641,7 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
           for (int e2 = Jb; e2 < M; ++e2) t += W.Ri[3 * Ia + c] * W.Ri[3 * Jb + e2] * Pk[(3 * c + i) * N + 3 * e2 + j];
         P[e] = t;
       }
+      }  // FP64 refinement
     } else {
       for (int e = lane; e < N * N; e += 32) P[e] = 0.0;
     }
@@ -648,7 +684,8 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
 
 // one point-point term by one thread (closed-form projection)
 __device__ __forceinline__ void pp_term(int f, const int4* __restrict__ termv, const int* __restrict__ tmeta,
-                                        const double4* x, double dhat, double kappa, int project, double* term) {
+                                        const double* __restrict__ td2, const double4* x, double dhat, double kappa,
+                                        int project, double* term) {
   const int4 vv = termv[f];
   const int meta = tmeta[f];
   const int kind = meta & 1, type = (meta >> 1) & 15;
@@ -656,11 +693,12 @@ __device__ __forceinline__ void pp_term(int f, const int4* __restrict__ termv, c
   Reduced R;
   reduce(kind, type, xs, R);
   const v3 e = R.r[0];
-  const double s = dot(e, e), d = sqrt(s);
+  const double s = dot(e, e);             // |e|^2 of the difference vector
+  const double sc = td2[f], d = sqrt(sc);  // the canonical distance, for the barrier's factors
   double B, B1, B2;
   barrier_derivs(d, dhat, B, B1, B2);
   const double cg = kappa * B1 / (2.0 * d);
-  const double ca = kappa * (B2 / (4.0 * s) - B1 / (4.0 * d * s));
+  const double ca = kappa * (B2 / (4.0 * sc) - B1 / (4.0 * d * sc));
   // H_r = h0 e e^T + h1 I
   double h0 = 4.0 * ca, h1 = 2.0 * cg;
   if (project) {
@@ -691,9 +729,10 @@ __device__ __forceinline__ void pp_term(int f, const int4* __restrict__ termv, c
 __global__ void __launch_bounds__(32 * kBarWarps) k_barrier(const DevStatus* __restrict__ cst, const int* tlist, long cap,
                                                             const int4* __restrict__ termv,
                                                             const int* __restrict__ tmeta,
-                                                            const double* __restrict__ teps, const double4* x,
-                                                            double dhat, double kappa, int project, GramTables gram,
-                                                            double* term, DevStatus* st) {
+                                                            const double* __restrict__ teps,
+                                                            const double* __restrict__ td2, const double4* x,
+                                                            double dhat, double kappa, int project, int mixed,
+                                                            GramTables gram, double* term, DevStatus* st) {
   __shared__ WarpScratch scratch[kBarWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpScratch& W = scratch[warp];
@@ -705,13 +744,15 @@ __global__ void __launch_bounds__(32 * kBarWarps) k_barrier(const DevStatus* __r
   // point-point terms 32 to a warp
   for (long t = (long)blockIdx.x * kBarWarps + warp; t < total; t += nwarps) {
     if (t < n9) {
-      warp_term<9>(tlist[2 * cap + t], lane, W, termv, tmeta, teps, x, dhat, kappa, project, gram, term, st);
+      warp_term<9>(tlist[2 * cap + t], lane, W, termv, tmeta, teps, td2, x, dhat, kappa, project, mixed, gram, term,
+                   st);
     } else if (t < n9 + n6) {
-      warp_term<6>(tlist[cap + (t - n9)], lane, W, termv, tmeta, teps, x, dhat, kappa, project, gram, term, st);
+      warp_term<6>(tlist[cap + (t - n9)], lane, W, termv, tmeta, teps, td2, x, dhat, kappa, project, mixed, gram,
+                   term, st);
     } else {
       const long k = (t - n9 - n6) * 32 + lane;
       const bool ok = k < n3;
-      if (ok) pp_term(tlist[k], termv, tmeta, x, dhat, kappa, project, term);
+      if (ok) pp_term(tlist[k], termv, tmeta, td2, x, dhat, kappa, project, term);
       const unsigned m = __ballot_sync(kAll, ok);
       if (lane == 0) atomicAdd(&st->bar_terms[1], (unsigned long long)__popc(m));
     }
@@ -725,10 +766,13 @@ void launch_barrier(Scene& s, int project, long cap) {
   counted(s, 2);
   ProfScope ps(s, PF_BARRIER);
   cudaMemsetAsync(reinterpret_cast<char*>(s.st) + offsetof(DevStatus, bar_cnt), 0, sizeof(int) * 4, s.stream);
-  k_bar_classify<<<152 * 8, 256, 0, s.stream>>>(s.st, s.aoff.p, s.act.p, s.tri.p, s.edge.p, s.x.p, s.l2e.p, s.maxc,
-                                                cap, s.termv.p, s.tmeta.p, s.teps.p, s.tlist.p, s.st);
-  k_barrier<<<152 * 8, 32 * kBarWarps, 0, s.stream>>>(s.st, s.tlist.p, cap, s.termv.p, s.tmeta.p, s.teps.p, s.x.p,
-                                                      s.prm.dhat, s.prm.kappa, project, gram, s.term.p, s.st);
+  k_bar_classify<<<152 * 8, 256, 0, s.stream>>>(s.st, s.aoff.p, s.act.p, s.act_d2.p, s.tri.p, s.edge.p, s.x.p,
+                                                s.l2e.p, s.maxc, cap, s.termv.p, s.tmeta.p, s.teps.p, s.td2.p,
+                                                s.tlist.p, s.st);
+  k_barrier<<<152 * 8, 32 * kBarWarps, 0, s.stream>>>(s.st, s.tlist.p, cap, s.termv.p, s.tmeta.p, s.teps.p, s.td2.p,
+                                                      s.x.p,
+                                                      s.prm.dhat, s.prm.kappa, project, s.fp32_proj ? 1 : 0,
+                                                      gram, s.term.p, s.st);
 }
 
 }  // namespace abd
