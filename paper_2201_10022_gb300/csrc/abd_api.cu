@@ -49,6 +49,7 @@ void grow(Scene& s, Buf<T>& b, size_t n) {
   }
   b.p = (T*)s.alloc.get(sizeof(T) * (n ? n : 1));
   b.cap = n;
+  ++s.gen;
   if (!b.p) throw OomError{};
 }
 
@@ -57,6 +58,7 @@ void release(Scene& s, Buf<T>& b) {
   s.alloc.put(b.p);
   b.p = nullptr;
   b.cap = 0;
+  ++s.gen;
 }
 
 // buffers whose size follows the body-pair capacity, the candidates per pair
@@ -248,6 +250,52 @@ abd_status with_capacity(Scene& s, F fn) {
 // candidates of the enumeration that produced the current candidate set
 long cand_total(Scene& s) { return s.cand_last; }
 
+// Run a fixed launch sequence: as a CUDA graph (captured on a private stream
+// the first time and after any buffer reallocation, then replayed on the
+// scene's stream), or directly while profiling or if capture is unavailable.
+// The sequence must not read device results on the host.
+template <typename F>
+void run_segment(Scene& s, Scene::Segment& g, F body) {
+  if (!s.graphs || s.prof.on) {
+    body();
+    return;
+  }
+  if (!g.exec || g.gen != s.gen) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    if (!s.cap_stream && cudaStreamCreateWithFlags(&s.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      s.graphs = false;
+      body();
+      return;
+    }
+    cudaStream_t user = s.stream;
+    const long n0 = s.nlaunch;
+    cudaGraph_t gr = nullptr;
+    bool ok = cudaStreamBeginCapture(s.cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      s.stream = s.cap_stream;
+      body();
+      s.stream = user;
+      ok = cudaStreamEndCapture(s.cap_stream, &gr) == cudaSuccess && gr;
+    }
+    g.nlaunch = s.nlaunch - n0;
+    s.nlaunch = n0;
+    if (ok) ok = cudaGraphInstantiate(&g.exec, gr, 0) == cudaSuccess;
+    if (gr) cudaGraphDestroy(gr);
+    if (!ok) {  // nothing of the captured body ran: run it directly from now on
+      cudaGetLastError();
+      g.exec = nullptr;
+      s.graphs = false;
+      body();
+      return;
+    }
+    g.gen = s.gen;
+  }
+  cudaGraphLaunch(g.exec, s.stream);
+  s.nlaunch += g.nlaunch;
+}
+
 // one implicit-Euler step from (q^t, qdot^t); on error the state is unchanged
 abd_status newton_step(Scene& s, abd_step_stats* stats) {
   const size_t qb = sizeof(double) * 12 * s.nb;
@@ -267,16 +315,22 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
   bool hp = s.prm.precision == 0;
   for (int it = 0; it < s.prm.newton_max; ++it) {
     s.fp32_proj = !hp;
-    launch_transform(s, s.q.p, s.x.p);
-    eval_system(s, s.q.p, 1);
-    // Newton direction: H dq = -g, enqueued behind the system without a host
-    // round trip; the status word the solver reads back also carries the
-    // system's flags and energies, checked before its result is used (every
-    // kernel bounds its work by the clamped counts, so an overflowed system
-    // is only discarded)
-    launch_negate(s, s.g.p, s.qsave.p, 12L * s.nb);
+    // system at q and the Newton direction H dq = -g, enqueued as one
+    // sequence with the solver's first two iterations; the status word read
+    // back at its end also carries the system's flags and energies, checked
+    // before the direction is used (every kernel bounds its work by the
+    // clamped counts, so an overflowed system is only discarded)
+    run_segment(s, s.seg_sys[s.fp32_proj ? 1 : 0], [&]() {
+      launch_transform(s, s.q.p, s.x.p);
+      eval_system(s, s.q.p, 1);
+      launch_negate(s, s.g.p, s.qsave.p, 12L * s.nb);
+      pcg_begin(s, s.qsave.p, s.dq.p);
+      pcg_iterate(s, s.dq.p, 2, s.prm.pcg_rel_tol);
+      cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
+    });
+    cudaStreamSynchronize(s.stream);
     double rel;
-    int its = run_pcg(s, s.qsave.p, s.dq.p, s.prm.pcg_max, s.prm.pcg_rel_tol, &rel);
+    int its = pcg_finish(s, s.dq.p, 2, s.prm.pcg_max, s.prm.pcg_rel_tol, &rel);
     if (s.st_host->flags & kCapFlags) return ABD_ERR_CAPACITY;
     if (abd_status r = flags_to_status(s, s.st_host->flags)) return r;
     loc.n_active = s.st_host->nact;
@@ -293,19 +347,18 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
     // step length for the convergence test, then (in the same batch) the CCD
     // bound over the swept candidates and the first trial at alpha = bound;
     // the swept candidates also serve the next iteration
-    launch_transform_dq(s, s.dq.p);
-    cudaMemsetAsync(&s.st->step_bits, 0, sizeof(unsigned long long), s.stream);
-    launch_max_step(s);
-    {
-      // reset the CCD minimum (toi_bits only: step_bits sits next to it)
-      const double one = 1.0;
-      cudaMemcpyAsync(&s.st->toi_bits, &one, sizeof(double), cudaMemcpyHostToDevice, s.stream);
-    }
-    broad_and_enumerate(s, true, true);
-    launch_trial(s, 1.0, true);
-    launch_transform(s, s.qtrial.p, s.xt.p);
-    eval_energy(s, s.qtrial.p);
-    read_status(s);
+    run_segment(s, s.seg_trial, [&]() {
+      launch_transform_dq(s, s.dq.p);
+      cudaMemsetAsync(&s.st->step_bits, 0, sizeof(unsigned long long), s.stream);
+      launch_max_step(s);
+      launch_reset_toi(s);
+      broad_and_enumerate(s, true, true);
+      launch_trial(s, 1.0, true);
+      launch_transform(s, s.qtrial.p, s.xt.p);
+      eval_energy(s, s.qtrial.p);
+      cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
+    });
+    cudaStreamSynchronize(s.stream);
     double step = bits_to_double(s.st_host->step_bits);
     loc.last_step = step;
     if (!(step == step)) {
@@ -357,7 +410,9 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
       s.err = "line search did not decrease the energy";
       return ABD_ERR_LINESEARCH;
     }
-    std::swap(s.q, s.qtrial);
+    // accept the trial (a copy, not a pointer swap: the captured sequences
+    // keep their buffers)
+    cudaMemcpyAsync(s.q.p, s.qtrial.p, qb, cudaMemcpyDeviceToDevice, s.stream);
   }
   if (status != ABD_OK) {
     if (s.err.empty()) s.err = "Newton iteration cap reached";
@@ -598,6 +653,9 @@ void abd_destroy(abd_scene* S) {
   if (!S) return;
   Scene& s = S->s;
   if (s.stream || s.st) cudaStreamSynchronize(s.stream);
+  for (Scene::Segment* g : {&s.seg_sys[0], &s.seg_sys[1], &s.seg_trial})
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (s.cap_stream) cudaStreamDestroy(s.cap_stream);
   release(s, s.xbar);
   release(s, s.l2e);
   release(s, s.scan_part);

@@ -126,6 +126,19 @@ struct Scene {
   int nb = 0, nv = 0, nt = 0, ne = 0, ndyn = 0;
   double newton_tol = 0;
   bool fp32_proj = false;  // barrier projection from the FP32 eigenbasis (mixed precision)
+
+  // CUDA graphs of the two fixed launch sequences of a Newton iteration
+  // (captured on a private stream, replayed on the scene's stream, captured
+  // again whenever a buffer has been reallocated)
+  struct Segment {
+    cudaGraphExec_t exec = nullptr;
+    long gen = -1;
+    long nlaunch = 0;
+  };
+  long gen = 0;  // bumped on every buffer (re)allocation
+  bool graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  Segment seg_sys[2], seg_trial;
   Alloc alloc;
   cudaStream_t stream = nullptr;
   std::string err;
@@ -255,6 +268,10 @@ void launch_gather(Scene& s);
 void launch_precond(Scene& s);
 void launch_energy_total(Scene& s, bool with_pairs);
 int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res);
+void pcg_begin(Scene& s, const double* rhs, double* xout);
+void pcg_iterate(Scene& s, double* xout, int n, double rel_tol);
+int pcg_finish(Scene& s, double* xout, int done_iters, int max_iter, double rel_tol, double* rel_res);
+void launch_reset_toi(Scene& s);
 void launch_max_step(Scene& s);
 void launch_trial(Scene& s, double alpha, bool alpha_from_ccd);
 void launch_finish_step(Scene& s);

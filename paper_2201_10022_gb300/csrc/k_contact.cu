@@ -408,7 +408,7 @@ int grid_for(long n, int per_block, int max_blocks) {
 
 void launch_enumerate(Scene& s, bool swept, bool ccd) {
   const int threads = 32 * kWarpsPerBlock;
-  int grid = grid_for(s.last_np > 0 ? s.last_np : s.nb, kWarpsPerBlock, 152 * 16);
+  int grid = grid_for(2L * s.nb, kWarpsPerBlock, 152 * 16);  // grid-stride over the device's pair count
   counted(s);
   ProfScope ps(s, PF_ENUM);
   k_enumerate<<<grid, threads, 0, s.stream>>>(s.P.p, s.st, s.vbeg.p, s.tbeg.p, s.ebeg.p, s.tri.p, s.edge.p, s.x.p,
@@ -417,7 +417,7 @@ void launch_enumerate(Scene& s, bool swept, bool ccd) {
 }
 
 void launch_active(Scene& s, const double4* x) {
-  int grid = grid_for(s.last_np > 0 ? s.last_np : s.nb, 8, 152 * 16);
+  int grid = grid_for(2L * s.nb, 8, 152 * 16);  // grid-stride over the device's pair count
   counted(s);
   ProfScope ps(s, PF_ACTIVE);
   k_active<<<grid, 256, 0, s.stream>>>(s.P.p, s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.prm.dhat, s.maxc,
@@ -440,7 +440,7 @@ void launch_friction_eval(Scene& s, const double4* x, bool derivs) {
 
 void launch_pair_energy(Scene& s, const double4* x) {
   const int nch = energy_chunks(s);
-  int grid = grid_for((long)(s.last_np > 0 ? s.last_np : s.nb) * nch, 8, 152 * 32);
+  int grid = grid_for(2L * s.nb * nch, 8, 152 * 32);  // grid-stride over the device's pair count
   counted(s);
   k_pair_energy<<<grid, 256, 0, s.stream>>>(s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.l2e.p,
                                             s.prm.dhat, s.prm.kappa, s.maxc, nch, s.Epair.p, s.st);

@@ -1387,43 +1387,49 @@ void launch_energy_total(Scene& s, bool from_terms) {
   k_energy_sum<<<1, 1, 0, s.stream>>>(s.st, from_terms ? 1 : 0);
 }
 
-int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res) {
+// PCG in three pieces so that its first iterations can join a captured launch
+// sequence: pcg_begin (r = rhs, x = 0, first direction), pcg_iterate (n
+// iterations, each a no-op once converged), pcg_finish (further chunks with a
+// status read-back after each, until converged or the cap)
+void pcg_begin(Scene& s, const double* rhs, double* xout) {
   const int nbk = blocks(s.nb, 128);
-  counted(s);
+  counted(s, 2);
   k_pcg_init<<<nbk, 128, 0, s.stream>>>(s.nb, s.is_static.p, s.Pinv.p, rhs, xout, s.r.p, s.z.p, s.pv.p, s.part.p);
-  counted(s);
   k_pcg_start<<<1, 256, 0, s.stream>>>(s.part.p, nbk, s.st);
+}
+
+void pcg_iterate(Scene& s, double* xout, int n, double rel_tol) {
+  const int nbk = blocks(s.nb, 128);
   const int sblocks = blocks(12L * s.nb, kPcgThreads);
   const double tol2 = rel_tol * rel_tol;
   // algorithmic bytes of one product: every stored block once (diagonal and
   // upper off-diagonal, 144 doubles each), the vector read once and the
   // product written once, the pair list once
   const double spmv_bytes = 8.0 * 144.0 * (s.nb + (double)s.last_np) + 2.0 * 8.0 * 12.0 * s.nb + 8.0 * s.last_np;
-  int it = 0;
-  int chunk = 2;
-  while (true) {
-    for (int k = 0; k < chunk; ++k) {
-      counted(s);
-      {
-        ProfScope pv(s, PF_SPMV, spmv_bytes);
-        k_spmv<<<sblocks, kPcgThreads, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.rowoff.p, s.in_off.p,
-                                                      s.in_list.p, s.P.p, s.pblk.p, s.pv.p, s.Ap.p, s.part.p, s.st);
-      }
-      counted(s);
-      k_pcg_alpha<<<1, 256, 0, s.stream>>>(s.part.p, sblocks, s.st);
-      counted(s);
-      k_pcg_update<<<nbk, 128, 0, s.stream>>>(s.nb, s.is_static.p, s.Pinv.p, s.pv.p, s.Ap.p, xout, s.r.p, s.z.p,
-                                              s.part.p, s.st);
-      counted(s);
-      k_pcg_beta<<<1, 256, 0, s.stream>>>(s.part.p, nbk, tol2, s.st);
-      counted(s);
-      k_pcg_dir<<<blocks(12L * s.nb, 256), 256, 0, s.stream>>>(12L * s.nb, s.z.p, s.pv.p, s.st);
+  for (int k = 0; k < n; ++k) {
+    counted(s, 5);
+    {
+      ProfScope pv(s, PF_SPMV, spmv_bytes);
+      k_spmv<<<sblocks, kPcgThreads, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.rowoff.p, s.in_off.p, s.in_list.p,
+                                                    s.P.p, s.pblk.p, s.pv.p, s.Ap.p, s.part.p, s.st);
     }
-    it += chunk;
+    k_pcg_alpha<<<1, 256, 0, s.stream>>>(s.part.p, sblocks, s.st);
+    k_pcg_update<<<nbk, 128, 0, s.stream>>>(s.nb, s.is_static.p, s.Pinv.p, s.pv.p, s.Ap.p, xout, s.r.p, s.z.p,
+                                            s.part.p, s.st);
+    k_pcg_beta<<<1, 256, 0, s.stream>>>(s.part.p, nbk, tol2, s.st);
+    k_pcg_dir<<<blocks(12L * s.nb, 256), 256, 0, s.stream>>>(12L * s.nb, s.z.p, s.pv.p, s.st);
+  }
+}
+
+int pcg_finish(Scene& s, double* xout, int done_iters, int max_iter, double rel_tol, double* rel_res) {
+  int it = done_iters;
+  int chunk = std::max(2, 2 * done_iters);
+  while (s.st_host->scal[6] == 0.0 && it < max_iter) {
+    pcg_iterate(s, xout, std::min(chunk, 16), rel_tol);
+    it += std::min(chunk, 16);
     cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
     cudaStreamSynchronize(s.stream);
-    if (s.st_host->scal[6] != 0.0 || it >= max_iter) break;
-    chunk = std::min(2 * chunk, 16);
+    chunk = 2 * chunk;
   }
   double rr = s.st_host->scal[2], rr0 = s.st_host->scal[3];
   *rel_res = rr0 > 0 ? sqrt(rr / rr0) : 0.0;
@@ -1431,6 +1437,22 @@ int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_
   if (s.st_host->scal[6] == 2.0) return -2;
   if (s.st_host->scal[6] == 0.0) return -1;
   return iters;
+}
+
+int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res) {
+  pcg_begin(s, rhs, xout);
+  pcg_iterate(s, xout, 2, rel_tol);
+  cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
+  cudaStreamSynchronize(s.stream);
+  return pcg_finish(s, xout, 2, max_iter, rel_tol, rel_res);
+}
+
+__global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+
+// the CCD minimum starts at 1 (a whole step)
+void launch_reset_toi(Scene& s) {
+  counted(s);
+  k_set_u64<<<1, 1, 0, s.stream>>>(&s.st->toi_bits, 0x3FF0000000000000ull);
 }
 
 void launch_max_step(Scene& s) {
