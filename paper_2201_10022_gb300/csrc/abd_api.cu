@@ -534,6 +534,7 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
       grow(s, *b, 12L * nb);
     grow(s, s.Eb, 2L * nb);
     for (Buf<double>* b : {&s.Db, &s.D, &s.Pinv}) grow(s, *b, 144L * nb);
+    grow(s, s.hfix, nb);
     grow(s, s.part, 2L * nb + 1024);
     for (Buf<double4>* b : {&s.x, &s.dx, &s.x1, &s.xt}) grow(s, *b, nv);
     grow(s, s.bbox, 6L * nb);
@@ -659,6 +660,7 @@ void abd_destroy(abd_scene* S) {
   release(s, s.xbar);
   release(s, s.l2e);
   release(s, s.scan_part);
+  release(s, s.hfix);
   release(s, s.vbody);
   release(s, s.tri);
   release(s, s.edge);

@@ -49,6 +49,8 @@ struct DevStatus {
   double energy[8];             // 0 total, 1 inertia, 2 ortho, 3 barrier, 4 friction
   int bar_cnt[4];               // active terms by working dimension 3, 6, 9 (classification pass)
   unsigned long long jac[3];    // Jacobi sweeps FP32, FP64, terms at the FP64 sweep cap (cumulative)
+  int bh_fix;                   // body blocks to project (not positive definite)
+  int pad3;
 };
 
 // ---- small device helpers shared by the kernel files -----------------------
@@ -196,6 +198,7 @@ struct Scene {
   // assembly
   Buf<double> pblk;    // np * (3*144 + 24 + 2): Hab, Dlo, Dhi, glo, ghi, Eb, Ef
   Buf<double> Db, gb, Eb;   // body terms
+  Buf<int> hfix;            // bodies whose block failed Cholesky (projected)
   Buf<double> D, g, Pinv;   // assembled diagonal, gradient, preconditioner
   Buf<double> red;     // reduction scratch
   Buf<long long> scan_part;  // tile sums of the two-phase scan

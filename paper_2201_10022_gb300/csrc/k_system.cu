@@ -2,6 +2,8 @@
 // (Sec. 3), body boxes and body-pair culling (Sec. 4.2), per-body inertia and
 // orthogonality terms (Sec. 3.2 / Sec. 4), Hessian assembly by body-pair
 // blocks (Sec. 4.3), block-Jacobi PCG, and deterministic reductions.
+#include <stddef.h>
+
 #include <algorithm>
 
 #include "abd_internal.cuh"
@@ -114,32 +116,51 @@ __global__ void k_transform_dq(int nv, const int* vbody, const double4* xbar, co
   x1[v] = make_double4(__dadd_rn(p.x, d.x), __dadd_rn(p.y, d.y), __dadd_rn(p.z, d.z), 0.0);
 }
 
+// order-preserving integer key of a double (non-NaN): min / max of keys is
+// the exact min / max of the values, on the integer units instead of the
+// (slow) FP64 pipe
+__device__ __forceinline__ long long dkey(double d) {
+  const long long b = __double_as_longlong(d);
+  return b >= 0 ? b : b ^ 0x7FFFFFFFFFFFFFFFll;
+}
+__device__ __forceinline__ double dval(long long k) {
+  return __longlong_as_double(k >= 0 ? k : k ^ 0x7FFFFFFFFFFFFFFFll);
+}
+
 __global__ void k_body_boxes(int nb, const int* vbeg, const double4* x, const double4* x1, double* bbox) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= nb) return;
   const int b = warp;
-  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  const long long klo = dkey(1e300), khi = dkey(-1e300);  // an empty body keeps an empty box
+  long long lo[3] = {klo, klo, klo}, hi[3] = {khi, khi, khi};
   for (int v = vbeg[b] + lane; v < vbeg[b + 1]; v += 32) {
-    double4 p = x[v];
-    lo[0] = fmin(lo[0], p.x); hi[0] = fmax(hi[0], p.x);
-    lo[1] = fmin(lo[1], p.y); hi[1] = fmax(hi[1], p.y);
-    lo[2] = fmin(lo[2], p.z); hi[2] = fmax(hi[2], p.z);
+    const double4 p = x[v];
+    const long long k[3] = {dkey(p.x), dkey(p.y), dkey(p.z)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      lo[c] = min(lo[c], k[c]);
+      hi[c] = max(hi[c], k[c]);
+    }
     if (x1) {
-      double4 r = x1[v];
-      lo[0] = fmin(lo[0], r.x); hi[0] = fmax(hi[0], r.x);
-      lo[1] = fmin(lo[1], r.y); hi[1] = fmax(hi[1], r.y);
-      lo[2] = fmin(lo[2], r.z); hi[2] = fmax(hi[2], r.z);
+      const double4 r = x1[v];
+      const long long kr[3] = {dkey(r.x), dkey(r.y), dkey(r.z)};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        lo[c] = min(lo[c], kr[c]);
+        hi[c] = max(hi[c], kr[c]);
+      }
     }
   }
-  for (int k = 0; k < 3; ++k)
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
     for (int o = 16; o > 0; o >>= 1) {
-      lo[k] = fmin(lo[k], __shfl_xor_sync(kFull, lo[k], o));
-      hi[k] = fmax(hi[k], __shfl_xor_sync(kFull, hi[k], o));
+      lo[c] = min(lo[c], __shfl_xor_sync(kFull, lo[c], o));
+      hi[c] = max(hi[c], __shfl_xor_sync(kFull, hi[c], o));
     }
   if (lane == 0)
-    for (int k = 0; k < 3; ++k) {
-      bbox[6 * b + k] = lo[k];
-      bbox[6 * b + 3 + k] = hi[k];
+    for (int c = 0; c < 3; ++c) {
+      bbox[6 * b + c] = dval(lo[c]);
+      bbox[6 * b + 3 + c] = dval(hi[c]);
     }
 }
 
@@ -744,101 +765,120 @@ __global__ void k_body_terms(int nb, const uint8_t* is_static, const double* q, 
 
 }
 
+// one body per thread, 32 bodies per block: the blocks are staged through
+// shared memory (rows padded to 145 doubles: conflict-free per-thread rows)
+// with coalesced loads and stores, and factored in registers
+constexpr int kBodyWarp = 32;
+
+__device__ __forceinline__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // j <= i
+
+// in-register Cholesky of a 12x12 symmetric matrix held as its lower
+// triangle: L receives the factor below the diagonal and 1 / L_ii on it;
+// false if a pivot is not positive
+__device__ __forceinline__ bool chol12(double* L) {
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    double d = L[tri(j, j)];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= L[tri(j, k)] * L[tri(j, k)];
+    ok = ok && d > 0.0;
+    const double r = rsqrt(d);
+    L[tri(j, j)] = r;
+#pragma unroll
+    for (int i = j + 1; i < 12; ++i) {
+      double t = L[tri(i, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) t -= L[tri(i, k)] * L[tri(j, k)];
+      L[tri(i, j)] = t * r;
+    }
+  }
+  return ok;
+}
+
 // Hessian block of the body terms (Sec. 3.2, Sec. 4): B = M + dt^2 hess V_ortho
 // over q = (p, rows a_i of A), with the closed form
 //   d2 V / da_k da_l = 4 kappa nu [(a_k.a_l - delta_kl) I + delta_kl A^T A + a_l a_k^T],
 // used as it is when it is positive definite (a Cholesky factorisation
-// succeeds) and replaced by its PSD projection otherwise.  Twelve threads per
-// body (one row each), sixteen bodies per block; static bodies get I.
-constexpr int kHessBodies = 16, kHessThreads = 12 * kHessBodies;
+// succeeds) and replaced by its PSD projection otherwise (listed for
+// k_body_hess_fix).  One body per thread; static bodies get I.
+__device__ __forceinline__ int qcomp(int i) { return i < 3 ? i : (i - 3) / 3; }  // spatial row of dof i
+__device__ __forceinline__ int qmono(int i) { return i < 3 ? 0 : 1 + (i - 3) % 3; }  // 1, xbar_x, xbar_y, xbar_z
 
-__global__ void __launch_bounds__(kHessThreads) k_body_hess(int nb, const uint8_t* is_static, const double* q,
-                                                            const double* mass10, const double* vol,
-                                                            const double* kappa_b, double dt, double* Db) {
-  __shared__ double Bs[kHessBodies][12][13];
-  __shared__ double L[kHessBodies][12][13];
-  __shared__ double rd[kHessBodies][12];
-  __shared__ int bad[kHessBodies];
-  const int bl = threadIdx.x / 12, r = threadIdx.x - 12 * (threadIdx.x / 12);
-  const int b = blockIdx.x * kHessBodies + bl;
+__global__ void __launch_bounds__(kBodyWarp) k_body_hess(int nb, const uint8_t* is_static, const double* q,
+                                                         const double* mass10, const double* vol,
+                                                         const double* kappa_b, double dt, double* Db, int* fix,
+                                                         DevStatus* st) {
+  __shared__ double S[kBodyWarp][145];
+  const int t = threadIdx.x;
+  const long b0 = (long)blockIdx.x * kBodyWarp, b = b0 + t;
   const bool live = b < nb && !is_static[b];
-  if (r == 0) bad[bl] = 0;
-  // row r of B
-  {
-    double row[12];
+  double B[78];
+  if (live) {
+    const double* m = mass10 + 10 * b;
+    const double W[4][4] = {{m[0], m[1], m[2], m[3]}, {m[1], m[4], m[5], m[6]}, {m[2], m[5], m[7], m[8]},
+                            {m[3], m[6], m[8], m[9]}};
+    double A[3][3];
 #pragma unroll
-    for (int j = 0; j < 12; ++j) row[j] = (j == r) ? 1.0 : 0.0;
-    if (live) {
-      const double* m = mass10 + 10 * b;
-      const double W[4][4] = {{m[0], m[1], m[2], m[3]}, {m[1], m[4], m[5], m[6]}, {m[2], m[5], m[7], m[8]},
-                              {m[3], m[6], m[8], m[9]}};
-      double A[3][3];
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
+      for (int c = 0; c < 3; ++c) A[i][c] = q[12 * b + 3 + 3 * i + c];
+    const double s4 = dt * dt * 4.0 * kappa_b[b] * vol[b];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) A[i][c] = q[12 * b + 3 + 3 * i + c];
-      const double kv4 = 4.0 * kappa_b[b] * vol[b], dt2 = dt * dt;
-      // q index j: translation component j (< 3), else A[(j-3)/3][(j-3)%3]
-      const int cr = r < 3 ? r : (r - 3) / 3, ur = r < 3 ? 0 : 1 + (r - 3) % 3;
+    for (int i = 0; i < 12; ++i)
 #pragma unroll
-      for (int j = 0; j < 12; ++j) {
-        const int cj = j < 3 ? j : (j - 3) / 3, uj = j < 3 ? 0 : 1 + (j - 3) % 3;
-        double v = cr == cj ? W[ur][uj] : 0.0;
-        if (r >= 3 && j >= 3) {
-          const int k = cr, ck = ur - 1, l = cj, cl = uj - 1;
+      for (int j = 0; j <= i; ++j) {
+        double v = qcomp(i) == qcomp(j) ? W[qmono(i)][qmono(j)] : 0.0;
+        if (i >= 3 && j >= 3) {
+          const int k = qcomp(i), ck = qmono(i) - 1, l = qcomp(j), cl = qmono(j) - 1;
           double h = A[l][ck] * A[k][cl];
           if (ck == cl) h += A[k][0] * A[l][0] + A[k][1] * A[l][1] + A[k][2] * A[l][2] - (k == l ? 1.0 : 0.0);
           if (k == l) h += A[0][ck] * A[0][cl] + A[1][ck] * A[1][cl] + A[2][ck] * A[2][cl];
-          v += dt2 * kv4 * h;
+          v += s4 * h;
         }
-        row[j] = v;
+        B[tri(i, j)] = v;
       }
-    }
+    double L[78];
 #pragma unroll
-    for (int j = 0; j < 12; ++j) {
-      Bs[bl][r][j] = row[j];
-      L[bl][r][j] = row[j];
-    }
-  }
-  __syncthreads();
-  // Cholesky test (left-looking, one column per step)
-  for (int j = 0; j < 12; ++j) {
-    double t = 0.0;
-    if (r >= j) {
-      t = L[bl][r][j];
-      for (int k = 0; k < j; ++k) t -= L[bl][r][k] * L[bl][j][k];
-    }
-    if (r == j) {
-      if (!(t > 0.0)) bad[bl] = 1;
-      const double ri = rsqrt(t);
-      L[bl][j][j] = t * ri;
-      rd[bl][j] = ri;
-    }
-    __syncthreads();
-    if (r > j) L[bl][r][j] = t * rd[bl][j];
-    __syncthreads();
-  }
-  if (live && bad[bl] && r == 0) {
-    // not positive definite: PSD projection of the whole block (rare)
-    double Ab[144], V[144];
+    for (int k = 0; k < 78; ++k) L[k] = B[k];
+    if (!chol12(L)) fix[atomicAdd(&st->bh_fix, 1)] = (int)b;  // rare: projected afterwards
+  } else {
+#pragma unroll
     for (int i = 0; i < 12; ++i)
-      for (int j = 0; j < 12; ++j) Ab[12 * i + j] = Bs[bl][i][j];
+#pragma unroll
+      for (int j = 0; j <= i; ++j) B[tri(i, j)] = i == j ? 1.0 : 0.0;
+  }
+#pragma unroll
+  for (int i = 0; i < 12; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      S[t][12 * i + j] = B[tri(i, j)];
+      S[t][12 * j + i] = B[tri(i, j)];
+    }
+  __syncthreads();
+  for (int k = t; k < kBodyWarp * 144; k += kBodyWarp) {
+    const int bb = k / 144, e = k - 144 * bb;
+    if (b0 + bb < nb) Db[144 * (b0 + bb) + e] = S[bb][e];
+  }
+}
+
+// PSD projection (eigenvalue clamp) of the body blocks that failed Cholesky
+__global__ void k_body_hess_fix(const DevStatus* cst, const int* fix, double* Db) {
+  const int n = cst->bh_fix;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double* Bk = Db + 144L * fix[k];
+    double Ab[144], V[144];
+    for (int i = 0; i < 144; ++i) Ab[i] = Bk[i];
     jacobi_eig<12, double>(Ab, V);
     for (int i = 0; i < 12; ++i)
       for (int j = 0; j < 12; ++j) {
         double t = 0.0;
-        for (int k = 0; k < 12; ++k) {
-          const double lam = Ab[13 * k];
-          if (lam > 0.0) t += V[12 * i + k] * lam * V[12 * j + k];
+        for (int c = 0; c < 12; ++c) {
+          const double lam = Ab[13 * c];
+          if (lam > 0.0) t += V[12 * i + c] * lam * V[12 * j + c];
         }
-        Bs[bl][i][j] = t;
+        Bk[12 * i + j] = t;
       }
-  }
-  __syncthreads();
-  const long base = (long)blockIdx.x * kHessBodies * 144, lim = 144L * nb;
-  for (int k = threadIdx.x; k < kHessBodies * 144; k += kHessThreads) {
-    const int bb = k / 144, e = k - 144 * (k / 144);
-    if (base + k < lim) Db[base + k] = Bs[bb][e / 12][e % 12];
   }
 }
 
@@ -866,61 +906,43 @@ __global__ void k_gather(int nb, const uint8_t* is_static, const int* rowoff, co
   }
 }
 
-// block-Jacobi preconditioner: Cholesky factor L of each dynamic diagonal
-// block, stored per body as 144 doubles with L below the diagonal (row-major)
-// and 1 / L_ii on it; the solver applies (L L^T)^-1 by forward and back
-// substitution (chol_apply).  Twelve threads per body (one matrix row each),
-// sixteen bodies per block, staged through shared memory with coalesced loads
-// and stores; left-looking, one column per step.  A block that is not
-// positive definite falls back to its diagonal (flagged).  Static bodies get
-// a zero factor (their rows stay zero).
-constexpr int kPreBodies = 16, kPreThreads = 12 * kPreBodies;
-
-__global__ void __launch_bounds__(kPreThreads) k_precond(int nb, const uint8_t* is_static, const double* D,
-                                                         double* Pinv, DevStatus* st) {
-  __shared__ double A[kPreBodies][12][13];
-  __shared__ double rd[kPreBodies][12];
-  __shared__ int bad[kPreBodies];
-  const int bl = threadIdx.x / 12, r = threadIdx.x - 12 * (threadIdx.x / 12);
-  const int b = blockIdx.x * kPreBodies + bl;
-  const long base = (long)blockIdx.x * kPreBodies * 144, lim = 144L * nb;
-  for (int k = threadIdx.x; k < kPreBodies * 144; k += kPreThreads) {
-    const int bb = k / 144, e = k - 144 * (k / 144);
-    A[bb][e / 12][e % 12] = base + k < lim ? D[base + k] : 0.0;
+// block-Jacobi preconditioner: Cholesky factor of each dynamic diagonal
+// block, stored per body as 144 doubles with L below the diagonal
+// (row-major), 1 / L_ii on it and zeros above; the solver applies
+// (L L^T)^-1 by forward and back substitution (chol_apply).  A block that is
+// not positive definite falls back to its diagonal (flagged); static bodies
+// get a zero factor (their rows stay zero).
+__global__ void __launch_bounds__(kBodyWarp) k_precond(int nb, const uint8_t* is_static, const double* D,
+                                                       double* Pinv, DevStatus* st) {
+  __shared__ double S[kBodyWarp][145];
+  const int t = threadIdx.x;
+  const long b0 = (long)blockIdx.x * kBodyWarp, b = b0 + t;
+  for (int k = t; k < kBodyWarp * 144; k += kBodyWarp) {
+    const int bb = k / 144, e = k - 144 * bb;
+    S[bb][e] = b0 + bb < nb ? D[144 * (b0 + bb) + e] : 0.0;
   }
-  if (r == 0) bad[bl] = 0;
   __syncthreads();
-  for (int j = 0; j < 12; ++j) {
-    double t = 0.0;
-    if (r >= j) {
-      t = A[bl][r][j];
-      for (int k = 0; k < j; ++k) t -= A[bl][r][k] * A[bl][j][k];
-    }
-    if (r == j) {
-      if (!(t > 0.0)) bad[bl] = 1;  // not positive definite
-      const double ri = rsqrt(t);
-      A[bl][j][j] = t * ri;
-      rd[bl][j] = ri;
-    }
-    __syncthreads();
-    if (r > j) A[bl][r][j] = t * rd[bl][j];
-    __syncthreads();
-  }
   const bool live = b < nb && !is_static[b];
-  const bool fallback = live && bad[bl];
-  // row r of the stored factor
+  double L[78];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    double v = 0.0;
-    if (live && !fallback) v = k < r ? A[bl][r][k] : (k == r ? rd[bl][r] : 0.0);
-    if (fallback && k == r) v = rsqrt(fabs(D[144L * b + 13 * r]));
-    A[bl][r][k] = v;  // each thread rewrites only its own row
-  }
-  if (fallback && r == 0) set_flag(st, ST_PCG_BREAKDOWN);
+  for (int i = 0; i < 12; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) L[tri(i, j)] = S[t][12 * i + j];
+  const bool fallback = live && !chol12(L);
+#pragma unroll
+  for (int i = 0; i < 12; ++i)
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      double v = 0.0;
+      if (live && !fallback && j <= i) v = L[tri(i, j)];
+      if (fallback && i == j) v = rsqrt(fabs(S[t][13 * i]));
+      S[t][12 * i + j] = v;
+    }
+  if (fallback) set_flag(st, ST_PCG_BREAKDOWN);
   __syncthreads();
-  for (int k = threadIdx.x; k < kPreBodies * 144; k += kPreThreads) {
-    const int bb = k / 144, e = k - 144 * (k / 144);
-    if (base + k < lim) Pinv[base + k] = A[bb][e / 12][e % 12];
+  for (int k = t; k < kBodyWarp * 144; k += kBodyWarp) {
+    const int bb = k / 144, e = k - 144 * bb;
+    if (b0 + bb < nb) Pinv[144 * (b0 + bb) + e] = S[bb][e];
   }
 }
 
@@ -1357,9 +1379,11 @@ void launch_body_terms(Scene& s, const double* q, bool hess) {
   k_body_terms<<<blocks(s.nb, 64), 64, 0, s.stream>>>(s.nb, s.is_static.p, q, s.qtilde.p, s.mass10.p, s.vol.p,
                                                        s.kappa_b.p, s.prm.dt, s.gb.p, s.Eb.p);
   if (hess) {
-    counted(s);
-    k_body_hess<<<blocks(s.nb, kHessBodies), kHessThreads, 0, s.stream>>>(s.nb, s.is_static.p, q, s.mass10.p,
-                                                                          s.vol.p, s.kappa_b.p, s.prm.dt, s.Db.p);
+    counted(s, 2);
+    cudaMemsetAsync(reinterpret_cast<char*>(s.st) + offsetof(DevStatus, bh_fix), 0, sizeof(int), s.stream);
+    k_body_hess<<<blocks(s.nb, kBodyWarp), kBodyWarp, 0, s.stream>>>(s.nb, s.is_static.p, q, s.mass10.p, s.vol.p,
+                                                                     s.kappa_b.p, s.prm.dt, s.Db.p, s.hfix.p, s.st);
+    k_body_hess_fix<<<1, 32, 0, s.stream>>>(s.st, s.hfix.p, s.Db.p);
   }
 }
 
@@ -1371,7 +1395,7 @@ void launch_gather(Scene& s) {
 
 void launch_precond(Scene& s) {
   counted(s);
-  k_precond<<<blocks(s.nb, kPreBodies), kPreThreads, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.Pinv.p, s.st);
+  k_precond<<<blocks(s.nb, kBodyWarp), kBodyWarp, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.Pinv.p, s.st);
 }
 
 // energies of the last evaluation into st->energy: bodies, barrier terms or
