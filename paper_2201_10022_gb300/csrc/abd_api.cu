@@ -538,6 +538,7 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
     grow(s, s.part, 2L * nb + 1024);
     for (Buf<double4>* b : {&s.x, &s.dx, &s.x1, &s.xt}) grow(s, *b, nv);
     grow(s, s.bbox, 6L * nb);
+    grow(s, s.bbox32, 6L * nb);
     s.maxn = 64;
     grow(s, s.nbr, (size_t)nb * s.maxn);
     grow(s, s.ncount, nb);
@@ -661,6 +662,7 @@ void abd_destroy(abd_scene* S) {
   release(s, s.l2e);
   release(s, s.scan_part);
   release(s, s.hfix);
+  release(s, s.bbox32);
   release(s, s.vbody);
   release(s, s.tri);
   release(s, s.edge);

@@ -157,6 +157,7 @@ struct Scene {
   Buf<double> q, qdot, qt, qtilde, dq, qtrial, qsave, qdotsave;
   Buf<double4> x, dx, x1, xt;
   Buf<double> bbox;    // nb*6
+  Buf<float> bbox32;   // nb*6, the same boxes rounded outward to FP32 (prefilter)
 
   // spatial hash over body boxes
   double cell_h = 1.0;         // cell edge

@@ -19,18 +19,32 @@ struct Box {
   double lo[3], hi[3];
 };
 
-__device__ __forceinline__ void box_point(Box& b, const double4& p) {
-  b.lo[0] = b.hi[0] = p.x;
-  b.lo[1] = b.hi[1] = p.y;
-  b.lo[2] = b.hi[2] = p.z;
+// order-preserving integer key of a double (non-NaN): min / max on keys is
+// the exact min / max of the values, on the integer units rather than the
+// (slow) FP64 pipe
+__device__ __forceinline__ long long dkey(double d) {
+  const long long b = __double_as_longlong(d);
+  return b >= 0 ? b : b ^ 0x7FFFFFFFFFFFFFFFll;
 }
-__device__ __forceinline__ void box_add(Box& b, const double4& p) {
-  b.lo[0] = fmin(b.lo[0], p.x);
-  b.hi[0] = fmax(b.hi[0], p.x);
-  b.lo[1] = fmin(b.lo[1], p.y);
-  b.hi[1] = fmax(b.hi[1], p.y);
-  b.lo[2] = fmin(b.lo[2], p.z);
-  b.hi[2] = fmax(b.hi[2], p.z);
+__device__ __forceinline__ double dval(long long k) {
+  return __longlong_as_double(k >= 0 ? k : k ^ 0x7FFFFFFFFFFFFFFFll);
+}
+
+struct KeyBox {
+  long long lo[3], hi[3];
+};
+__device__ __forceinline__ void kbox_point(KeyBox& b, const double4& p) {
+  b.lo[0] = b.hi[0] = dkey(p.x);
+  b.lo[1] = b.hi[1] = dkey(p.y);
+  b.lo[2] = b.hi[2] = dkey(p.z);
+}
+__device__ __forceinline__ void kbox_add(KeyBox& b, const double4& p) {
+  const long long k[3] = {dkey(p.x), dkey(p.y), dkey(p.z)};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    b.lo[c] = min(b.lo[c], k[c]);
+    b.hi[c] = max(b.hi[c], k[c]);
+  }
 }
 // canonical proximity test: on every axis lo_P - hi_Q <= dhat and lo_Q - hi_P <= dhat
 __device__ __forceinline__ bool box_near(const double* plo, const double* phi, const double* qlo, const double* qhi,
@@ -43,17 +57,24 @@ __device__ __forceinline__ bool box_near(const double* plo, const double* phi, c
   return true;
 }
 
-// box of primitive `id` of type t (0 vertex, 1 edge, 2 triangle)
+// box of primitive `id` of type t (0 vertex, 1 edge, 2 triangle): exact
+// min / max of its vertices (and their end positions when swept)
 __device__ __forceinline__ void prim_box(int t, int id, const int* tri, const int* edge, const double4* x,
                                          const double4* x1, Box& b) {
   int nvtx = t == 0 ? 1 : (t == 1 ? 2 : 3);
   int v0 = t == 0 ? id : (t == 1 ? edge[2 * id] : tri[3 * id]);
-  box_point(b, x[v0]);
-  if (x1) box_add(b, x1[v0]);
-  for (int k = 1; k < nvtx; ++k) {
-    int v = t == 1 ? edge[2 * id + k] : tri[3 * id + k];
-    box_add(b, x[v]);
-    if (x1) box_add(b, x1[v]);
+  KeyBox k;
+  kbox_point(k, x[v0]);
+  if (x1) kbox_add(k, x1[v0]);
+  for (int j = 1; j < nvtx; ++j) {
+    int v = t == 1 ? edge[2 * id + j] : tri[3 * id + j];
+    kbox_add(k, x[v]);
+    if (x1) kbox_add(k, x1[v]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    b.lo[c] = dval(k.lo[c]);
+    b.hi[c] = dval(k.hi[c]);
   }
 }
 

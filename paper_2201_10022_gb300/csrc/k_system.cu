@@ -127,7 +127,8 @@ __device__ __forceinline__ double dval(long long k) {
   return __longlong_as_double(k >= 0 ? k : k ^ 0x7FFFFFFFFFFFFFFFll);
 }
 
-__global__ void k_body_boxes(int nb, const int* vbeg, const double4* x, const double4* x1, double* bbox) {
+__global__ void k_body_boxes(int nb, const int* vbeg, const double4* x, const double4* x1, double* bbox,
+                             float* bbox32) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= nb) return;
   const int b = warp;
@@ -157,11 +158,12 @@ __global__ void k_body_boxes(int nb, const int* vbeg, const double4* x, const do
       lo[c] = min(lo[c], __shfl_xor_sync(kFull, lo[c], o));
       hi[c] = max(hi[c], __shfl_xor_sync(kFull, hi[c], o));
     }
-  if (lane == 0)
-    for (int c = 0; c < 3; ++c) {
-      bbox[6 * b + c] = dval(lo[c]);
-      bbox[6 * b + 3 + c] = dval(hi[c]);
-    }
+  if (lane < 6) {  // FP64 box and its FP32 copy rounded outward
+    const int c = lane % 3;
+    const double v = dval(lane < 3 ? lo[c] : hi[c]);
+    bbox[6 * b + lane] = v;
+    bbox32[6 * b + lane] = lane < 3 ? __double2float_rd(v) : __double2float_ru(v);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -184,6 +186,16 @@ __device__ __forceinline__ void cell_range(const double* bb, double dhat, double
     hi[k] = cell_of(bb[3 + k] + dhat, inv_h);
   }
 }
+// conservative FP32 test on the outward-rounded boxes: true only if some
+// axis is separated by more than dh32 (d-hat rounded up with a relative
+// margin of 1e-6), in which case the exact FP64 predicate below is false too
+__device__ __forceinline__ bool bodies_far32(const float* A, const float* B, float dh32) {
+  bool far = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) far = far || __fsub_rd(A[k], B[3 + k]) > dh32 || __fsub_rd(B[k], A[3 + k]) > dh32;
+  return far;
+}
+
 __device__ __forceinline__ bool bodies_near(const double* A, const double* B, double dhat) {
   for (int k = 0; k < 3; ++k) {
     if (!(__dsub_rn(A[k], B[3 + k]) <= dhat)) return false;
@@ -223,7 +235,8 @@ __global__ void k_hash_slots(int nb, const double* bbox, const int* large, doubl
       }
 }
 
-__global__ void k_rows(int nb, const uint8_t* is_static, const double* bbox, double dhat, double inv_h, unsigned mask,
+__global__ void k_rows(int nb, const uint8_t* is_static, const double* bbox, const float* bbox32, float dh32,
+                       double dhat, double inv_h, unsigned mask,
                        const int* large, const int* large_list, const int* slot_off, const int* entries,
                        const int2* fpairs, const DevStatus* cst, int maxn, int* nbr, int* ncount, DevStatus* st) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -259,7 +272,8 @@ __global__ void k_rows(int nb, const uint8_t* is_static, const double* bbox, dou
               if (k < e1) {
                 b = entries[k];
                 const double* B = bbox + 6 * b;
-                if (b > a && !(sa && is_static[b]) && bodies_near(A, B, dhat)) {
+                if (b > a && !(sa && is_static[b]) && !bodies_far32(bbox32 + 6 * a, bbox32 + 6 * b, dh32) &&
+                    bodies_near(A, B, dhat)) {
                   // report the pair only in the cell of the low corner of the
                   // dilated boxes' overlap, so it is found once
                   keep = cell_of(fmax(A[0], B[0]) - dhat, inv_h) == ix && cell_of(fmax(A[1], B[1]) - dhat, inv_h) == iy &&
@@ -273,7 +287,8 @@ __global__ void k_rows(int nb, const uint8_t* is_static, const double* bbox, dou
       for (int k0 = 0; k0 < nlarge; k0 += 32) {
         int k = k0 + lane;
         int b = k < nlarge ? large_list[k] : -1;
-        bool keep = b > a && !(sa && is_static[b]) && bodies_near(A, bbox + 6 * b, dhat);
+        bool keep = b > a && !(sa && is_static[b]) && !bodies_far32(bbox32 + 6 * a, bbox32 + 6 * b, dh32) &&
+                    bodies_near(A, bbox + 6 * b, dhat);
         emit(keep, b);
       }
       // hash order is arbitrary: sort the row and drop repeats (a body
@@ -328,7 +343,8 @@ __global__ void k_rows(int nb, const uint8_t* is_static, const double* bbox, dou
 
 // rows of large bodies: one block scans every body after the large one, in
 // order, with a block-wide ordered compaction; then the friction merge
-__global__ void k_rows_large(int nb, const uint8_t* is_static, const double* bbox, double dhat, const int* large_list,
+__global__ void k_rows_large(int nb, const uint8_t* is_static, const double* bbox, const float* bbox32, float dh32,
+                             double dhat, const int* large_list,
                              const int2* fpairs, const DevStatus* cst, int maxn, int* nbr, int* ncount, DevStatus* st) {
   __shared__ int wcount[32];
   __shared__ int wbase[33];
@@ -342,7 +358,8 @@ __global__ void k_rows_large(int nb, const uint8_t* is_static, const double* bbo
     int base = 0;
     for (int b0 = a + 1; b0 < nb; b0 += 1024) {
       const int b = b0 + t;
-      const bool keep = b < nb && !(sa && is_static[b]) && bodies_near(A, bbox + 6 * b, dhat);
+      const bool keep = b < nb && !(sa && is_static[b]) && !bodies_far32(bbox32 + 6 * a, bbox32 + 6 * b, dh32) &&
+                        bodies_near(A, bbox + 6 * b, dhat);
       const unsigned m = __ballot_sync(kFull, keep);
       if (lane == 0) wcount[w] = __popc(m);
       __syncthreads();
@@ -1290,7 +1307,7 @@ void launch_transform_dq(Scene& s, const double* dq) {
 void launch_body_boxes(Scene& s, bool swept) {
   counted(s);
   k_body_boxes<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.vbeg.p, s.x.p, swept ? s.x1.p : nullptr,
-                                                               s.bbox.p);
+                                                               s.bbox.p, s.bbox32.p);
 }
 
 void launch_scan(Scene& s, const int* cnt, int* off, const int* n_dev, int* total_dev, long cap, unsigned flag_bit,
@@ -1298,6 +1315,9 @@ void launch_scan(Scene& s, const int* cnt, int* off, const int* n_dev, int* tota
   counted(s);
   k_scan<<<1, 1024, 0, s.stream>>>(cnt, off, n_dev, n_dev ? 0 : s.nb, total_dev, cap, flag_bit, need, s.st);
 }
+
+// d-hat for the FP32 box prefilter: rounded up, with a relative margin
+float dh32(const Scene& s) { return nextafterf((float)(s.prm.dhat * (1.0 + 1e-6)), INFINITY); }
 
 void launch_body_pairs(Scene& s) {
   const double inv_h = 1.0 / s.cell_h;
@@ -1323,10 +1343,12 @@ void launch_body_pairs(Scene& s) {
   k_hash_slots<<<nbk, 128, 0, s.stream>>>(s.nb, s.bbox.p, s.large.p, s.prm.dhat, inv_h, mask, s.slot_cnt.p,
                                           s.slot_off.p, s.entries.p, (long)s.entries.cap, true);
   counted(s, 3);
-  k_rows<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.is_static.p, s.bbox.p, s.prm.dhat, inv_h, mask,
+  k_rows<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.is_static.p, s.bbox.p, s.bbox32.p, dh32(s),
+                                                        s.prm.dhat, inv_h, mask,
                                                         s.large.p, s.large_list.p, s.slot_off.p, s.entries.p,
                                                         s.fpairs.p, s.st, s.maxn, s.nbr.p, s.ncount.p, s.st);
-  k_rows_large<<<64, 1024, 0, s.stream>>>(s.nb, s.is_static.p, s.bbox.p, s.prm.dhat, s.large_list.p, s.fpairs.p, s.st,
+  k_rows_large<<<64, 1024, 0, s.stream>>>(s.nb, s.is_static.p, s.bbox.p, s.bbox32.p, dh32(s), s.prm.dhat,
+                                          s.large_list.p, s.fpairs.p, s.st,
                                           s.maxn, s.nbr.p, s.ncount.p, s.st);
   launch_scan(s, s.ncount.p, s.rowoff.p, nullptr, &s.st->np, (long)s.P.cap, ST_CAP_PAIRS, &s.st->need_pairs);
   k_rows_compact<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.nbr.p, s.ncount.p, s.rowoff.p, s.maxn, s.P.p,
