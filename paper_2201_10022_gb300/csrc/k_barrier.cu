@@ -20,9 +20,13 @@
 //     and of K = (Rm x I) H_r (Rm^T x I), find an eigenbasis of K by cyclic
 //     Jacobi in FP32 with round-robin ordering (n/2 disjoint rotations per
 //     round), then refine it in FP64: one Newton-Schulz step V (3I - V^T V)/2,
-//     K' = V^T K V, and FP64 round-robin Jacobi sweeps on the nearly diagonal
-//     K' until its off-diagonal mass is below 1e-11 of the total (squares
-//     below 1e-22).  Negative eigenvalues are clamped to zero.
+//     K' = V^T K V, a second FP32 Jacobi pass on K' (it resolves the lower
+//     levels of the spectrum, which the first pass on K / max|K| cannot see;
+//     scale-aware skip test, until a sweep takes no rotation) with the same
+//     FP64 basis update, and FP64 round-robin Jacobi sweeps on the nearly
+//     diagonal result until the couplings between its positive and
+//     non-positive diagonal entries are below 1e-11 of the total (squares
+//     below 1e-22); the clamp keeps the whole block on the positive entries.
 // A mollified edge-edge pair (near-parallel edges) is worked in the line-line
 // coordinates (n = 9) whatever its distance type.
 #include <math.h>
@@ -310,10 +314,14 @@ __device__ __forceinline__ void rot64(double app, double aqq, double apq, double
 // one round: n/2 disjoint rotations J (J_pp = J_qq = c, J_pq = s, J_qp = -s)
 // chosen to annihilate K_pq, applied as K <- J^T K J, V <- V J into the
 // other buffers.  rc[i] = J_ii, rs[i] = J_{partner(i), i}.
-template <int N, typename T>
-__device__ __forceinline__ void jacobi_round(int r, int lane, const T* Kc, T* Kn, const T* Vc, T* Vn, T* rc, T* rs,
+// rel (FP32 only): skip a rotation whose off-diagonal entry is below 1e-7 of
+// its diagonal pair (the scale-aware test of the second FP32 pass).  Returns
+// whether any rotation of the round was taken.
+template <int N, typename T, bool REL = false>
+__device__ __forceinline__ bool jacobi_round(int r, int lane, const T* Kc, T* Kn, const T* Vc, T* Vn, T* rc, T* rs,
                                              double sc) {
   constexpr int NP = N + (N & 1), last = NP - 1;
+  bool took = false;
   if (lane < NP / 2) {
     int p = lane == 0 ? r : (r + lane) % last;
     int q = lane == 0 ? last : (r - lane + last) % last;
@@ -324,8 +332,18 @@ __device__ __forceinline__ void jacobi_round(int r, int lane, const T* Kc, T* Kn
     }
     if (q < N) {
       T c, s;
-      if constexpr (sizeof(T) == 4) rot32(Kc[p * N + p], Kc[q * N + q], Kc[p * N + q], c, s);
-      else rot64(Kc[p * N + p], Kc[q * N + q], Kc[p * N + q], sc, c, s);
+      if constexpr (sizeof(T) == 4) {
+        const float app = Kc[p * N + p], aqq = Kc[q * N + q], apq = Kc[p * N + q];
+        if (REL && fabsf(apq) <= 1e-7f * sqrtf(fabsf(app * aqq))) {
+          c = 1.0f;
+          s = 0.0f;
+        } else {
+          rot32(app, aqq, apq, c, s);
+        }
+      } else {
+        rot64(Kc[p * N + p], Kc[q * N + q], Kc[p * N + q], sc, c, s);
+      }
+      took = s != T(0);
       rc[p] = c;
       rc[q] = c;
       rs[p] = -s;
@@ -346,6 +364,7 @@ __device__ __forceinline__ void jacobi_round(int r, int lane, const T* Kc, T* Kn
     Vn[e] = cb * Vc[a * N + b] + sb * Vc[a * N + pb];
   }
   __syncwarp();
+  return __ballot_sync(kAll, took) != 0;
 }
 
 template <typename T>
@@ -363,6 +382,22 @@ __device__ __forceinline__ void off_tot(const T* K, int lane, T& off, T& tot) {
     const T v = K[e] * K[e];
     tot += v;
     if (e / N != e - N * (e / N)) off += v;
+  }
+  off = warp_sum(off);
+  tot = warp_sum(tot);
+}
+
+// squares of the couplings between indices of opposite diagonal sign (the
+// only off-diagonal entries that change the clamp), and the total
+template <int N>
+__device__ __forceinline__ void off_cross_tot(const double* K, int lane, double& off, double& tot) {
+  off = 0.0;
+  tot = 0.0;
+  for (int e = lane; e < N * N; e += 32) {
+    const int a = e / N, b = e - N * (e / N);
+    const double v = K[e] * K[e];
+    tot += v;
+    if ((K[a * N + a] > 0.0) != (K[b * N + b] > 0.0)) off += v;
   }
   off = warp_sum(off);
   tot = warp_sum(tot);
@@ -594,6 +629,78 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
         const int a = e / N, b = e - N * (e / N);
         K[e] = 0.5 * (W.Kd[1][a * N + b] + W.Kd[1][b * N + a]);
       }
+      __syncwarp();
+      // second FP32 pass on K' (floating point keeps the lower levels of the
+      // spectrum, which the first pass on K / max|K| could not resolve), a
+      // scale-aware skip test, until a sweep takes no rotation; then the
+      // basis update in FP64: V2 <- V2 (3I - V2^T V2) / 2, K'' = V2^T K' V2,
+      // V = V' V2
+      {
+        double mx2 = 0.0;
+        for (int e = lane; e < N * N; e += 32) mx2 = fmax(mx2, fabs(K[e]));
+        for (int o = 16; o > 0; o >>= 1) mx2 = fmax(mx2, __shfl_xor_sync(kAll, mx2, o));
+        const double inv2 = 1.0 / mx2;
+        for (int e = lane; e < N * N; e += 32) {
+          W.K32[0][e] = (float)(K[e] * inv2);
+          W.V32[0][e] = (e / N == e - N * (e / N)) ? 1.0f : 0.0f;
+        }
+        __syncwarp();
+        int c2 = 0;
+        for (int sweep = 0; sweep < 5; ++sweep) {
+          bool any = false;
+          for (int r = 0; r < NP - 1; ++r) {
+            any |= jacobi_round<N, float, true>(r, lane, W.K32[c2], W.K32[c2 ^ 1], W.V32[c2], W.V32[c2 ^ 1], W.rc32,
+                                                W.rs32, 1.0);
+            c2 ^= 1;
+          }
+          ++n32;
+          if (!any) break;
+        }
+        double* V2 = W.Vd[0];  // free: the first basis lives in V1
+        for (int e = lane; e < N * N; e += 32) V2[e] = (double)W.V32[c2][e];
+        __syncwarp();
+        for (int e = lane; e < N * N; e += 32) {  // S = V2^T V2 into H
+          const int a = e / N, b = e - N * (e / N);
+          double t = 0.0;
+          for (int k = 0; k < N; ++k) t += V2[k * N + a] * V2[k * N + b];
+          W.H[e] = t;
+        }
+        __syncwarp();
+        double* V2n = W.Kd[1];
+        for (int e = lane; e < N * N; e += 32) {
+          const int a = e / N, b = e - N * (e / N);
+          double t = 1.5 * V2[a * N + b];
+          for (int k = 0; k < N; ++k) t -= 0.5 * V2[a * N + k] * W.H[k * N + b];
+          V2n[e] = t;
+        }
+        __syncwarp();
+        for (int e = lane; e < N * N; e += 32) {  // K' V2 into H
+          const int a = e / N, b = e - N * (e / N);
+          double t = 0.0;
+          for (int k = 0; k < N; ++k) t += K[a * N + k] * V2n[k * N + b];
+          W.H[e] = t;
+        }
+        __syncwarp();
+        for (int e = lane; e < N * N; e += 32) {  // K'' = V2^T (K' V2) into Vd[0]
+          const int a = e / N, b = e - N * (e / N);
+          double t = 0.0;
+          for (int k = 0; k < N; ++k) t += V2n[k * N + a] * W.H[k * N + b];
+          V2[e] = t;
+        }
+        __syncwarp();
+        for (int e = lane; e < N * N; e += 32) {  // V = V' V2 into H
+          const int a = e / N, b = e - N * (e / N);
+          double t = 0.0;
+          for (int k = 0; k < N; ++k) t += V1[a * N + k] * V2n[k * N + b];
+          W.H[e] = t;
+        }
+        __syncwarp();
+        for (int e = lane; e < N * N; e += 32) {
+          const int a = e / N, b = e - N * (e / N);
+          K[e] = 0.5 * (V2[a * N + b] + V2[b * N + a]);
+          V1[e] = W.H[e];
+        }
+      }
       // current: K in Kd[0], V in Vd[1]
       double* Kb[2] = {W.Kd[0], W.Kd[1]};
       double* Vb[2] = {W.Vd[1], W.Vd[0]};
@@ -601,7 +708,7 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
       __syncwarp();
       for (int sweep = 0; sweep <= 8; ++sweep) {
         double off, tot;
-        off_tot<N>(Kb[c64], lane, off, tot);
+        off_cross_tot<N>(Kb[c64], lane, off, tot);
         if (!(off > 1e-22 * tot)) break;
         if (sweep == 8) {  // cap reached: keep the last basis
           capped = 1;
@@ -618,17 +725,25 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
         atomicAdd(&st->jac[1], (unsigned long long)n64);
         if (capped) atomicAdd(&st->jac[2], 1ull);
       }
-      // Proj = V diag(max(lambda, 0)) V^T
+      // Proj = V P V^T with P the block of K'' on its positive diagonal
+      // entries: couplings inside that block are kept exactly, couplings to
+      // the clamped part are below the threshold above
       const double* Kf = Kb[c64];
       const double* Vf = Vb[c64];
       double* Pk = W.Kd[c64 ^ 1];
-      for (int e = lane; e < N * N; e += 32) {
+      for (int e = lane; e < N * N; e += 32) {  // T = V P into H
+        const int a = e / N, l = e - N * (e / N);
+        double t = 0.0;
+        if (Kf[l * N + l] > 0.0)
+          for (int k = 0; k < N; ++k)
+            if (Kf[k * N + k] > 0.0) t += Vf[a * N + k] * Kf[k * N + l];
+        W.H[e] = t;
+      }
+      __syncwarp();
+      for (int e = lane; e < N * N; e += 32) {  // T V^T
         const int a = e / N, b = e - N * (e / N);
         double t = 0.0;
-        for (int k = 0; k < N; ++k) {
-          const double lam = Kf[k * N + k];
-          if (lam > 0.0) t += Vf[a * N + k] * lam * Vf[b * N + k];
-        }
+        for (int l = 0; l < N; ++l) t += W.H[a * N + l] * Vf[b * N + l];
         Pk[e] = t;
       }
       __syncwarp();
