@@ -221,11 +221,11 @@ constexpr int kTermStride = 91;
 
 // algorithmic FP64 operations of one barrier term by reduced dimension m.
 // m = 1: derivatives, closed-form clamp, 91 outputs.  m = 2, 3: the n x n
-// Hessian entries, the Gram congruence, the Newton-Schulz step, the basis
-// change V^T K V, one FP64 round-robin Jacobi sweep, the clamped
-// reconstruction, the inverse congruence and the expansion to 12x12 (the
-// FP32 eigenbasis is not counted)
-constexpr double kBarrierFlops[4] = {0.0, 380.0, 7500.0, 25300.0};
+// Hessian entries, the Gram congruence, two FP64 basis updates (Newton-Schulz
+// and the change of basis, after each FP32 pass), the clamp as two products,
+// the inverse congruence and the expansion to 12x12 (the FP32 passes and the
+// rare FP64 sweeps are not counted)
+constexpr double kBarrierFlops[4] = {0.0, 380.0, 7000.0, 22100.0};
 
 // launch bookkeeping: count every kernel; with profiling on, bracket the
 // launches of a slot with events
