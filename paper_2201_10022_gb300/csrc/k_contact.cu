@@ -119,8 +119,7 @@ __device__ int fill_chunk(int t, int cur, int hi, const double* olo, const doubl
 // triangles (PT) or edges (EE) of body `qa`.
 __device__ void enum_kind(int kind, int p_lo, int p_hi, int q_lo, int q_hi, const Box& boxP, const Box& boxQ,
                           double dhat, const int* tri, const int* edge, const double4* x, const double4* x1,
-                          const double4* dx, WarpLists& L, int2* out, int maxc, int& base, bool ccd, double ccd_s,
-                          int ccd_max, double& tmin, DevStatus* st) {
+                          WarpLists& L, int2* out, int maxc, int& base) {
   const int lane = threadIdx.x & 31;
   const int tp = kind == 0 ? 0 : 1, tq = kind == 0 ? 2 : 1;
   int qc = q_lo;
@@ -147,18 +146,6 @@ __device__ void enum_kind(int kind, int p_lo, int p_hi, int q_lo, int q_hi, cons
           int pos = base + __popc(m & ((1u << lane) - 1u));
           int i = L.pid[pi], j = L.qid[qi];
           if (pos < maxc) out[pos] = make_int2(i | (kind << 31), j);
-          if (ccd) {
-            int v[4];
-            pair_vertices(kind, i, j, tri, edge, v);
-            v3 xs[4], ds[4];
-            for (int k = 0; k < 4; ++k) {
-              xs[k] = mk(x[v[k]]);
-              ds[k] = mk(dx[v[k]]);
-            }
-            double toi;
-            if (accd(kind, xs, ds, ccd_s, 1.0, ccd_max, toi)) set_flag(st, ST_CCD_MAXITER);
-            tmin = fmin(tmin, toi);
-          }
         }
         base += __popc(m);
       }
@@ -169,14 +156,13 @@ __device__ void enum_kind(int kind, int p_lo, int p_hi, int q_lo, int q_hi, cons
 
 __global__ void k_enumerate(const int2* __restrict__ P, const DevStatus* __restrict__ cst, const int* vbeg,
                             const int* tbeg, const int* ebeg, const int* tri, const int* edge, const double4* x,
-                            const double4* x1, const double4* dx, const double* bbox, double dhat, int maxc,
-                            int2* cand, int* ccount, bool ccd, double ccd_s, int ccd_max, DevStatus* st) {
+                            const double4* x1, const double* bbox, double dhat, int maxc, int2* cand, int* ccount,
+                            DevStatus* st) {
   __shared__ WarpLists lists[kWarpsPerBlock];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * kWarpsPerBlock;
   const int np = cst->np;
   WarpLists& L = lists[warp];
-  double tmin = 1.0;
   unsigned long long ncand = 0;
   for (int p = blockIdx.x * kWarpsPerBlock + warp; p < np; p += nwarps) {
     const int a = P[p].x, b = P[p].y;
@@ -190,13 +176,10 @@ __global__ void k_enumerate(const int2* __restrict__ P, const DevStatus* __restr
     int base = 0;
     int2* out = cand + (size_t)p * maxc;
     // vertices of a against triangles of b, vertices of b against triangles of a
-    enum_kind(0, vbeg[a], vbeg[a + 1], tbeg[b], tbeg[b + 1], Ba, Bb, dhat, tri, edge, x, x1, dx, L, out, maxc, base,
-              ccd, ccd_s, ccd_max, tmin, st);
-    enum_kind(0, vbeg[b], vbeg[b + 1], tbeg[a], tbeg[a + 1], Bb, Ba, dhat, tri, edge, x, x1, dx, L, out, maxc, base,
-              ccd, ccd_s, ccd_max, tmin, st);
+    enum_kind(0, vbeg[a], vbeg[a + 1], tbeg[b], tbeg[b + 1], Ba, Bb, dhat, tri, edge, x, x1, L, out, maxc, base);
+    enum_kind(0, vbeg[b], vbeg[b + 1], tbeg[a], tbeg[a + 1], Bb, Ba, dhat, tri, edge, x, x1, L, out, maxc, base);
     // edges of a against edges of b
-    enum_kind(1, ebeg[a], ebeg[a + 1], ebeg[b], ebeg[b + 1], Ba, Bb, dhat, tri, edge, x, x1, dx, L, out, maxc, base,
-              ccd, ccd_s, ccd_max, tmin, st);
+    enum_kind(1, ebeg[a], ebeg[a + 1], ebeg[b], ebeg[b + 1], Ba, Bb, dhat, tri, edge, x, x1, L, out, maxc, base);
     if (lane == 0) {
       ccount[p] = base;
       if (base > maxc) {
@@ -206,11 +189,40 @@ __global__ void k_enumerate(const int2* __restrict__ P, const DevStatus* __restr
     }
     ncand += base;
   }
-  if (ccd) {
-    for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_xor_sync(kFull, tmin, o));
-    if (lane == 0 && tmin < 1.0) atomicMin(&st->toi_bits, (unsigned long long)__double_as_longlong(tmin));
-  }
   if (lane == 0 && ncand) atomicAdd(&st->n_cand, ncand);
+}
+
+// additive CCD (Sec. 4.1) over the stored swept candidates: one warp per
+// (body pair, 32 candidates), the minimum time of impact by an atomic
+// minimum on the bits of the positive double (exact, order-independent)
+__global__ void k_ccd_chunks(const DevStatus* __restrict__ cst, const int2* cand, const int* ccount, const int* tri,
+                             const int* edge, const double4* x, const double4* dx, int maxc, int nch, double ccd_s,
+                             int ccd_max, DevStatus* st) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+  const long nw = (long)cst->np * nch;
+  double tmin = 1.0;
+  for (long w = (long)blockIdx.x * (blockDim.x >> 5) + warp; w < nw; w += nwarps) {
+    const int p = (int)(w / nch), c = (int)(w - (long)p * nch);
+    const int n = min(ccount[p], maxc);
+    const int k = c * 32 + lane;
+    if (k < n) {
+      const int2 cc = cand[(size_t)p * maxc + k];
+      const int kind = (unsigned)cc.x >> 31, i = cc.x & 0x7fffffff;
+      int v[4];
+      pair_vertices(kind, i, cc.y, tri, edge, v);
+      v3 xs[4], ds[4];
+      for (int m = 0; m < 4; ++m) {
+        xs[m] = mk(x[v[m]]);
+        ds[m] = mk(dx[v[m]]);
+      }
+      double toi;
+      if (accd(kind, xs, ds, ccd_s, 1.0, ccd_max, toi)) set_flag(st, ST_CCD_MAXITER);
+      tmin = fmin(tmin, toi);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_xor_sync(kFull, tmin, o));
+  if (lane == 0 && tmin < 1.0) atomicMin(&st->toi_bits, (unsigned long long)__double_as_longlong(tmin));
 }
 
 // active pairs: canonical d^2 < dhat^2, compacted per body pair in slot order
@@ -433,8 +445,14 @@ void launch_enumerate(Scene& s, bool swept, bool ccd) {
   counted(s);
   ProfScope ps(s, PF_ENUM);
   k_enumerate<<<grid, threads, 0, s.stream>>>(s.P.p, s.st, s.vbeg.p, s.tbeg.p, s.ebeg.p, s.tri.p, s.edge.p, s.x.p,
-                                              swept ? s.x1.p : nullptr, s.dx.p, s.bbox.p, s.prm.dhat, s.maxc,
-                                              s.cand.p, s.ccount.p, ccd, s.prm.ccd_s, s.prm.ccd_max, s.st);
+                                              swept ? s.x1.p : nullptr, s.bbox.p, s.prm.dhat, s.maxc, s.cand.p,
+                                              s.ccount.p, s.st);
+  if (ccd) {
+    const int nch = energy_chunks(s);
+    counted(s);
+    k_ccd_chunks<<<grid_for(2L * s.nb * nch, 8, 152 * 32), 256, 0, s.stream>>>(
+        s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, s.x.p, s.dx.p, s.maxc, nch, s.prm.ccd_s, s.prm.ccd_max, s.st);
+  }
 }
 
 void launch_active(Scene& s, const double4* x) {

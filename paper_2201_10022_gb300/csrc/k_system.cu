@@ -363,9 +363,14 @@ __global__ void k_rows_large(int nb, const uint8_t* is_static, const double* bbo
       const unsigned m = __ballot_sync(kFull, keep);
       if (lane == 0) wcount[w] = __popc(m);
       __syncthreads();
-      if (t == 0) {
-        wbase[0] = 0;
-        for (int k = 0; k < 32; ++k) wbase[k + 1] = wbase[k] + wcount[k];
+      if (w == 0) {  // warp offsets by an inclusive shuffle scan
+        int x = wcount[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, x, o);
+          if (lane >= o) x += y;
+        }
+        wbase[lane + 1] = x;
+        if (lane == 0) wbase[0] = 0;
       }
       __syncthreads();
       if (keep) {
@@ -641,7 +646,8 @@ __device__ int find_fpair(const int2* fp, int n, int a, int b) {
   return (lo < n && fp[lo].x == a && fp[lo].y == b) ? lo : -1;
 }
 
-__global__ void k_assemble(const DevStatus* __restrict__ cst, const int2* P, const int* aoff, const double* term,
+__global__ void __launch_bounds__(128) k_assemble(const DevStatus* __restrict__ cst, const int2* P, const int* aoff,
+                                                  const double* term,
                            const int4* termv, const int2* fpairs, const int* fpoff, const double* fterm,
                            const int4* ftermv, const int* vbody, const double4* xbar, double* pblk) {
   __shared__ double sH[8][kTermStride];
@@ -661,8 +667,17 @@ __global__ void k_assemble(const DevStatus* __restrict__ cst, const int2* P, con
         f1 = fpoff[q + 1];
       }
     }
-    double acc[15];
-    for (int k = 0; k < 15; ++k) acc[k] = 0.0;
+    // lanes 0..26: region r = lane / 9 (0: H_ab, 1: D_a, 2: D_b) and spatial
+    // component pair (c, c2) = ((lane % 9) / 3, lane % 3); each accumulates
+    // the 4x4 block over the weight indices (u, u2) of
+    //   sum_{k on side sk, l on side sl} w_k[u] w_l[u2] H_kl[c][c2]
+    // as two 4x4 products (T = W_sk^T H_c, then T W_sl) with the other side's
+    // weights zeroed; lanes 27..31: the 24 gradient entries and two energies
+    double acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+    const int r = lane / 9, cc = (lane % 9) / 3, c2 = lane % 3;
+    const int sk = r == 2 ? 1 : 0, sl = r == 1 ? 0 : 1;
     const int nterms = (t1 - t0) + (f1 - f0);
     for (int it = 0; it < nterms; ++it) {
       const bool fr = it >= (t1 - t0);
@@ -682,42 +697,68 @@ __global__ void k_assemble(const DevStatus* __restrict__ cst, const int2* P, con
       __syncwarp();
       const double* H = sH[wib] + 13;
       const double* g = sH[wib] + 1;
-      for (int k = 0; k < 15; ++k) {
-        const int o = lane + 32 * k;
-        if (o >= kBlkStride) break;
-        double c = 0.0;
-        if (o < 432) {
-          const int region = o / 144, e = o % 144;
-          const int sk = region == 2 ? 1 : 0, sl = region == 1 ? 0 : 1;
-          int u, cc, u2, c2;
-          inv_dof(e / 12, u, cc);
-          inv_dof(e % 12, u2, c2);
-          for (int kk = 0; kk < 4; ++kk) {
-            if (sside[wib][kk] != sk) continue;
-            const double wk = sw[wib][kk][u];
-            for (int ll = 0; ll < 4; ++ll) {
-              if (sside[wib][ll] != sl) continue;
-              c += wk * sw[wib][ll][u2] * H[up12(3 * kk + cc, 3 * ll + c2)];
-            }
+      if (lane < 27) {
+        double wk[4][4], wl[4][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            wk[k][u] = sside[wib][k] == sk ? sw[wib][k][u] : 0.0;
+            wl[k][u] = sside[wib][k] == sl ? sw[wib][k][u] : 0.0;
           }
-        } else if (o < 456) {
-          const int gi = o - 432, sd = gi / 12;
-          int u, cc;
-          inv_dof(gi % 12, u, cc);
-          for (int kk = 0; kk < 4; ++kk)
-            if (sside[wib][kk] == sd) c += sw[wib][kk][u] * g[3 * kk + cc];
-        } else if (o == 456) {
-          c = fr ? 0.0 : sH[wib][0];
-        } else {
-          c = fr ? sH[wib][0] : 0.0;
+        double Tm[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            double x = 0.0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x += wk[k][u] * H[up12(3 * k + cc, 3 * l + c2)];
+            Tm[u][l] = x;
+          }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int u2 = 0; u2 < 4; ++u2) {
+            double x = acc[4 * u + u2];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) x += Tm[u][l] * wl[l][u2];
+            acc[4 * u + u2] = x;
+          }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          const int gi = (lane - 27) + 5 * j;
+          double c = 0.0;
+          if (gi < 24) {
+            const int sd = gi / 12;
+            int u, ci;
+            inv_dof(gi % 12, u, ci);
+            for (int k = 0; k < 4; ++k)
+              if (sside[wib][k] == sd) c += sw[wib][k][u] * g[3 * k + ci];
+          } else if (gi == 24) {
+            c = fr ? 0.0 : sH[wib][0];
+          } else if (gi == 25) {
+            c = fr ? sH[wib][0] : 0.0;
+          }
+          acc[j] += c;
         }
-        acc[k] += c;
       }
       __syncwarp();
     }
-    for (int k = 0; k < 15; ++k) {
-      const int o = lane + 32 * k;
-      if (o < kBlkStride) pblk[(size_t)p * kBlkStride + o] = acc[k];
+    double* out = pblk + (size_t)p * kBlkStride;
+    if (lane < 27) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int u2 = 0; u2 < 4; ++u2)
+          out[144 * r + 12 * dof(u, cc) + dof(u2, c2)] = acc[4 * u + u2];
+    } else {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const int gi = (lane - 27) + 5 * j;
+        if (gi < 26) out[432 + gi] = acc[j];
+      }
     }
   }
 }
@@ -1391,7 +1432,7 @@ void launch_negate(Scene& s, const double* in, double* out, long n) {
 void launch_assemble(Scene& s) {
   counted(s);
   ProfScope pa(s, PF_ASSEMBLE);
-  k_assemble<<<152 * 8, 256, 0, s.stream>>>(s.st, s.P.p, s.aoff.p, s.term.p, s.termv.p, s.fpairs.p, s.fpoff.p,
+  k_assemble<<<152 * 16, 128, 0, s.stream>>>(s.st, s.P.p, s.aoff.p, s.term.p, s.termv.p, s.fpairs.p, s.fpoff.p,
                                             s.fterm.p, s.ftermv.p, s.vbody.p, s.xbar.p, s.pblk.p);
 }
 
