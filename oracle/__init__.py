@@ -86,6 +86,7 @@ def lib():
             "orc_pair_dist2": (d, [i, vp, vp]), "orc_barrier": (d, [d, d]),
             "orc_pair_barrier": (i, [i, vp, d, d, d, i, vp, vp, vp]),
             "orc_ee_cross2": (d, [vp]), "orc_ee_mollifier": (d, [d, d, vp, vp]),
+            "orc_adjoint_step": (i, [vp, vp, vp, vp, vp, vp, vp]),
             "orc_sym_eig": (None, [i, vp, vp, vp]), "orc_project_psd": (None, [i, vp]),
             "orc_accd": (i, [i, vp, vp, d, d, i, vp]),
             "orc_friction_pair": (d, [vp, vp, vp, vp, d, d, vp, vp]),
@@ -377,6 +378,17 @@ class Oracle:
         t = np.zeros(1)
         st = lib().orc_ccd_toi(self.ctx, _p(q), _p(dq), _p(t))
         return st, t[0]
+
+    def adjoint_step(self, q_t, qdot_t, q_next, rhs):
+        """one step backwards (implicit function theorem): returns (status,
+        M lam, dL/dkappa) with H(q_next) lam = rhs, H the unprojected Hessian
+        of the step that started at (q_t, qdot_t); leaves the state there"""
+        n = 12 * self.nb
+        args = [_f64(a, n) for a in (q_t, qdot_t, q_next, rhs)]
+        Mlam = np.zeros(n)
+        gk = np.zeros(self.nb)
+        st = lib().orc_adjoint_step(self.ctx, *[_p(a) for a in args], _p(Mlam), _p(gk))
+        return st, Mlam.reshape(-1, 12), gk
 
     def step(self, n=1):
         st = Stats()

@@ -116,6 +116,13 @@ int orc_solve(orc_ctx* c, const double* rhs, double* dq, int* iters); /* H dq = 
 int orc_ccd_toi(orc_ctx* c, const double* q, const double* dq, double* toi);
 int orc_step(orc_ctx* c, int nsteps, orc_stats* st);
 
+/* --- adjoint (implicit function theorem) ----------------------------------- */
+/* One step backwards: H(q_next) lam = rhs with the unprojected Hessian of the
+ * step that started at (q_t, qdot_t); returns M lam (12 nb) and dL/dkappa (nb).
+ * Leaves the context at state (q_t, qdot_t). */
+int orc_adjoint_step(orc_ctx* c, const double* q_t, const double* qdot_t, const double* q_next, const double* rhs,
+                     double* Mlam, double* gkappa);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1418,3 +1418,52 @@ int orc_step(orc_ctx* c, int nsteps, orc_stats* st) {
   }
   return ORC_OK;
 }
+
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of one step by the implicit function theorem.  The step's q^{t+1} */
+/* minimises E(q; q~) with q~ = q^t + dt qdot^t + dt^2 g, so grad E(q^{t+1}) */
+/* = 0 and, with H the unprojected Hessian there and H lam = dL/dq^{t+1},    */
+/* dL/dq~ = M lam and dL/dkappa_b = -dt^2 lam_b . grad V_b / kappa_b.  The   */
+/* lagged friction quantities are held fixed (their dependence on q^t is     */
+/* not differentiated).  Returns M lam per body (zero rows for static        */
+/* bodies) and dL/dkappa per body.                                          */
+/* ------------------------------------------------------------------------ */
+int orc_adjoint_step(orc_ctx* c, const double* q_t, const double* qdot_t, const double* q_next, const double* rhs,
+                     double* Mlam, double* gkappa) {
+  const orc_scene* s = &c->sc;
+  const int nb = s->nb;
+  int st = orc_set_state(c, q_t, qdot_t);
+  if (st != ORC_OK) return st;
+  double E[5];
+  double* g = (double*)calloc(12 * (size_t)nb, sizeof(double));
+  double* lam = (double*)calloc(12 * (size_t)nb, sizeof(double));
+  st = orc_energy_grad_hess(c, q_next, E, g, 0);
+  int iters = 0;
+  if (st == ORC_OK) st = orc_solve(c, rhs, lam, &iters);
+  const double dt2 = s->dt * s->dt;
+  for (int b = 0; b < nb; ++b) {
+    double* o = Mlam + 12 * b;
+    gkappa[b] = 0.0;
+    if (s->is_static[b] || st != ORC_OK) {
+      memset(o, 0, 12 * sizeof(double));
+      continue;
+    }
+    const double* M = c->M + 144 * b;
+    const double* l = lam + 12 * b;
+    for (int i = 0; i < 12; ++i) {
+      double t = 0.0;
+      for (int j = 0; j < 12; ++j) t += M[12 * i + j] * l[j];
+      o[i] = t;
+    }
+    double gv[12], Hv[144];
+    orc_ortho(q_next + 12 * b, c->kappa_body[b], c->vol[b], gv, Hv);
+    double t = 0.0;
+    for (int i = 0; i < 12; ++i) t += l[i] * gv[i];
+    gkappa[b] = -dt2 * t / c->kappa_body[b];
+  }
+  free(g);
+  free(lam);
+  return st;
+}
+

@@ -1,0 +1,131 @@
+"""Pins of the oracle's implicit-function adjoint of the time step: the
+closed form of free flight, and central finite differences of a multi-step
+loss through contact (frictionless: the lagged friction quantities are held
+fixed by the adjoint, so a finite difference of the step map with friction
+would also see their dependence on q^t)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2201_10022_gb300 import scenes
+
+
+def rollout(o, q0, qd0, n):
+    """forward with per-step checkpoints"""
+    o.set_state(q0, qd0)
+    states = [(q0.copy(), qd0.copy())]
+    for _ in range(n):
+        r, _ = o.step(1)
+        assert r == 0, O.ERRORS[r]
+        q, qd = o.get_state()
+        states.append((q.copy(), qd.copy()))
+    return states
+
+
+def backward(o, s, states, gq, gqd):
+    """chain of adjoint steps: dL/dq_{t+1} (total) -> M lam; dL/dq_t =
+    M lam - gqd/dt, dL/dqdot_t = dt M lam (q~ = q + dt qdot + dt^2 g,
+    qdot_{t+1} = (q_{t+1} - q_t)/dt)"""
+    dt = s.params["dt"]
+    gk = np.zeros(s.nb)
+    for t in range(len(states) - 2, -1, -1):
+        (qt, qdt), (qn, _) = states[t], states[t + 1]
+        rhs = gq + gqd / dt
+        st, Mlam, gkt = o.adjoint_step(qt, qdt, qn, rhs)
+        assert st == 0, O.ERRORS[st]
+        gq, gqd = Mlam - gqd / dt, dt * Mlam
+        gk += gkt
+    dyn = s.is_static == 0
+    gq[~dyn] = 0.0
+    gqd[~dyn] = 0.0
+    return gq, gqd, gk
+
+
+def _loss(states, s, target):
+    qK = states[-1][0]
+    dyn = s.is_static == 0
+    return float(np.sum((qK[dyn, :3].mean(axis=0) - target) ** 2))
+
+
+def _dloss(states, s, target):
+    qK = states[-1][0]
+    dyn = s.is_static == 0
+    m = qK[dyn, :3].mean(axis=0)
+    g = np.zeros_like(qK)
+    g[dyn, :3] = 2.0 * (m - target) / dyn.sum()
+    return g
+
+
+def test_free_flight_closed_form():
+    """no contact, A a rotation, centred bodies (M decouples p from A): the
+    translation of every step is p~_t, so dp_K / dpdot_0 = K dt I, and a
+    loss on translations back-propagates to K dt times itself with nothing
+    in the A rows; grad V = 0 on rotations gives dL/dkappa = 0"""
+    s = scenes.random_pair(5, kinds=("cube", "cube"), sep=0.5)
+    o = O.Oracle(s, newton_rel=1e-13)
+    n = 5
+    states = rollout(o, s.q0.copy(), s.qdot0.copy(), n)
+    rng = np.random.default_rng(0)
+    gq = np.zeros_like(s.q0)
+    gq[:, :3] = rng.normal(size=(s.nb, 3))
+    gq[s.is_static == 1] = 0.0
+    _, gqd0, gk = backward(o, s, states, gq, np.zeros_like(gq))
+    dt = s.params["dt"]
+    np.testing.assert_allclose(gqd0[:, :3], n * dt * gq[:, :3], rtol=1e-9, atol=1e-12)
+    assert np.abs(gqd0[:, 3:]).max() < 1e-9
+    assert np.abs(gk).max() < 1e-9
+
+
+def test_adjoint_matches_central_differences_through_contact():
+    # a cube in resting contact with a box, pushed sideways: the barrier is
+    # active at every step
+    B = scenes._Builder("adjoint", 0)
+    gv, gt = scenes.box_mesh(2.0, 2.0, 0.4)
+    B.add(gv, gt, p=(0.0, 0.0, -0.2), static=True)
+    cv, ct = scenes.cube_mesh(0.2)
+    B.add(cv, ct, R=scenes.small_rotation(np.random.default_rng(1), 2.0), p=(0.0, 0.0, 0.1 + 0.0012),
+          v=(0.4, -0.2, 0.05), kappa=1e6)
+    B.add(cv, ct, p=(0.35, 0.0, 0.1 + 0.0012), v=(-0.3, 0.1, 0.0), kappa=2e6)
+    s = B.build(dict(mu=0.0))
+    target = np.array([0.3, -0.1, 0.2])
+    n = 4
+    mk = lambda: O.Oracle(s, newton_rel=1e-14, newton_max=200)
+    o = mk()
+    states = rollout(o, s.q0.copy(), s.qdot0.copy(), n)
+    assert o.pairs(1)["kind"].size > 0  # contact active at the last state
+    _, gqd0, gk = backward(o, s, states, _dloss(states, s, target), np.zeros_like(s.q0))
+
+    def loss_at(qd0=None, kappa=None):
+        s2 = s
+        if kappa is not None:
+            s2 = scenes.Scene(**{**s.__dict__, "kappa_body": kappa})
+        o2 = O.Oracle(s2, newton_rel=1e-14, newton_max=200)
+        return _loss(rollout(o2, s.q0.copy(), qd0 if qd0 is not None else s.qdot0.copy(), n), s, target)
+
+    h = 1e-6
+    for b in (1, 2):
+        for k in (0, 1, 2, 3, 7, 11):
+            e = np.zeros_like(s.qdot0)
+            e[b, k] = h
+            fd = (loss_at(qd0=s.qdot0 + e) - loss_at(qd0=s.qdot0 - e)) / (2 * h)
+            assert gqd0[b, k] == pytest.approx(fd, rel=2e-4, abs=1e-9 * np.abs(gqd0).max()), (b, k)
+    for b in (1, 2):
+        kp = s.kappa_body.copy()
+        hk = 1e-5 * kp[b]
+        kp[b] += hk
+        km = s.kappa_body.copy()
+        km[b] -= hk
+        fd = (loss_at(kappa=kp) - loss_at(kappa=km)) / (2 * hk)
+        assert gk[b] == pytest.approx(fd, rel=2e-3, abs=1e-6 * np.abs(gk).max()), b
+
+
+def test_unprojected_hessian_is_positive_definite_at_the_step():
+    """at a converged step the unprojected IP Hessian is positive definite
+    here, so the adjoint's Cholesky solve applies"""
+    s = scenes.cube_stack(seed=1, gap=0.0004)
+    o = O.Oracle(s, newton_rel=1e-13)
+    states = rollout(o, s.q0.copy(), s.qdot0.copy(), 2)
+    o.set_state(*states[1])
+    st, E, g = o.energy_grad_hess(states[2][0].reshape(-1), project=False)
+    H = o.dense_hessian()
+    assert np.linalg.eigvalsh(H).min() > 0
