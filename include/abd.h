@@ -208,6 +208,25 @@ ABD_API abd_status abd_step(abd_scene* s, int nsteps, abd_step_stats* stats);
 ABD_API abd_status abd_set_profiling(abd_scene* s, int on);
 ABD_API abd_status abd_get_profile(abd_scene* s, abd_kernel_profile* out, int cap, int* n);
 
+/* Adjoint of one time step by the implicit function theorem (differentiating
+ * through the step's minimisation of the IP, Sec. 4).  The step started at
+ * (q_t, qdot_t) and ended at q_next; with H the UNPROJECTED Hessian of its IP
+ * at q_next (body blocks M + dt^2 hess V_ortho, barrier terms without the PSD
+ * clamp, friction with its lagged quantities held fixed) and
+ *   rhs = dL/dq_next + dL/dqdot_next / dt   (qdot_next = (q_next - q_t)/dt),
+ * it solves H lam = rhs by the block-Jacobi PCG to rel_tol and, since
+ * dL/dq~ = M lam (q~ = q_t + dt qdot_t + dt^2 g):
+ *   gq    <- M lam - dL/dqdot_next / dt          (dL/dq_t)
+ *   gqdot <- dt M lam                            (dL/dqdot_t)
+ *   gkappa += -dt^2 lam_b . grad V_b / kappa_b   (per body)
+ * gq_dev / gqdot_dev (12 nb, device) hold dL/dq_next, dL/dqdot_next on entry
+ * and are overwritten; gkappa_dev (nb, device) is accumulated; static rows are
+ * zero.  Leaves the scene's state at (q_t, qdot_t).  Errors as abd_solve
+ * (ABD_ERR_PCG_BREAKDOWN if H is not positive definite along the iterates). */
+ABD_API abd_status abd_adjoint_step(abd_scene* s, const double* q_t_dev, const double* qdot_t_dev,
+                                    const double* q_next_dev, double* gq_dev, double* gqdot_dev, double* gkappa_dev,
+                                    double rel_tol, abd_solve_stats* stats);
+
 /* Work counters of the barrier-term kernel, cumulative since the scene was
  * created (diagnostics of the eigen-projection's cost; no effect on
  * results).  Synchronises the scene's stream. */

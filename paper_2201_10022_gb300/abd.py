@@ -78,8 +78,8 @@ def _as_dict(st):
 _lib = None
 EXPORTS = ["abd_default_params", "abd_create_scene", "abd_destroy", "abd_set_state", "abd_get_state",
            "abd_energy_grad_hess", "abd_get_hessian", "abd_get_pairs", "abd_solve", "abd_ccd_toi", "abd_step",
-           "abd_set_profiling", "abd_get_profile", "abd_get_counters", "abd_ccd_toi_pairs_noalloc",
-           "abd_last_error"]
+           "abd_set_profiling", "abd_get_profile", "abd_get_counters", "abd_adjoint_step",
+           "abd_ccd_toi_pairs_noalloc", "abd_last_error"]
 
 
 def lib_path() -> str:
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = True):
         "abd_set_profiling": (i, [vp, i]),
         "abd_get_profile": (i, [vp, vp, i, vp]),
         "abd_get_counters": (i, [vp, vp]),
+        "abd_adjoint_step": (i, [vp, vp, vp, vp, vp, vp, vp, d, vp]),
         "abd_ccd_toi_pairs_noalloc": (i, [vp, vp, i, vp, vp, l, d, i, vp, vp]),
         "abd_last_error": (C.c_char_p, [vp]),
     }
@@ -191,6 +192,11 @@ def abd_get_profile(h, out, cap, n):
 
 def abd_get_counters(h, out):
     return load().abd_get_counters(h, out)
+
+
+def abd_adjoint_step(h, q_t, qdot_t, q_next, gq, gqdot, gkappa, rel_tol, stats):
+    return load().abd_adjoint_step(h, C.c_void_p(q_t), C.c_void_p(qdot_t), C.c_void_p(q_next), C.c_void_p(gq),
+                                   C.c_void_p(gqdot), C.c_void_p(gkappa), float(rel_tol), stats)
 
 
 def abd_ccd_toi_pairs_noalloc(x_ptr, dx_ptr, nv, verts_ptr, kind_ptr, npairs, ccd_s, ccd_max, stream, toi):
@@ -373,6 +379,20 @@ class AbdScene:
         return {arr[k].name.decode(): dict(launches=arr[k].launches, total_ms=arr[k].total_ms, bytes=arr[k].bytes,
                                            flops=arr[k].flops)
                 for k in range(min(n.value, 16))}
+
+    def adjoint_step(self, q_t, qdot_t, q_next, gq, gqdot, gkappa, rel_tol=1e-12):
+        """one step backwards (see abd_adjoint_step): gq, gqdot (nb x 12) hold
+        dL/dq_next, dL/dqdot_next and receive dL/dq_t, dL/dqdot_t; gkappa (nb)
+        accumulates dL/dkappa_body.  All float64 tensors on the scene's device."""
+        st = abd_solve_stats()
+        args = [self._dev(t) for t in (q_t, qdot_t, q_next)]
+        for t in (gq, gqdot, gkappa):
+            if t.device != self.device or t.dtype != self.torch.float64 or not t.is_contiguous():
+                raise ValueError("gq, gqdot, gkappa: contiguous float64 tensors on the scene's device")
+        with self.torch.cuda.device(self.device):
+            self._check(abd_adjoint_step(self.h, *[a.data_ptr() for a in args], gq.data_ptr(), gqdot.data_ptr(),
+                                         gkappa.data_ptr(), rel_tol, C.byref(st)))
+        return _as_dict(st)
 
     def counters(self):
         c = abd_counters()

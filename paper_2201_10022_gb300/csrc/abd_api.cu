@@ -186,7 +186,7 @@ void eval_system(Scene& s, const double* q, int project) {
   launch_friction_eval(s, s.x.p, true);
   launch_incoming(s);
   launch_assemble(s);
-  launch_body_terms(s, q, true);
+  launch_body_terms(s, q, true, project != 0);
   launch_gather(s);
   launch_precond(s);
   launch_energy_total(s, true);
@@ -994,6 +994,44 @@ abd_status abd_get_profile(abd_scene* S, abd_kernel_profile* out, int cap, int* 
     out[k].flops = k == PF_BARRIER ? bar_flops : 0.0;
   }
   return check_cuda(s);
+}
+
+abd_status abd_adjoint_step(abd_scene* S, const double* q_t, const double* qdot_t, const double* q_next, double* gq,
+                            double* gqdot, double* gkappa, double rel_tol, abd_solve_stats* stats) {
+  if (!S || !q_t || !qdot_t || !q_next || !gq || !gqdot || !gkappa || !(rel_tol > 0.0)) return ABD_ERR_INVALID_ARG;
+  Scene& s = S->s;
+  if (abd_status r = abd_set_state(S, q_t, qdot_t, 1)) return r;
+  // unprojected system of the step at its end state
+  abd_status r = with_capacity(s, [&]() {
+    launch_transform(s, q_next, s.x.p);
+    broad_and_enumerate(s, false, false);
+    s.fp32_proj = false;
+    eval_system(s, q_next, 0);
+    return ABD_OK;
+  });
+  if (r != ABD_OK) return r;
+  if (abd_status f = flags_to_status(s, s.st_host->flags & ~ST_CCD_MAXITER)) return f;
+  s.have_hess = false;  // not the projected system abd_solve expects
+  s.last_np = s.st_host->np;
+  launch_adjoint_rhs(s, gq, gqdot, s.qsave.p);
+  double rel;
+  const int its = run_pcg(s, s.qsave.p, s.dq.p, s.prm.pcg_max, rel_tol, &rel);
+  launch_adjoint_out(s, q_next, s.dq.p, gq, gqdot, gkappa);
+  cudaStreamSynchronize(s.stream);
+  if (stats) {
+    stats->iterations = its < 0 ? s.prm.pcg_max : its;
+    stats->rel_residual = rel;
+  }
+  if (abd_status c = check_cuda(s)) return c;
+  if (its == -2) {
+    s.err = "PCG breakdown (Hessian not positive definite along the iterates)";
+    return ABD_ERR_PCG_BREAKDOWN;
+  }
+  if (its == -1) {
+    s.err = "PCG iteration cap reached";
+    return ABD_ERR_PCG_MAXITER;
+  }
+  return ABD_OK;
 }
 
 abd_status abd_get_counters(abd_scene* S, abd_counters* out) {

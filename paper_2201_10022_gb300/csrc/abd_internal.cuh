@@ -267,7 +267,9 @@ void launch_body_boxes(Scene& s, bool swept);
 void launch_body_pairs(Scene& s);                       // rows -> P (uses friction pairs)
 void launch_incoming(Scene& s);
 void launch_assemble(Scene& s);
-void launch_body_terms(Scene& s, const double* q, bool hess);
+void launch_body_terms(Scene& s, const double* q, bool hess, bool project = true);
+void launch_adjoint_rhs(Scene& s, const double* gq, const double* gqd, double* rhs);
+void launch_adjoint_out(Scene& s, const double* q, const double* lam, double* gq, double* gqd, double* gkappa);
 void launch_gather(Scene& s);
 void launch_precond(Scene& s);
 void launch_energy_total(Scene& s, bool with_pairs);

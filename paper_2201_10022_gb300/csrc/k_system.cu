@@ -1436,7 +1436,7 @@ void launch_assemble(Scene& s) {
                                             s.fterm.p, s.ftermv.p, s.vbody.p, s.xbar.p, s.pblk.p);
 }
 
-void launch_body_terms(Scene& s, const double* q, bool hess) {
+void launch_body_terms(Scene& s, const double* q, bool hess, bool project) {
   counted(s);
   ProfScope pb(s, PF_BODY);
   k_body_terms<<<blocks(s.nb, 64), 64, 0, s.stream>>>(s.nb, s.is_static.p, q, s.qtilde.p, s.mass10.p, s.vol.p,
@@ -1446,7 +1446,7 @@ void launch_body_terms(Scene& s, const double* q, bool hess) {
     cudaMemsetAsync(reinterpret_cast<char*>(s.st) + offsetof(DevStatus, bh_fix), 0, sizeof(int), s.stream);
     k_body_hess<<<blocks(s.nb, kBodyWarp), kBodyWarp, 0, s.stream>>>(s.nb, s.is_static.p, q, s.mass10.p, s.vol.p,
                                                                      s.kappa_b.p, s.prm.dt, s.Db.p, s.hfix.p, s.st);
-    k_body_hess_fix<<<1, 32, 0, s.stream>>>(s.st, s.hfix.p, s.Db.p);
+    if (project) k_body_hess_fix<<<1, 32, 0, s.stream>>>(s.st, s.hfix.p, s.Db.p);
   }
 }
 
@@ -1535,6 +1535,77 @@ int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_
 }
 
 __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+
+// adjoint of a step: rhs = dL/dq_next + dL/dqdot_next / dt (dynamic rows)
+__global__ void k_adj_rhs(int n, const uint8_t* is_static, const double* gq, const double* gqd, double dt,
+                          double* rhs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) rhs[i] = is_static[i / 12] ? 0.0 : gq[i] + gqd[i] / dt;
+}
+
+// adjoint of a step: M lam, then dL/dq_t = M lam - dL/dqdot_next / dt,
+// dL/dqdot_t = dt M lam, dL/dkappa_b += -dt^2 lam_b . grad V_b / kappa_b
+// with grad V / kappa = 4 nu sum_j (a_i . a_j - delta_ij) a_j at q_next
+__global__ void k_adj_out(int nb, const uint8_t* is_static, const double* mass10, const double* vol,
+                          const double* q, double dt, const double* lam, double* gq, double* gqd, double* gkappa) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  if (is_static[b]) {
+    for (int k = 0; k < 12; ++k) gq[12 * b + k] = gqd[12 * b + k] = 0.0;
+    return;
+  }
+  const double* m = mass10 + 10 * b;
+  const double W[4][4] = {{m[0], m[1], m[2], m[3]}, {m[1], m[4], m[5], m[6]}, {m[2], m[5], m[7], m[8]},
+                          {m[3], m[6], m[8], m[9]}};
+  double l[12], Ml[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) l[k] = lam[12 * b + k];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      double t = 0.0;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) t += W[u][v] * l[dof(v, c)];
+      Ml[dof(u, c)] = t;
+    }
+  double A[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A[i][c] = q[12 * b + 3 + 3 * i + c];
+  double dot = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double gi = 0.0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double Gij = A[i][0] * A[j][0] + A[i][1] * A[j][1] + A[i][2] * A[j][2] - (i == j ? 1.0 : 0.0);
+        gi += Gij * A[j][c];
+      }
+      dot += l[3 + 3 * i + c] * 4.0 * vol[b] * gi;
+    }
+  gkappa[b] += -dt * dt * dot;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const double g_v = gqd[12 * b + k];
+    gq[12 * b + k] = Ml[k] - g_v / dt;
+    gqd[12 * b + k] = dt * Ml[k];
+  }
+}
+
+void launch_adjoint_rhs(Scene& s, const double* gq, const double* gqd, double* rhs) {
+  counted(s);
+  k_adj_rhs<<<blocks(12L * s.nb, 256), 256, 0, s.stream>>>(12 * s.nb, s.is_static.p, gq, gqd, s.prm.dt, rhs);
+}
+
+void launch_adjoint_out(Scene& s, const double* q, const double* lam, double* gq, double* gqd, double* gkappa) {
+  counted(s);
+  k_adj_out<<<blocks(s.nb, 128), 128, 0, s.stream>>>(s.nb, s.is_static.p, s.mass10.p, s.vol.p, q, s.prm.dt, lam, gq,
+                                                     gqd, gkappa);
+}
 
 // the CCD minimum starts at 1 (a whole step)
 void launch_reset_toi(Scene& s) {

@@ -1,0 +1,136 @@
+"""CUDA implicit-function adjoint (abd_adjoint_step, the Rollout autograd
+function) against the oracle's adjoint and against central finite
+differences of the CUDA forward map, on a frictionless contact scene."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2201_10022_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def abd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_10022_gb300 import abd as A
+    A.load()
+    return A
+
+
+def contact_scene():
+    B = scenes._Builder("adjoint", 0)
+    gv, gt = scenes.box_mesh(2.0, 2.0, 0.4)
+    B.add(gv, gt, p=(0.0, 0.0, -0.2), static=True)
+    cv, ct = scenes.cube_mesh(0.2)
+    B.add(cv, ct, R=scenes.small_rotation(np.random.default_rng(1), 2.0), p=(0.0, 0.0, 0.1 + 0.0012),
+          v=(0.4, -0.2, 0.05), kappa=1e6)
+    B.add(cv, ct, p=(0.35, 0.0, 0.1 + 0.0012), v=(-0.3, 0.1, 0.0), kappa=2e6)
+    return B.build(dict(mu=0.0))
+
+
+TARGET = np.array([0.3, -0.1, 0.2])
+NSTEPS = 4
+
+
+def oracle_states(s):
+    o = O.Oracle(s, newton_rel=1e-14, newton_max=200)
+    o.set_state(s.q0, s.qdot0)
+    states = [(s.q0.copy(), s.qdot0.copy())]
+    for _ in range(NSTEPS):
+        r, _ = o.step(1)
+        assert r == 0, O.ERRORS[r]
+        q, qd = o.get_state()
+        states.append((q.copy(), qd.copy()))
+    return o, states
+
+
+def dloss(s, qK):
+    dyn = s.is_static == 0
+    g = np.zeros_like(qK)
+    g[dyn, :3] = 2.0 * (qK[dyn, :3].mean(axis=0) - TARGET) / dyn.sum()
+    return g
+
+
+def oracle_backward(o, s, states, gq, gqd):
+    dt = s.params["dt"]
+    gk = np.zeros(s.nb)
+    for t in range(len(states) - 2, -1, -1):
+        (qt, qdt), (qn, _) = states[t], states[t + 1]
+        st, Mlam, gkt = o.adjoint_step(qt, qdt, qn, gq + gqd / dt)
+        assert st == 0, O.ERRORS[st]
+        gq, gqd = Mlam - gqd / dt, dt * Mlam
+        gk += gkt
+    gq[s.is_static == 1] = 0.0
+    gqd[s.is_static == 1] = 0.0
+    return gq, gqd, gk
+
+
+def test_adjoint_steps_match_oracle(abd):
+    s = contact_scene()
+    o, states = oracle_states(s)
+    gq0, gqd0, gk0 = oracle_backward(o, s, states, dloss(s, states[-1][0]), np.zeros_like(s.q0))
+    gpu = abd.AbdScene(s)
+    dev = gpu.device
+    gq = torch.tensor(dloss(s, states[-1][0]), device=dev)
+    gqd = torch.zeros_like(gq)
+    gk = torch.zeros(s.nb, dtype=torch.float64, device=dev)
+    for t in range(NSTEPS - 1, -1, -1):
+        (qt, qdt), (qn, _) = states[t], states[t + 1]
+        st = gpu.adjoint_step(qt, qdt, qn, gq, gqd, gk)
+        assert st["rel_residual"] <= 1e-11
+    scale = np.abs(gqd0).max()
+    np.testing.assert_allclose(gqd.cpu().numpy(), gqd0, rtol=0, atol=1e-9 * scale)
+    np.testing.assert_allclose(gq.cpu().numpy(), gq0, rtol=0, atol=1e-9 * np.abs(gq0).max())
+    np.testing.assert_allclose(gk.cpu().numpy(), gk0, rtol=0, atol=1e-9 * np.abs(gk0).max())
+
+
+def _rollout_grads(abd, s):
+    from paper_2201_10022_gb300.autograd import Rollout
+    orc = O.Oracle(s)
+    # a tight Newton and linear tolerance: the finite differences below see
+    # the forward map's solver noise
+    gpu = abd.AbdScene(s, newton_tol=1e-5 * orc.newton_tol, pcg_rel_tol=1e-12)
+    dev = gpu.device
+    q0 = torch.tensor(s.q0, device=dev, requires_grad=True)
+    qd0 = torch.tensor(s.qdot0, device=dev, requires_grad=True)
+    kb = torch.tensor(s.kappa_body, device=dev, requires_grad=True)
+    qK, _ = Rollout.apply(gpu, NSTEPS, q0, qd0, kb)
+    dyn = torch.tensor(s.is_static == 0, device=dev)
+    loss = ((qK[dyn, :3].mean(dim=0) - torch.tensor(TARGET, device=dev)) ** 2).sum()
+    loss.backward()
+    return gpu, loss.item(), qd0.grad.cpu().numpy(), kb.grad.cpu().numpy()
+
+
+def test_rollout_gradient_matches_oracle(abd):
+    s = contact_scene()
+    o, states = oracle_states(s)
+    _, gqd0, gk0 = oracle_backward(o, s, states, dloss(s, states[-1][0]), np.zeros_like(s.q0))
+    _, _, gqd, gk = _rollout_grads(abd, s)
+    np.testing.assert_allclose(gqd, gqd0, rtol=0, atol=1e-7 * np.abs(gqd0).max())
+    np.testing.assert_allclose(gk, gk0, rtol=0, atol=1e-7 * np.abs(gk0).max())
+
+
+def test_rollout_gradient_matches_central_differences(abd):
+    s = contact_scene()
+    gpu, _, gqd, gk = _rollout_grads(abd, s)
+    dyn = s.is_static == 0
+
+    def loss(qd0):
+        gpu.set_state(torch.tensor(s.q0), torch.tensor(qd0))
+        gpu.step(NSTEPS)
+        qK = gpu.get_state()[0].cpu().numpy()
+        return float(np.sum((qK[dyn, :3].mean(axis=0) - TARGET) ** 2))
+
+    h = 1e-6
+    for b in (1, 2):
+        for k in (0, 1, 2, 4, 9):
+            e = np.zeros_like(s.qdot0)
+            e[b, k] = h
+            fd = (loss(s.qdot0 + e) - loss(s.qdot0 - e)) / (2 * h)
+            # absolute floor: the finite-difference noise of the loss (~1e-15)
+            # over 2h, against components down to 1e-9 of the largest
+            assert gqd[b, k] == pytest.approx(fd, rel=2e-4, abs=2e-7 * np.abs(gqd).max()), (b, k)
