@@ -133,6 +133,73 @@ def bbox_diag(x):
     return float(np.linalg.norm(x.max(axis=0) - x.min(axis=0)))
 
 
+def adjoint_run(dev, nsteps=100, seed=4, budget_s=60.0):
+    """Throw into a stack (64 thrown cubes, 10-cube stack, FP64): forward and
+    implicit-function backward through nsteps steps; loss = squared distance
+    of the thrown cubes' mean final translation to a seeded target; gradients
+    with respect to their initial velocities and the per-body kappa.  The
+    forward uses the library's inexact-Newton defaults; the adjoint solves run
+    to 1e-8 within 2000 PCG iterations; two velocity components are checked
+    by central differences (h = 1e-4, matched to the inexact forward map's
+    noise) while the run stays within budget_s."""
+    import torch
+    from paper_2201_10022_gb300 import scenes
+    from paper_2201_10022_gb300.abd import AbdError, AbdScene
+    from paper_2201_10022_gb300.autograd import Rollout
+
+    s = scenes.throw_stack(seed=seed)
+    thrown = np.arange(s.nb - 64, s.nb)
+    target = np.random.default_rng(seed).uniform([-1.0, -0.5, 0.0], [0.0, 0.5, 0.5])
+    g = AbdScene(s, device=dev, pcg_max=2000)
+    g.adjoint_rel_tol = 1e-8
+    tgt = torch.tensor(target, device=dev)
+    idx = torch.tensor(thrown, device=dev)
+    out = {"workload": f"throw_stack seed {seed}: 64 thrown + 10 stacked 0.2 m cubes, {nsteps} steps, FP64, mu 0"}
+
+    def loss_of(qK):
+        return ((qK[idx, :3].mean(dim=0) - tgt) ** 2).sum()
+
+    t_start = time.perf_counter()
+    try:
+        q0 = torch.tensor(s.q0, device=dev, requires_grad=True)
+        qd0 = torch.tensor(s.qdot0, device=dev, requires_grad=True)
+        kb = torch.tensor(s.kappa_body, device=dev, requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qK, _ = Rollout.apply(g, nsteps, q0, qd0, kb)
+        loss = loss_of(qK)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+    except AbdError as e:
+        out["error"] = str(e)
+        g.close()
+        return out
+    gv = qd0.grad[idx, :3].cpu().numpy()
+    out.update({"forward_ms_per_step": 1e3 * (t1 - t0) / nsteps, "backward_ms_per_step": 1e3 * (t2 - t1) / nsteps,
+                "loss": loss.item(), "grad_v0_norm": float(np.linalg.norm(gv)),
+                "grad_kappa_norm": float(kb.grad.norm().item())})
+    checks = []
+    h = 1e-4
+    for b, k in ((int(thrown[0]), 0), (int(thrown[-1]), 2)):
+        if time.perf_counter() - t_start > budget_s:
+            break
+        vals = []
+        for sgn in (1.0, -1.0):
+            qd = s.qdot0.copy()
+            qd[b, k] += sgn * h
+            g.set_state(torch.tensor(s.q0), torch.tensor(qd))
+            g.step(nsteps)
+            vals.append(loss_of(g.get_state()[0]).item())
+        checks.append({"body": b, "component": k, "adjoint": float(qd0.grad[b, k].item()),
+                       "central_difference": (vals[0] - vals[1]) / (2 * h)})
+    out["fd_checks"] = checks
+    g.close()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -248,6 +315,8 @@ def run_abd(args, rank, world):
                               "energies, gradients, CCD, Newton test and line search FP64"}
         gm.close()
 
+    adjoint = adjoint_run(dev) if args.adjoint else None
+
     steps_total = args.steps * world
     ms_per_step = total_ms / steps_total
     newton = sum(st["newton_iters"] for st in stats)
@@ -297,6 +366,7 @@ def run_abd(args, rank, world):
         "kernel_ms": {k: round(v["total_ms"], 3) for k, v in prof.items()},
         "barrier_counters": cnt,
         "mixed": mixed,
+        "adjoint": adjoint,
         "clocks": clocks,
     }
     return out
@@ -311,6 +381,8 @@ def main():
     ap.add_argument("--impl", default="abd", choices=["abd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision run")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="also run the throw-into-stack adjoint (slow: block-Jacobi PCG on the 10-cube stack)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

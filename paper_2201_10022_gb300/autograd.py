@@ -10,7 +10,9 @@ q~ = q + dt qdot + dt^2 g and qdot_next = (q_next - q) / dt), and returns the
 gradients with respect to ``q0``, ``qdot0`` and the per-body orthogonality
 stiffness ``kappa_body``.  The lagged friction quantities of each step are
 held fixed.  ``kappa_body`` must hold the scene's values (the scene is built
-with them); it is an input only so that its gradient can be returned.
+with them); it is an input only so that its gradient can be returned.  The
+adjoint solves run to ``scene.adjoint_rel_tol`` (default 1e-12) within the
+scene's PCG iteration cap.
 """
 from __future__ import annotations
 
@@ -44,6 +46,7 @@ class Rollout(torch.autograd.Function):
         gq = (gq_out if gq_out is not None else torch.zeros_like(qs[0])).to(dev, torch.float64).contiguous().clone()
         gqd = (gqd_out if gqd_out is not None else torch.zeros_like(qs[0])).to(dev, torch.float64).contiguous().clone()
         gk = torch.zeros(scene.nb, dtype=torch.float64, device=dev)
+        rel_tol = getattr(scene, "adjoint_rel_tol", 1e-12)
         for t in range(qs.shape[0] - 2, -1, -1):
-            scene.adjoint_step(qs[t], qds[t], qs[t + 1], gq, gqd, gk)
+            scene.adjoint_step(qs[t], qds[t], qs[t + 1], gq, gqd, gk, rel_tol=rel_tol)
         return None, None, gq, gqd, gk
