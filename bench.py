@@ -122,6 +122,23 @@ def oracle_sample(start_step, warmup, steps, dims=(6, 6, 3)):
             "seconds": dt}
 
 
+def max_over_ranks(x, world, device):
+    """the largest value of x over the ranks of the job (the slowest rank's
+    time); x itself on a single rank"""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_ms_per_step(total_ms, steps, world):
+    """replicas: every rank steps its own copy of the scene, so the job
+    advances steps * world scene-steps in the slowest rank's time"""
+    return total_ms / (steps * world)
+
+
 def vertices(s, q):
     """world vertex positions x = A xbar + p for body states q (nb, 12)"""
     q = np.asarray(q).reshape(-1, 12)
@@ -260,11 +277,7 @@ def run_abd(args, rank, world):
     prof = g.profile()
     g.set_profiling(False)
     cnt = g.counters()
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ms), world, dev)
 
     # ---- end to end through the C ABI with host buffers -------------------
     qh = torch.empty((s.nb, 12), dtype=torch.float64).pin_memory()
@@ -280,11 +293,7 @@ def run_abd(args, rank, world):
         r = r or abd_get_state(g.h, qh.data_ptr(), qdh.data_ptr(), 0)
         if r:
             raise RuntimeError(f"e2e step failed: {r}")
-    e2e_ms = 1e3 * (time.perf_counter() - t0)
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), world, dev)
 
     # ---- mixed precision (precision = 1): the same steps from the same state;
     # the end state is compared with the FP64 run's (the e2e pass above)
@@ -318,7 +327,7 @@ def run_abd(args, rank, world):
     adjoint = adjoint_run(dev) if args.adjoint else None
 
     steps_total = args.steps * world
-    ms_per_step = total_ms / steps_total
+    ms_per_step = aggregate_ms_per_step(total_ms, args.steps, world)
     newton = sum(st["newton_iters"] for st in stats)
     cand = sum(st["candidates_tested"] for st in stats)
     act = sum(st["active_evaluated"] for st in stats)
