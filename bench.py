@@ -220,6 +220,69 @@ def adjoint_run(dev, nsteps=100, seed=4, budget_s=60.0):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def batched_run(dev, steps=2, pre_steps=10, seed=5, n_scenes=256):
+    """Many independent scenes (log-uniform 16..2048 bodies of 0.2 m cubes and
+    radius-0.1 m icosphere-2s per scene, lattice-pile layouts, seeded
+    velocities, frictionless), advanced pre_steps steps, then timed over
+    `steps` steps from one saved state three ways: the plain FP64 path one
+    scene after another (one host worker, full-device grids); the FP64 batch
+    (autotuned workers and grid divisor: bit-identical results); and the
+    mixed-precision batch.  Wall-clock around each batch call, which returns
+    once every scene's stream has drained."""
+    import torch
+    from paper_2201_10022_gb300 import scenes
+    from paper_2201_10022_gb300.batch import SceneBatch
+
+    t0 = time.perf_counter()
+    S = scenes.scene_batch(seed=seed, n_scenes=n_scenes)
+    nb = np.array([s.nb - 1 for s in S])
+    B = SceneBatch(S, device=dev)
+    B.step(pre_steps)
+    saved = [(q.clone(), qd.clone()) for q, qd in B.get_states()]
+    setup_s = time.perf_counter() - t0
+
+    def timed(batch, nworkers, grid_div):
+        batch.set_tuning(nworkers=nworkers, grid_div=grid_div)
+        batch.set_states(saved)
+        batch.step(1)  # capture of the launch sequences at this shape
+        batch.set_states(saved)
+        ms, st = batch.time_steps(steps)
+        return ms, st
+
+    ms_seq, st_seq = timed(B, 1, 1)
+    tune = B.tune(trial_steps=1, use_cache=False, write_cache=False)
+    ms_b, st_b = timed(B, tune["nworkers"], tune["grid_div"])
+    q_b = [q.clone() for q, _ in B.get_states()]
+    B.close()
+    Bm = SceneBatch(S, device=dev, precision=1)
+    ms_m, st_m = timed(Bm, tune["nworkers"], tune["grid_div"])  # the FP64 batch's launch shape
+    dev_max = 0.0
+    for s, qb, (qm, _) in zip(S, q_b, Bm.get_states()):
+        x0 = vertices(s, qb.cpu().numpy())
+        dev_max = max(dev_max, float(np.abs(vertices(s, qm.cpu().numpy()) - x0).max() / bbox_diag(x0)))
+    Bm.close()
+    newton = sum(st["newton_iters"] for st in st_b)
+    return {
+        "workload": f"{n_scenes} scenes seed {seed}: {int(nb.sum())} bodies (per scene {int(nb.min())}..{int(nb.max())}, "
+                    f"median {int(np.median(nb))}), {sum(s.nv for s in S)} vertices, steps {pre_steps + 1}.."
+                    f"{pre_steps + steps} timed, mu 0",
+        "steps": steps,
+        "sequential_fp64_ms_per_step": ms_seq / steps,
+        "batched_fp64_ms_per_step": ms_b / steps,
+        "batched_mixed_ms_per_step": ms_m / steps,
+        "speedup_batched_fp64_vs_sequential": ms_seq / ms_b,
+        "scene_steps_per_s_batched_fp64": n_scenes * steps / (ms_b * 1e-3),
+        "newton_iters_per_s_batched_fp64": newton / (ms_b * 1e-3),
+        "newton_iters_per_scene_step": newton / (n_scenes * steps),
+        "mixed_max_vertex_deviation_vs_fp64_over_scene_lbbox": dev_max,
+        "tuning": {"nworkers": tune["nworkers"], "grid_div": tune["grid_div"],
+                   "trials": [(t["nworkers"], t["grid_div"], round(t["ms"], 1)) for t in tune["trials"]]},
+        "gpu_launches": sum(st["kernel_launches"] for st in st_b),
+        "setup_s": setup_s,
+        "timing": "wall clock around abd_step_batch (returns after every scene's stream drained)",
+    }
+
+
 def run_abd(args, rank, world):
     import torch
     from paper_2201_10022_gb300.abd import AbdScene, abd_get_state, abd_set_state, abd_step, abd_step_stats
@@ -325,6 +388,7 @@ def run_abd(args, rank, world):
         gm.close()
 
     adjoint = adjoint_run(dev) if args.adjoint else None
+    batched = None if args.no_batched else batched_run(dev)
 
     steps_total = args.steps * world
     ms_per_step = aggregate_ms_per_step(total_ms, args.steps, world)
@@ -376,6 +440,7 @@ def run_abd(args, rank, world):
         "barrier_counters": cnt,
         "mixed": mixed,
         "adjoint": adjoint,
+        "batched": batched,
         "clocks": clocks,
     }
     return out
@@ -390,6 +455,7 @@ def main():
     ap.add_argument("--impl", default="abd", choices=["abd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision run")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-scene batch run")
     ap.add_argument("--adjoint", action="store_true",
                     help="also run the throw-into-stack adjoint (slow: block-Jacobi PCG on the 10-cube stack)")
     args = ap.parse_args()

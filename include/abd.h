@@ -201,6 +201,37 @@ ABD_API abd_status abd_ccd_toi(abd_scene* s, const double* q_dev, const double* 
  * receives the statistics of the last step. */
 ABD_API abd_status abd_step(abd_scene* s, int nsteps, abd_step_stats* stats);
 
+/* Launch shape of a scene's kernels.  grid_div divides the grids that are
+ * sized by the device rather than by a host-known count (kernels that
+ * grid-stride over a count held on the device: barrier terms, assembly
+ * blocks, friction records, incoming-pair lists); 1 = one full wave per
+ * kernel class (the default), larger values leave SMs to the kernels of
+ * other scenes stepped concurrently.  Results do not depend on it (every
+ * such kernel writes per-item outputs or exact integer reductions).  Values
+ * outside 1..64 return ABD_ERR_INVALID_ARG.  The scene's captured launch
+ * sequences are re-captured on its next step. */
+typedef struct {
+  int grid_div;
+  int reserved[7];   /* zero */
+} abd_tuning;
+ABD_API abd_status abd_set_tuning(abd_scene* s, const abd_tuning* t);
+ABD_API abd_status abd_get_tuning(const abd_scene* s, abd_tuning* t);
+
+/* Step a batch of independent scenes nsteps each (the many-scene form of
+ * Sec. 4's time step: every scene keeps its own Newton loop, line search
+ * and convergence, so each result is bit-identical to abd_step on that scene
+ * alone).  nworkers host threads (1..256) take scenes, largest body count
+ * first, and drive each on its own stream; scenes must have distinct streams
+ * for their work to overlap on the GPU, and must be created on the same
+ * device.  status (n entries, may be NULL) receives each scene's result;
+ * stats (n entries, may be NULL) each scene's abd_step_stats.  Returns
+ * ABD_OK if every scene succeeded, else the first failing scene's status in
+ * batch order (the other scenes still run; a failed scene is left at its
+ * state before the failing step, as abd_step leaves it).  No other call may
+ * use these scenes until it returns. */
+ABD_API abd_status abd_step_batch(abd_scene* const* scenes, int n, int nsteps, int nworkers, abd_status* status,
+                                  abd_step_stats* stats);
+
 /* Profiling (the step's tracing facility): on != 0 starts recording CUDA
  * events around each launch of the timed kernel classes and clears the
  * accumulators; 0 stops.  abd_get_profile synchronises the stream and fills

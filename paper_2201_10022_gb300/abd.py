@@ -70,6 +70,10 @@ class abd_counters(C.Structure):
                 ("sweeps_fp64", C.c_ulonglong), ("capped_fp64", C.c_ulonglong)]
 
 
+class abd_tuning(C.Structure):
+    _fields_ = [("grid_div", C.c_int), ("reserved", C.c_int * 7)]
+
+
 def _as_dict(st):
     return {k: (list(getattr(st, k)) if isinstance(getattr(st, k), C.Array) else getattr(st, k))
             for k, _ in st._fields_}
@@ -79,7 +83,7 @@ _lib = None
 EXPORTS = ["abd_default_params", "abd_create_scene", "abd_destroy", "abd_set_state", "abd_get_state",
            "abd_energy_grad_hess", "abd_get_hessian", "abd_get_pairs", "abd_solve", "abd_ccd_toi", "abd_step",
            "abd_set_profiling", "abd_get_profile", "abd_get_counters", "abd_adjoint_step",
-           "abd_ccd_toi_pairs_noalloc", "abd_last_error"]
+           "abd_ccd_toi_pairs_noalloc", "abd_set_tuning", "abd_get_tuning", "abd_step_batch", "abd_last_error"]
 
 
 def lib_path() -> str:
@@ -113,6 +117,9 @@ def load(build_if_missing: bool = True):
         "abd_get_counters": (i, [vp, vp]),
         "abd_adjoint_step": (i, [vp, vp, vp, vp, vp, vp, vp, d, vp]),
         "abd_ccd_toi_pairs_noalloc": (i, [vp, vp, i, vp, vp, l, d, i, vp, vp]),
+        "abd_set_tuning": (i, [vp, vp]),
+        "abd_get_tuning": (i, [vp, vp]),
+        "abd_step_batch": (i, [vp, i, i, i, vp, vp]),
         "abd_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -204,6 +211,21 @@ def abd_ccd_toi_pairs_noalloc(x_ptr, dx_ptr, nv, verts_ptr, kind_ptr, npairs, cc
     return load().abd_ccd_toi_pairs_noalloc(C.c_void_p(x_ptr), C.c_void_p(dx_ptr), int(nv), C.c_void_p(verts_ptr),
                                             C.c_void_p(kind_ptr), int(npairs), float(ccd_s), int(ccd_max),
                                             C.c_void_p(stream), toi)
+
+
+def abd_set_tuning(h, tuning):
+    return load().abd_set_tuning(h, C.byref(tuning))
+
+
+def abd_get_tuning(h, tuning):
+    return load().abd_get_tuning(h, C.byref(tuning))
+
+
+def abd_step_batch(handles, nsteps, nworkers, status, stats):
+    """handles: sequence of scene handles; status: (c_int * n) or None;
+    stats: (abd_step_stats * n) or None"""
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    return load().abd_step_batch(arr, len(handles), int(nsteps), int(nworkers), status, stats)
 
 
 def abd_last_error(h) -> str:
@@ -393,6 +415,16 @@ class AbdScene:
             self._check(abd_adjoint_step(self.h, *[a.data_ptr() for a in args], gq.data_ptr(), gqdot.data_ptr(),
                                          gkappa.data_ptr(), rel_tol, C.byref(st)))
         return _as_dict(st)
+
+    def set_tuning(self, grid_div=1):
+        t = abd_tuning()
+        t.grid_div = int(grid_div)
+        self._check(abd_set_tuning(self.h, t))
+
+    def tuning(self):
+        t = abd_tuning()
+        self._check(abd_get_tuning(self.h, t))
+        return {"grid_div": t.grid_div}
 
     def counters(self):
         c = abd_counters()

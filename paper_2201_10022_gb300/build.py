@@ -54,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     objs = [os.path.join(OUT, s.replace(".cu", ".o")) for s in SOURCES]
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+        r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"], capture_output=True, text=True)
         if r.returncode:
             print(r.stdout, r.stderr)
             raise RuntimeError("link of libabd.so failed")

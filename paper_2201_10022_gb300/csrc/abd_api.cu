@@ -7,6 +7,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <numeric>
+#include <thread>
 #include <vector>
 
 #include "abd_internal.cuh"
@@ -511,6 +514,7 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
   s.ne = ne;
   s.stream = (cudaStream_t)stream;
   s.alloc.stream = s.stream;
+  cudaGetDevice(&s.device);
   if (alloc && alloc->alloc && alloc->free) {
     s.alloc.a = *alloc;
     s.alloc.custom = true;
@@ -955,6 +959,75 @@ abd_status abd_step(abd_scene* S, int nsteps, abd_step_stats* stats) {
   acc.kernel_launches = s.nlaunch - launches0;
   if (stats) *stats = acc;
   return check_cuda(s);
+}
+
+abd_status abd_set_tuning(abd_scene* S, const abd_tuning* t) {
+  if (!S || !t || t->grid_div < 1 || t->grid_div > 64) return ABD_ERR_INVALID_ARG;
+  Scene& s = S->s;
+  if (t->grid_div != s.grid_div) {
+    s.grid_div = t->grid_div;
+    ++s.gen;  // the captured sequences hold the old grids
+  }
+  return ABD_OK;
+}
+
+abd_status abd_get_tuning(const abd_scene* S, abd_tuning* t) {
+  if (!S || !t) return ABD_ERR_INVALID_ARG;
+  memset(t, 0, sizeof(*t));
+  t->grid_div = S->s.grid_div;
+  return ABD_OK;
+}
+
+abd_status abd_step_batch(abd_scene* const* scenes, int n, int nsteps, int nworkers, abd_status* status,
+                          abd_step_stats* stats) {
+  if (n < 0 || nsteps < 0 || nworkers < 1 || nworkers > 256 || (n > 0 && !scenes)) return ABD_ERR_INVALID_ARG;
+  std::vector<abd_scene*> uniq(scenes, scenes + n);
+  std::sort(uniq.begin(), uniq.end());
+  if (n && !uniq[0]) return ABD_ERR_INVALID_ARG;
+  if (std::adjacent_find(uniq.begin(), uniq.end()) != uniq.end()) return ABD_ERR_INVALID_ARG;
+  // largest scenes first: the longest jobs start early (list scheduling)
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return scenes[a]->s.nb > scenes[b]->s.nb; });
+  std::vector<abd_status> res(n, ABD_OK);
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    int dev = -1;
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= n) break;
+      const int i = order[k];
+      Scene& s = scenes[i]->s;
+      try {
+        if (s.device != dev) {
+          cudaSetDevice(s.device);
+          dev = s.device;
+        }
+        res[i] = abd_step(scenes[i], nsteps, stats ? &stats[i] : nullptr);
+      } catch (...) {
+        s.err = "host allocation failed";
+        res[i] = ABD_ERR_OOM;
+      }
+    }
+  };
+  const int nw = std::min(nworkers, n);
+  if (nw <= 1) {
+    int dev0 = 0;
+    cudaGetDevice(&dev0);
+    work();
+    cudaSetDevice(dev0);
+  } else {
+    std::vector<std::thread> pool;
+    pool.reserve(nw);
+    for (int w = 0; w < nw; ++w) pool.emplace_back(work);
+    for (auto& t : pool) t.join();
+  }
+  abd_status first = ABD_OK;
+  for (int i = 0; i < n; ++i) {
+    if (status) status[i] = res[i];
+    if (first == ABD_OK && res[i] != ABD_OK) first = res[i];
+  }
+  return first;
 }
 
 static const char* kSlotNames[PF_COUNT] = {"enumerate_ccd", "active_set", "barrier_terms", "friction_terms",

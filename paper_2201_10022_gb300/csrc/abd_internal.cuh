@@ -143,6 +143,8 @@ struct Scene {
   Segment seg_sys[2], seg_trial;
   Alloc alloc;
   cudaStream_t stream = nullptr;
+  int device = 0;    // CUDA device the scene was created on
+  int grid_div = 1;  // divisor of the device-sized grids (abd_tuning)
   std::string err;
 
   // topology and body constants
@@ -234,6 +236,14 @@ inline void counted(Scene& s, int n = 1) { s.nlaunch += n; }
 
 // chunks of 32 candidate slots per body pair (energy-only pass partial sums)
 inline int energy_chunks(const Scene& s) { return (s.maxc + 31) / 32; }
+
+// grid of a kernel that grid-strides over a count held on the device:
+// per_sm blocks on each of the 152 SMs, divided by the scene's grid_div
+constexpr int kNumSMs = 152;
+inline int sm_grid(const Scene& s, int per_sm) {
+  const int g = kNumSMs * per_sm / s.grid_div;
+  return g < 1 ? 1 : g;
+}
 struct ProfScope {
   Scene& s;
   int slot;

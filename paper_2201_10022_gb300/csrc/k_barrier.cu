@@ -881,10 +881,10 @@ void launch_barrier(Scene& s, int project, long cap) {
   counted(s, 2);
   ProfScope ps(s, PF_BARRIER);
   cudaMemsetAsync(reinterpret_cast<char*>(s.st) + offsetof(DevStatus, bar_cnt), 0, sizeof(int) * 4, s.stream);
-  k_bar_classify<<<152 * 8, 256, 0, s.stream>>>(s.st, s.aoff.p, s.act.p, s.act_d2.p, s.tri.p, s.edge.p, s.x.p,
+  k_bar_classify<<<sm_grid(s, 8), 256, 0, s.stream>>>(s.st, s.aoff.p, s.act.p, s.act_d2.p, s.tri.p, s.edge.p, s.x.p,
                                                 s.l2e.p, s.maxc, cap, s.termv.p, s.tmeta.p, s.teps.p, s.td2.p,
                                                 s.tlist.p, s.st);
-  k_barrier<<<152 * 8, 32 * kBarWarps, 0, s.stream>>>(s.st, s.tlist.p, cap, s.termv.p, s.tmeta.p, s.teps.p, s.td2.p,
+  k_barrier<<<sm_grid(s, 8), 32 * kBarWarps, 0, s.stream>>>(s.st, s.tlist.p, cap, s.termv.p, s.tmeta.p, s.teps.p, s.td2.p,
                                                       s.x.p,
                                                       s.prm.dhat, s.prm.kappa, project, s.fp32_proj ? 1 : 0,
                                                       gram, s.term.p, s.st);

@@ -441,7 +441,7 @@ int grid_for(long n, int per_block, int max_blocks) {
 
 void launch_enumerate(Scene& s, bool swept, bool ccd) {
   const int threads = 32 * kWarpsPerBlock;
-  int grid = grid_for(2L * s.nb, kWarpsPerBlock, 152 * 16);  // grid-stride over the device's pair count
+  int grid = grid_for(2L * s.nb, kWarpsPerBlock, sm_grid(s, 16));  // grid-stride over the device's pair count
   counted(s);
   ProfScope ps(s, PF_ENUM);
   k_enumerate<<<grid, threads, 0, s.stream>>>(s.P.p, s.st, s.vbeg.p, s.tbeg.p, s.ebeg.p, s.tri.p, s.edge.p, s.x.p,
@@ -450,13 +450,13 @@ void launch_enumerate(Scene& s, bool swept, bool ccd) {
   if (ccd) {
     const int nch = energy_chunks(s);
     counted(s);
-    k_ccd_chunks<<<grid_for(2L * s.nb * nch, 8, 152 * 32), 256, 0, s.stream>>>(
+    k_ccd_chunks<<<grid_for(2L * s.nb * nch, 8, sm_grid(s, 32)), 256, 0, s.stream>>>(
         s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, s.x.p, s.dx.p, s.maxc, nch, s.prm.ccd_s, s.prm.ccd_max, s.st);
   }
 }
 
 void launch_active(Scene& s, const double4* x) {
-  int grid = grid_for(2L * s.nb, 8, 152 * 16);  // grid-stride over the device's pair count
+  int grid = grid_for(2L * s.nb, 8, sm_grid(s, 16));  // grid-stride over the device's pair count
   counted(s);
   ProfScope ps(s, PF_ACTIVE);
   k_active<<<grid, 256, 0, s.stream>>>(s.P.p, s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.prm.dhat, s.maxc,
@@ -465,7 +465,7 @@ void launch_active(Scene& s, const double4* x) {
 
 void launch_friction_lag(Scene& s) {
   counted(s);
-  k_friction_lag<<<152 * 4, 128, 0, s.stream>>>(s.st, s.P.p, s.aoff.p, s.act.p, s.act_d2.p, s.tri.p, s.edge.p,
+  k_friction_lag<<<sm_grid(s, 4), 128, 0, s.stream>>>(s.st, s.P.p, s.aoff.p, s.act.p, s.act_d2.p, s.tri.p, s.edge.p,
                                                s.vbody.p, s.x.p, s.l2e.p, s.prm.dhat, s.prm.kappa, s.prm.mu, s.maxc,
                                                s.fric.p);
 }
@@ -473,13 +473,13 @@ void launch_friction_lag(Scene& s) {
 void launch_friction_eval(Scene& s, const double4* x, bool derivs) {
   counted(s);
   ProfScope ps(s, PF_FRICTION);
-  k_friction_eval<<<152 * 4, 128, 0, s.stream>>>(s.st, s.fric.p, x, s.prm.eps_v * s.prm.dt, s.fterm.p,
+  k_friction_eval<<<sm_grid(s, 4), 128, 0, s.stream>>>(s.st, s.fric.p, x, s.prm.eps_v * s.prm.dt, s.fterm.p,
                                                 s.ftermv.p, derivs);
 }
 
 void launch_pair_energy(Scene& s, const double4* x) {
   const int nch = energy_chunks(s);
-  int grid = grid_for(2L * s.nb * nch, 8, 152 * 32);  // grid-stride over the device's pair count
+  int grid = grid_for(2L * s.nb * nch, 8, sm_grid(s, 32));  // grid-stride over the device's pair count
   counted(s);
   k_pair_energy<<<grid, 256, 0, s.stream>>>(s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.l2e.p,
                                             s.prm.dhat, s.prm.kappa, s.maxc, nch, s.Epair.p, s.st);

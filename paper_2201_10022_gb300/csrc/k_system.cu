@@ -1399,25 +1399,25 @@ void launch_body_pairs(Scene& s) {
 void launch_incoming(Scene& s) {
   cudaMemsetAsync(s.in_cnt.p, 0, sizeof(int) * s.nb, s.stream);
   counted(s);
-  k_in_count<<<152 * 4, 256, 0, s.stream>>>(s.st, s.P.p, s.in_cnt.p);
+  k_in_count<<<sm_grid(s, 4), 256, 0, s.stream>>>(s.st, s.P.p, s.in_cnt.p);
   counted(s);
   k_scan<<<1, 1024, 0, s.stream>>>(s.in_cnt.p, s.in_off.p, nullptr, s.nb, &s.st->pad, (long)s.P.cap, 0,
                                    &s.st->need_misc, s.st);
   cudaMemsetAsync(s.in_cnt.p, 0, sizeof(int) * s.nb, s.stream);
   counted(s);
-  k_in_fill<<<152 * 4, 256, 0, s.stream>>>(s.st, s.P.p, s.in_off.p, s.in_cnt.p, s.in_list.p);
+  k_in_fill<<<sm_grid(s, 4), 256, 0, s.stream>>>(s.st, s.P.p, s.in_off.p, s.in_cnt.p, s.in_list.p);
   counted(s);
   k_in_sort<<<blocks(s.nb, 128), 128, 0, s.stream>>>(s.nb, s.in_off.p, s.in_list.p);
 }
 
 void launch_fpairs(Scene& s) {
   counted(s);
-  k_flag_active<<<152 * 4, 256, 0, s.stream>>>(s.st, s.acount.p, s.flagbuf.p);
+  k_flag_active<<<sm_grid(s, 4), 256, 0, s.stream>>>(s.st, s.acount.p, s.flagbuf.p);
   counted(s);
   k_scan<<<1, 1024, 0, s.stream>>>(s.flagbuf.p, s.posbuf.p, &s.st->np, 0, &s.st->nfp, (long)s.fpairs.cap,
                                    ST_CAP_PAIRS, &s.st->need_misc, s.st);
   counted(s);
-  k_fpairs<<<152 * 4, 256, 0, s.stream>>>(s.st, s.P.p, s.flagbuf.p, s.posbuf.p, s.aoff.p, s.fpairs.p, s.fpoff.p);
+  k_fpairs<<<sm_grid(s, 4), 256, 0, s.stream>>>(s.st, s.P.p, s.flagbuf.p, s.posbuf.p, s.aoff.p, s.fpairs.p, s.fpoff.p);
 }
 
 __global__ void k_negate(long n, const double* in, double* out) {
@@ -1432,7 +1432,7 @@ void launch_negate(Scene& s, const double* in, double* out, long n) {
 void launch_assemble(Scene& s) {
   counted(s);
   ProfScope pa(s, PF_ASSEMBLE);
-  k_assemble<<<152 * 16, 128, 0, s.stream>>>(s.st, s.P.p, s.aoff.p, s.term.p, s.termv.p, s.fpairs.p, s.fpoff.p,
+  k_assemble<<<sm_grid(s, 16), 128, 0, s.stream>>>(s.st, s.P.p, s.aoff.p, s.term.p, s.termv.p, s.fpairs.p, s.fpoff.p,
                                             s.fterm.p, s.ftermv.p, s.vbody.p, s.xbar.p, s.pblk.p);
 }
 

@@ -201,12 +201,12 @@ class _Builder:
         self.nv = 0
 
     def add(self, verts, tris, R=None, p=(0, 0, 0), v=(0, 0, 0), density=1000.0,
-            kappa=1e8, static=False):
+            kappa=1e8, static=False, edges=None):
         b = len(self.q0)
         R = np.eye(3) if R is None else np.asarray(R, dtype=np.float64)
         self.xbar.append(np.asarray(verts, dtype=np.float64))
         self.tri.append(np.asarray(tris, dtype=np.int32) + self.nv)
-        self.edge.append(mesh_edges(np.asarray(tris)) + self.nv)
+        self.edge.append((mesh_edges(np.asarray(tris)) if edges is None else edges) + self.nv)
         self.vbody.append(np.full(len(verts), b, dtype=np.int32))
         q = np.zeros(12)
         q[:3] = p
@@ -391,6 +391,49 @@ def random_pair(seed: int, kinds=("cube", "ico1"), sep: float = 0.0005, **params
     p1 = s0 + sep * n - s1
     B.add(v1, t1, R=R1, p=p1)
     return B.build(params)
+
+
+def scene_batch(seed: int = 5, n_scenes: int = 256, nmin: int = 16, nmax: int = 2048, pitch: float = 0.5,
+                jitter: float = 0.05, z0: float = 0.3, vel_sigma: float = 0.5, ground: float = 40.0,
+                types=("cube", "ico2"), **params) -> list:
+    """Independent scenes of uneven size: per scene a body count N drawn
+    log-uniformly from [nmin, nmax], then the lattice-pile layout (jittered
+    lattice, uniform rotations, bottom layers filled first) of N bodies of the
+    given types (0.2 m cubes, radius-0.1 m icospheres) over a static ground,
+    with translational velocities N(0, vel_sigma) per component.  Scene k
+    draws from the generator seeded (seed, k).  The pitch clears the largest
+    rotated extent (cube half-diagonal 0.173 m) plus the jitter on both
+    sides, so no pair starts closer than d-hat."""
+    meshes = {"cube": cube_mesh(0.2), "ico1": icosphere_mesh(1, 0.1), "ico2": icosphere_mesh(2, 0.1)}
+    edges = {k: mesh_edges(np.asarray(t)) for k, (_, t) in meshes.items()}
+    gv, gt = box_mesh(ground, ground, 1.0)
+    out = []
+    for k in range(n_scenes):
+        rng = np.random.default_rng([seed, k])
+        n = int(round(np.exp(rng.uniform(np.log(nmin), np.log(nmax)))))
+        nz = max(1, int(np.ceil(n ** (1.0 / 3.0))))
+        nx = int(np.ceil(np.sqrt(n / nz)))
+        ny = int(np.ceil(n / (nx * nz)))
+        B = _Builder(f"scene_batch_{k}", seed)
+        B.add(gv, gt, p=(0.0, 0.0, -0.5), static=True)
+        placed = 0
+        for iz in range(nz):
+            for iy in range(ny):
+                for ix in range(nx):
+                    if placed == n:
+                        break
+                    kind = types[int(rng.integers(len(types)))]
+                    R = random_rotation(rng)
+                    p = np.array([(ix - 0.5 * (nx - 1)) * pitch, (iy - 0.5 * (ny - 1)) * pitch,
+                                  z0 + iz * pitch]) + rng.uniform(-jitter, jitter, size=3)
+                    v = rng.normal(0.0, vel_sigma, size=3)
+                    verts, tris = meshes[kind]
+                    B.add(verts, tris, R=R, p=p, v=v, edges=edges[kind])
+                    placed += 1
+        prm = dict(mu=0.0)
+        prm.update(params)
+        out.append(B.build(prm))
+    return out
 
 
 RECIPES = {
