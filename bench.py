@@ -437,7 +437,14 @@ def run_abd(args, rank, world):
         "gpu_launches": launches,
         "roofline": roof,
         "kernel_ms": {k: round(v["total_ms"], 3) for k, v in prof.items()},
-        "barrier_counters": cnt,
+        "barrier_counters": {k: cnt[k] for k in ("barrier_terms", "sweeps_fp32", "sweeps_fp64", "capped_fp64")},
+        "culling": {"prim_pairs_of_body_pairs": cnt["prim_pairs_body"],
+                    "prim_pairs_after_iaabb": cnt["prim_pairs_iaabb"],
+                    "candidates": cnt["prim_pairs_cand"],
+                    "iaabb_kept_frac": cnt["prim_pairs_iaabb"] / max(cnt["prim_pairs_body"], 1),
+                    "candidates_frac_of_iaabb": cnt["prim_pairs_cand"] / max(cnt["prim_pairs_iaabb"], 1),
+                    "scope": "every enumeration since the scene was created (pre-roll, warm-up, timed and "
+                             "profiled steps)"},
         "mixed": mixed,
         "adjoint": adjoint,
         "batched": batched,

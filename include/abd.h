@@ -266,6 +266,15 @@ typedef struct {
   unsigned long long sweeps_fp32;      /* FP32 Jacobi sweeps over all 6- and 9-dimensional terms */
   unsigned long long sweeps_fp64;      /* FP64 refinement sweeps over the same terms */
   unsigned long long capped_fp64;      /* terms whose FP64 sweeps reached the sweep cap */
+  /* culling of the candidate enumeration (Sec. 4.2), summed over every
+   * enumeration pass: all primitive pairs (point-triangle both ways,
+   * edge-edge) of the body pairs whose d-hat-dilated boxes overlap; the pairs
+   * left after restricting each body's primitives to the other body's box
+   * (the i-AABB intersection test); the candidates passing the exact
+   * primitive box test */
+  unsigned long long prim_pairs_body;
+  unsigned long long prim_pairs_iaabb;
+  unsigned long long prim_pairs_cand;
 } abd_counters;
 ABD_API abd_status abd_get_counters(abd_scene* s, abd_counters* out);
 

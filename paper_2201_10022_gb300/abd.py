@@ -67,7 +67,9 @@ class abd_kernel_profile(C.Structure):
 
 class abd_counters(C.Structure):
     _fields_ = [("barrier_terms", C.c_ulonglong * 4), ("sweeps_fp32", C.c_ulonglong),
-                ("sweeps_fp64", C.c_ulonglong), ("capped_fp64", C.c_ulonglong)]
+                ("sweeps_fp64", C.c_ulonglong), ("capped_fp64", C.c_ulonglong),
+                ("prim_pairs_body", C.c_ulonglong), ("prim_pairs_iaabb", C.c_ulonglong),
+                ("prim_pairs_cand", C.c_ulonglong)]
 
 
 class abd_tuning(C.Structure):

@@ -181,25 +181,35 @@ void broad_and_enumerate(Scene& s, bool swept, bool ccd) {
   launch_enumerate(s, swept, ccd);
 }
 
-// actives, terms, assembly and preconditioner at positions s.x (from q)
+// actives, terms, assembly and preconditioner at positions s.x (from q):
+// the body terms and the incoming-pair lists (which need only q and the
+// body pairs) and the friction terms (only x) run beside the active set and
+// the barrier terms, and join before the assembly
 void eval_system(Scene& s, const double* q, int project) {
+  on_side(s, 0, 0, [&]() {
+    launch_body_terms(s, q, true, project != 0);
+    launch_incoming(s);
+  });
+  on_side(s, 1, 1, [&]() { launch_friction_eval(s, s.x.p, true); });
   launch_active(s, s.x.p);
   launch_scan(s, s.acount.p, s.aoff.p, &s.st->np, &s.st->nact, (long)term_cap(s), ST_CAP_ACTIVE, &s.st->need_act);
   launch_barrier(s, project, (long)term_cap(s));
-  launch_friction_eval(s, s.x.p, true);
-  launch_incoming(s);
+  join_side(s, 0, 0);
+  join_side(s, 1, 1);
   launch_assemble(s);
-  launch_body_terms(s, q, true, project != 0);
   launch_gather(s);
   launch_precond(s);
   launch_energy_total(s, true);
 }
 
-// energy only at positions s.xt (from qv), over the stored candidates
+// energy only at positions s.xt (from qv), over the stored candidates; the
+// body and friction terms run beside the pair energies
 void eval_energy(Scene& s, const double* qv) {
+  on_side(s, 0, 2, [&]() { launch_body_terms(s, qv, false); });
+  on_side(s, 1, 3, [&]() { launch_friction_eval(s, s.xt.p, false); });
   launch_pair_energy(s, s.xt.p);
-  launch_friction_eval(s, s.xt.p, false);
-  launch_body_terms(s, qv, false);
+  join_side(s, 0, 2);
+  join_side(s, 1, 3);
   launch_energy_total(s, false);
 }
 
@@ -353,7 +363,9 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
     run_segment(s, s.seg_trial, [&]() {
       launch_transform_dq(s, s.dq.p);
       cudaMemsetAsync(&s.st->step_bits, 0, sizeof(unsigned long long), s.stream);
-      launch_max_step(s);
+      // the step length beside the broad phase; eval_energy's join of side
+      // stream 0 (queued behind it) also joins it
+      on_side(s, 0, 0, [&]() { launch_max_step(s); });
       launch_reset_toi(s);
       broad_and_enumerate(s, true, true);
       launch_trial(s, 1.0, true);
@@ -515,12 +527,25 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
   s.stream = (cudaStream_t)stream;
   s.alloc.stream = s.stream;
   cudaGetDevice(&s.device);
+  for (cudaStream_t& x : s.side)
+    if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      for (cudaStream_t y : s.side)
+        if (y) cudaStreamDestroy(y);
+      delete S;
+      return ABD_ERR_CUDA;
+    }
+  for (int k = 0; k < 5; ++k) {
+    cudaEventCreateWithFlags(&s.ev_fork[k], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&s.ev_join[k], cudaEventDisableTiming);
+  }
   if (alloc && alloc->alloc && alloc->free) {
     s.alloc.a = *alloc;
     s.alloc.custom = true;
   }
   try {
     grow(s, s.xbar, nv);
+    grow(s, s.red, 4L * kEnergyParts);
     grow(s, s.vbody, nv);
     grow(s, s.tri, 3L * nt + 1);
     grow(s, s.edge, 2L * ne + 1);
@@ -662,6 +687,12 @@ void abd_destroy(abd_scene* S) {
   for (Scene::Segment* g : {&s.seg_sys[0], &s.seg_sys[1], &s.seg_trial})
     if (g->exec) cudaGraphExecDestroy(g->exec);
   if (s.cap_stream) cudaStreamDestroy(s.cap_stream);
+  for (cudaStream_t x : s.side)
+    if (x) cudaStreamDestroy(x);
+  for (int k = 0; k < 5; ++k) {
+    if (s.ev_fork[k]) cudaEventDestroy(s.ev_fork[k]);
+    if (s.ev_join[k]) cudaEventDestroy(s.ev_join[k]);
+  }
   release(s, s.xbar);
   release(s, s.l2e);
   release(s, s.scan_part);
@@ -1115,6 +1146,9 @@ abd_status abd_get_counters(abd_scene* S, abd_counters* out) {
   out->sweeps_fp32 = s.st_host->jac[0];
   out->sweeps_fp64 = s.st_host->jac[1];
   out->capped_fp64 = s.st_host->jac[2];
+  out->prim_pairs_body = s.st_host->cull[0];
+  out->prim_pairs_iaabb = s.st_host->cull[1];
+  out->prim_pairs_cand = s.st_host->cull[2];
   return check_cuda(s);
 }
 

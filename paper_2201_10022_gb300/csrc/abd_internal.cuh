@@ -51,6 +51,10 @@ struct DevStatus {
   unsigned long long jac[3];    // Jacobi sweeps FP32, FP64, terms at the FP64 sweep cap (cumulative)
   int bh_fix;                   // body blocks to project (not positive definite)
   int pad3;
+  // culling of the enumeration (cumulative): primitive pairs of the body
+  // pairs, pairs left after restricting each side to the other body's box,
+  // candidates passing the exact primitive box test
+  unsigned long long cull[3];
 };
 
 // ---- small device helpers shared by the kernel files -----------------------
@@ -143,6 +147,10 @@ struct Scene {
   Segment seg_sys[2], seg_trial;
   Alloc alloc;
   cudaStream_t stream = nullptr;
+  // two side streams for the independent branches of a Newton iteration
+  // (fork / join by events; inside a capture they become graph branches)
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork[5] = {}, ev_join[5] = {};
   int device = 0;    // CUDA device the scene was created on
   int grid_div = 1;  // divisor of the device-sized grids (abd_tuning)
   std::string err;
@@ -237,9 +245,27 @@ inline void counted(Scene& s, int n = 1) { s.nlaunch += n; }
 // chunks of 32 candidate slots per body pair (energy-only pass partial sums)
 inline int energy_chunks(const Scene& s) { return (s.maxc + 31) / 32; }
 
+// run `body` on side stream k, after the work enqueued so far on the scene's
+// stream (fork point f); join_side makes the scene's stream wait for it
+template <typename F>
+void on_side(Scene& s, int k, int f, F body) {
+  cudaEventRecord(s.ev_fork[f], s.stream);
+  cudaStreamWaitEvent(s.side[k], s.ev_fork[f], 0);
+  cudaStream_t main = s.stream;
+  s.stream = s.side[k];
+  body();
+  s.stream = main;
+}
+inline void join_side(Scene& s, int k, int f) {
+  cudaEventRecord(s.ev_join[f], s.side[k]);
+  cudaStreamWaitEvent(s.stream, s.ev_join[f], 0);
+}
+
 // grid of a kernel that grid-strides over a count held on the device:
 // per_sm blocks on each of the 152 SMs, divided by the scene's grid_div
 constexpr int kNumSMs = 152;
+// ranges per energy component in the two-stage energy reduction
+constexpr int kEnergyParts = 256;
 inline int sm_grid(const Scene& s, int per_sm) {
   const int g = kNumSMs * per_sm / s.grid_div;
   return g < 1 ? 1 : g;

@@ -119,7 +119,7 @@ __device__ int fill_chunk(int t, int cur, int hi, const double* olo, const doubl
 // triangles (PT) or edges (EE) of body `qa`.
 __device__ void enum_kind(int kind, int p_lo, int p_hi, int q_lo, int q_hi, const Box& boxP, const Box& boxQ,
                           double dhat, const int* tri, const int* edge, const double4* x, const double4* x1,
-                          WarpLists& L, int2* out, int maxc, int& base) {
+                          WarpLists& L, int2* out, int maxc, int& base, unsigned long long& tested) {
   const int lane = threadIdx.x & 31;
   const int tp = kind == 0 ? 0 : 1, tq = kind == 0 ? 2 : 1;
   int qc = q_lo;
@@ -132,6 +132,7 @@ __device__ void enum_kind(int kind, int p_lo, int p_hi, int q_lo, int q_hi, cons
       int npp;
       pc = fill_chunk(tp, pc, p_hi, boxQ.lo, boxQ.hi, dhat, tri, edge, x, x1, L.pid, L.pb, npp);
       const int tot = npp * nq;
+      tested += tot;
       for (int t0 = 0; t0 < tot; t0 += 32) {
         int t = t0 + lane;
         bool c = false;
@@ -163,7 +164,7 @@ __global__ void k_enumerate(const int2* __restrict__ P, const DevStatus* __restr
   const int nwarps = gridDim.x * kWarpsPerBlock;
   const int np = cst->np;
   WarpLists& L = lists[warp];
-  unsigned long long ncand = 0;
+  unsigned long long ncand = 0, nall = 0, ntested = 0;
   for (int p = blockIdx.x * kWarpsPerBlock + warp; p < np; p += nwarps) {
     const int a = P[p].x, b = P[p].y;
     Box Ba, Bb;
@@ -176,10 +177,16 @@ __global__ void k_enumerate(const int2* __restrict__ P, const DevStatus* __restr
     int base = 0;
     int2* out = cand + (size_t)p * maxc;
     // vertices of a against triangles of b, vertices of b against triangles of a
-    enum_kind(0, vbeg[a], vbeg[a + 1], tbeg[b], tbeg[b + 1], Ba, Bb, dhat, tri, edge, x, x1, L, out, maxc, base);
-    enum_kind(0, vbeg[b], vbeg[b + 1], tbeg[a], tbeg[a + 1], Bb, Ba, dhat, tri, edge, x, x1, L, out, maxc, base);
+    enum_kind(0, vbeg[a], vbeg[a + 1], tbeg[b], tbeg[b + 1], Ba, Bb, dhat, tri, edge, x, x1, L, out, maxc, base,
+              ntested);
+    enum_kind(0, vbeg[b], vbeg[b + 1], tbeg[a], tbeg[a + 1], Bb, Ba, dhat, tri, edge, x, x1, L, out, maxc, base,
+              ntested);
     // edges of a against edges of b
-    enum_kind(1, ebeg[a], ebeg[a + 1], ebeg[b], ebeg[b + 1], Ba, Bb, dhat, tri, edge, x, x1, L, out, maxc, base);
+    enum_kind(1, ebeg[a], ebeg[a + 1], ebeg[b], ebeg[b + 1], Ba, Bb, dhat, tri, edge, x, x1, L, out, maxc, base,
+              ntested);
+    nall += (unsigned long long)(vbeg[a + 1] - vbeg[a]) * (tbeg[b + 1] - tbeg[b]) +
+            (unsigned long long)(vbeg[b + 1] - vbeg[b]) * (tbeg[a + 1] - tbeg[a]) +
+            (unsigned long long)(ebeg[a + 1] - ebeg[a]) * (ebeg[b + 1] - ebeg[b]);
     if (lane == 0) {
       ccount[p] = base;
       if (base > maxc) {
@@ -190,6 +197,11 @@ __global__ void k_enumerate(const int2* __restrict__ P, const DevStatus* __restr
     ncand += base;
   }
   if (lane == 0 && ncand) atomicAdd(&st->n_cand, ncand);
+  if (lane == 0 && nall) {
+    atomicAdd(&st->cull[0], nall);
+    atomicAdd(&st->cull[1], ntested);
+    atomicAdd(&st->cull[2], ncand);
+  }
 }
 
 // additive CCD (Sec. 4.1) over the stored swept candidates: one warp per

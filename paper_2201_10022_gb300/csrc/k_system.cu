@@ -1243,37 +1243,49 @@ __global__ void k_pcg_start(const double* part, int n, DevStatus* st) {
 }
 
 // fixed-order sum: out = sum_i v[i * stride] for i < n
-__device__ void block_reduce_to(const double* v, long stride, long n, double* out) {
-  __shared__ double red[1024];
-  double s = 0.0;
-  for (long i = threadIdx.x; i < n; i += 1024) s += v[i * stride];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 512; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+// the four energy components (inertia, orthogonality, barrier, friction) in
+// fixed order: component k = blockIdx.y is cut into kEnergyParts contiguous
+// ranges of equal length (a function of its count only, not of the grid);
+// block x sums range x (strided per thread, then a shared-memory tree)
+__global__ void __launch_bounds__(256) k_energies(const double* Eb, int nb, const double* bar, long bar_stride,
+                                                  const int* nbar, int nbar_mul, const double* fterm, const int* nfr,
+                                                  double* part) {
+  __shared__ double red[256];
+  const int k = blockIdx.y;
+  const double* v = k == 0 ? Eb : (k == 1 ? Eb + 1 : (k == 2 ? bar : fterm));
+  const long stride = k < 2 ? 2 : (k == 2 ? bar_stride : kTermStride);
+  const long n = k < 2 ? nb : (k == 2 ? (long)*nbar * nbar_mul : *nfr);
+  const long len = (n + kEnergyParts - 1) / kEnergyParts;
+  for (int x = blockIdx.x; x < kEnergyParts; x += gridDim.x) {
+    const long lo = x * len, hi = min(n, lo + len);
+    double acc = 0.0;
+    for (long i = lo + threadIdx.x; i < hi; i += 256) acc += v[i * stride];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[k * kEnergyParts + x] = red[0];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = red[0];
 }
 
-__global__ void k_reduce(const double* v, long stride, const int* n_dev, long n_const, double* out) {
-  block_reduce_to(v, stride, n_dev ? *n_dev : n_const, out);
-}
-
-// the four energy components in one launch (block k reduces component k)
-__global__ void k_energies(const double* Eb, int nb, const double* bar, long bar_stride, const int* nbar,
-                           int nbar_mul, const double* fterm, const int* nfr, DevStatus* st) {
-  if (blockIdx.x == 0) block_reduce_to(Eb, 2, nb, &st->energy[1]);
-  else if (blockIdx.x == 1) block_reduce_to(Eb + 1, 2, nb, &st->energy[2]);
-  else if (blockIdx.x == 2) block_reduce_to(bar, bar_stride, (long)*nbar * nbar_mul, &st->energy[3]);
-  else block_reduce_to(fterm, kTermStride, *nfr, &st->energy[4]);
-}
-
-// total energy; keep != 0 also stores it in energy[5] (the reference value of
-// the line search, which later energy-only passes do not overwrite)
-__global__ void k_energy_sum(DevStatus* st, int keep) {
-  st->energy[0] = ((st->energy[1] + st->energy[2]) + st->energy[3]) + st->energy[4];
-  if (keep) st->energy[5] = st->energy[0];
+// components from their partial sums (warp k sums component k in fixed
+// order), then the total; keep != 0 also stores it in energy[5] (the
+// reference value of the line search, which later energy-only passes do not
+// overwrite)
+__global__ void k_energy_sum(const double* part, DevStatus* st, int keep) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double acc = 0.0;
+  for (int i = lane; i < kEnergyParts; i += 32) acc += part[w * kEnergyParts + i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+  if (lane == 0) st->energy[1 + w] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->energy[0] = ((st->energy[1] + st->energy[2]) + st->energy[3]) + st->energy[4];
+    if (keep) st->energy[5] = st->energy[0];
+  }
 }
 
 __global__ void k_max_step(int nv, const int* vbody, const uint8_t* is_static, const double4* dx, DevStatus* st) {
@@ -1369,6 +1381,13 @@ void launch_body_pairs(Scene& s) {
   k_hash_count<<<nbk, 128, 0, s.stream>>>(s.nb, s.bbox.p, s.prm.dhat, inv_h, s.hcount.p, s.large.p);
   launch_scan(s, s.large.p, s.large_pos.p, nullptr, &s.st->nlarge, (long)s.nb, 0, &s.st->need_misc);
   k_large_list<<<nbk, 128, 0, s.stream>>>(s.nb, s.large.p, s.large_pos.p, s.large_list.p);
+  // rows of the large bodies (direct scan over all bodies, no hash) beside
+  // the hash build and the hashed rows; both write disjoint rows
+  counted(s);
+  on_side(s, 1, 4, [&]() {
+    k_rows_large<<<64, 1024, 0, s.stream>>>(s.nb, s.is_static.p, s.bbox.p, s.bbox32.p, dh32(s), s.prm.dhat,
+                                            s.large_list.p, s.fpairs.p, s.st, s.maxn, s.nbr.p, s.ncount.p, s.st);
+  });
   launch_scan(s, s.hcount.p, s.hoff.p, nullptr, &s.st->nent, (long)s.entries.cap, ST_CAP_HASH, &s.st->need_misc);
   cudaMemsetAsync(s.slot_cnt.p, 0, sizeof(int) * s.hash_T, s.stream);
   k_hash_slots<<<nbk, 128, 0, s.stream>>>(s.nb, s.bbox.p, s.large.p, s.prm.dhat, inv_h, mask, s.slot_cnt.p,
@@ -1383,14 +1402,12 @@ void launch_body_pairs(Scene& s) {
   cudaMemsetAsync(s.slot_cnt.p, 0, sizeof(int) * s.hash_T, s.stream);
   k_hash_slots<<<nbk, 128, 0, s.stream>>>(s.nb, s.bbox.p, s.large.p, s.prm.dhat, inv_h, mask, s.slot_cnt.p,
                                           s.slot_off.p, s.entries.p, (long)s.entries.cap, true);
-  counted(s, 3);
+  counted(s, 2);
   k_rows<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.is_static.p, s.bbox.p, s.bbox32.p, dh32(s),
                                                         s.prm.dhat, inv_h, mask,
                                                         s.large.p, s.large_list.p, s.slot_off.p, s.entries.p,
                                                         s.fpairs.p, s.st, s.maxn, s.nbr.p, s.ncount.p, s.st);
-  k_rows_large<<<64, 1024, 0, s.stream>>>(s.nb, s.is_static.p, s.bbox.p, s.bbox32.p, dh32(s), s.prm.dhat,
-                                          s.large_list.p, s.fpairs.p, s.st,
-                                          s.maxn, s.nbr.p, s.ncount.p, s.st);
+  join_side(s, 1, 4);
   launch_scan(s, s.ncount.p, s.rowoff.p, nullptr, &s.st->np, (long)s.P.cap, ST_CAP_PAIRS, &s.st->need_pairs);
   k_rows_compact<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.nbr.p, s.ncount.p, s.rowoff.p, s.maxn, s.P.p,
                                                                 (long)s.P.cap);
@@ -1465,13 +1482,14 @@ void launch_precond(Scene& s) {
 // per-body-pair barrier energies (energy-only pass), friction terms
 void launch_energy_total(Scene& s, bool from_terms) {
   counted(s, 2);
+  const dim3 grid(std::max(1, kEnergyParts / s.grid_div), 4);
   if (from_terms)
-    k_energies<<<4, 1024, 0, s.stream>>>(s.Eb.p, s.nb, s.term.p, kTermStride, &s.st->nact, 1, s.fterm.p, &s.st->nfr,
-                                         s.st);
+    k_energies<<<grid, 256, 0, s.stream>>>(s.Eb.p, s.nb, s.term.p, kTermStride, &s.st->nact, 1, s.fterm.p,
+                                           &s.st->nfr, s.red.p);
   else
-    k_energies<<<4, 1024, 0, s.stream>>>(s.Eb.p, s.nb, s.Epair.p, 1, &s.st->np, energy_chunks(s), s.fterm.p,
-                                         &s.st->nfr, s.st);
-  k_energy_sum<<<1, 1, 0, s.stream>>>(s.st, from_terms ? 1 : 0);
+    k_energies<<<grid, 256, 0, s.stream>>>(s.Eb.p, s.nb, s.Epair.p, 1, &s.st->np, energy_chunks(s), s.fterm.p,
+                                           &s.st->nfr, s.red.p);
+  k_energy_sum<<<1, 128, 0, s.stream>>>(s.red.p, s.st, from_terms ? 1 : 0);
 }
 
 // PCG in three pieces so that its first iterations can join a captured launch
