@@ -1242,7 +1242,6 @@ __global__ void k_pcg_start(const double* part, int n, DevStatus* st) {
   }
 }
 
-// fixed-order sum: out = sum_i v[i * stride] for i < n
 // the four energy components (inertia, orthogonality, barrier, friction) in
 // fixed order: component k = blockIdx.y is cut into kEnergyParts contiguous
 // ranges of equal length (a function of its count only, not of the grid);
