@@ -122,6 +122,14 @@ def oracle_sample(start_step, warmup, steps, dims=(6, 6, 3)):
             "seconds": dt}
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    """progress on stderr (the JSON line goes to stdout)"""
+    print(f"[bench {time.perf_counter() - _T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
 def max_over_ranks(x, world, device):
     """the largest value of x over the ranks of the job (the slowest rank's
     time); x itself on a single rank"""
@@ -237,7 +245,9 @@ def batched_run(dev, steps=2, pre_steps=10, seed=5, n_scenes=256):
     S = scenes.scene_batch(seed=seed, n_scenes=n_scenes)
     nb = np.array([s.nb - 1 for s in S])
     B = SceneBatch(S, device=dev)
+    log(f"batch: {n_scenes} scenes created ({int(nb.sum())} bodies)")
     B.step(pre_steps)
+    log(f"batch: {pre_steps} pre-steps done")
     saved = [(q.clone(), qd.clone()) for q, qd in B.get_states()]
     setup_s = time.perf_counter() - t0
 
@@ -250,8 +260,10 @@ def batched_run(dev, steps=2, pre_steps=10, seed=5, n_scenes=256):
         return ms, st
 
     ms_seq, st_seq = timed(B, 1, 1)
-    tune = B.tune(trial_steps=1, use_cache=False, write_cache=False)
+    log(f"batch: sequential {ms_seq / steps:.1f} ms/step")
+    tune = B.tune(trial_steps=1, use_cache=False, write_cache=False, log=log)
     ms_b, st_b = timed(B, tune["nworkers"], tune["grid_div"])
+    log(f"batch: batched {ms_b / steps:.1f} ms/step")
     q_b = [q.clone() for q, _ in B.get_states()]
     B.close()
     Bm = SceneBatch(S, device=dev, precision=1)
@@ -294,6 +306,7 @@ def run_abd(args, rank, world):
     g = AbdScene(s, device=dev)
     if args.start_step:
         g.step(args.start_step)
+    log(f"workload: {args.start_step} pre-roll steps done")
     g.step(args.warmup)
     torch.cuda.synchronize()
     q0, qd0 = g.get_state()
@@ -387,8 +400,10 @@ def run_abd(args, rank, world):
                               "energies, gradients, CCD, Newton test and line search FP64"}
         gm.close()
 
+    log("timed, profiled, e2e and mixed runs done")
     adjoint = adjoint_run(dev) if args.adjoint else None
     batched = None if args.no_batched else batched_run(dev)
+    log("batched run done")
 
     steps_total = args.steps * world
     ms_per_step = aggregate_ms_per_step(total_ms, args.steps, world)
