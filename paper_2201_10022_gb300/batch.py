@@ -10,9 +10,10 @@ Every scene keeps its own Newton iteration, line search and convergence test,
 so its result is bit-identical to stepping it alone.
 
 ``tune()`` picks the two knobs of the batch (host workers, i.e. scenes in
-flight, and the grid divisor of the device-sized kernels) by timing short
-runs from the current state, restores the state afterwards, and caches the
-choice per (GPU, size class) in a JSON file.
+flight, and the grid divisor of the device-sized kernels: one value for all
+scenes or a divisor per scene by its size) by timing short runs from the
+current state, restores the state afterwards, and caches the choice per
+(GPU, size class) in a JSON file.
 """
 from __future__ import annotations
 
@@ -110,11 +111,24 @@ class SceneBatch:
         name = self.torch.cuda.get_device_name(self.device)
         return f"{name}|{self.size_class()}"
 
-    def tune(self, trial_steps=1, use_cache=True, write_cache=True, log=None):
-        """choose (nworkers, grid_div): grid divisor first at the default
-        worker count, then the worker count at that divisor; every trial runs
-        one untimed step (re-capture of the launch sequences) and trial_steps
-        timed steps from the same saved state, which is restored at the end"""
+    def set_grid_policy(self, policy):
+        """grid divisor per scene: an int for every scene, or "by_size"
+        (2^round(log2(4096 / bodies)), clamped to 1..64: small scenes leave
+        most SMs to the others)"""
+        if policy == "by_size":
+            for s in self.scenes:
+                g = int(2 ** np.round(np.log2(4096.0 / max(s.nb, 1))))
+                s.set_tuning(grid_div=min(64, max(1, g)))
+            self.grid_div = "by_size"
+        else:
+            self.set_tuning(grid_div=int(policy))
+
+    def tune(self, trial_steps=1, use_cache=True, write_cache=True, log=None, workers=None, policies=None):
+        """choose (nworkers, grid policy): the worker count first at the
+        by-size grid policy, then the policy at that worker count; every trial
+        runs one untimed step (re-capture of the launch sequences) and
+        trial_steps timed steps from the same saved state, which is restored
+        at the end"""
         key = self._key()
         path = _cache_path()
         cache = {}
@@ -126,31 +140,42 @@ class SceneBatch:
                 cache = {}
         if use_cache and key in cache:
             c = cache[key]
-            self.set_tuning(c["nworkers"], c["grid_div"])
+            self.nworkers = c["nworkers"]
+            self.set_grid_policy(c["grid_div"])
             return dict(c, cached=True)
         saved = [(q.clone(), qd.clone()) for q, qd in self.get_states()]
         cpus = os.cpu_count() or 1
         trials = []
 
-        def run(nw, gd):
-            self.set_tuning(nw, gd)
+        memo = {}
+
+        def run(nw, gp):
+            if (nw, gp) in memo:
+                return memo[(nw, gp)]
+            self.nworkers = nw
+            self.set_grid_policy(gp)
             self.set_states(saved)
             self.step(1)
             self.set_states(saved)
             ms, _ = self.time_steps(trial_steps)
-            trials.append({"nworkers": nw, "grid_div": gd, "ms": ms})
+            trials.append({"nworkers": nw, "grid_div": gp, "ms": ms})
             if log:
-                log(f"tune: workers {nw} grid_div {gd}: {ms:.1f} ms")
+                log(f"tune: workers {nw} grid {gp}: {ms:.1f} ms")
+            memo[(nw, gp)] = ms
             return ms
 
-        nw0 = self.nworkers
-        best_gd = min(_GRID_DIVS, key=lambda gd: run(nw0, gd))
-        # a worker waits on its scene's stream by polling: no more workers than cores
-        workers = [w for w in _WORKERS if w <= max(1, min(len(self.scenes), cpus))]
-        best_nw = min(workers, key=lambda nw: run(nw, best_gd))
-        self.set_tuning(best_nw, best_gd)
+        # a worker waits on its scene's stream by polling: no more workers
+        # than cores; one or two workers only for small batches
+        if workers is None:
+            lo = 1 if len(self.scenes) < 32 else 4
+            workers = [w for w in _WORKERS if lo <= w <= max(1, min(len(self.scenes), cpus))] or [1]
+        policies = policies or ["by_size", *_GRID_DIVS]
+        best_nw = min(workers, key=lambda nw: run(nw, policies[0]))
+        best_gp = min(policies, key=lambda gp: run(best_nw, gp))
+        self.nworkers = best_nw
+        self.set_grid_policy(best_gp)
         self.set_states(saved)
-        res = {"nworkers": best_nw, "grid_div": best_gd, "trial_steps": trial_steps, "trials": trials}
+        res = {"nworkers": best_nw, "grid_div": best_gp, "trial_steps": trial_steps, "trials": trials}
         if write_cache:
             cache[key] = res
             try:

@@ -566,29 +566,35 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
         }
       }
       if (mixed) {
-        // mixed precision: the clamp from the FP32 eigenpairs and the
-        // back-transform in FP32, no FP64 refinement
+        // mixed precision: the clamp from the FP32 eigenpairs, no FP64
+        // refinement.  The factor G = (Ri x I) V sqrt(max(lambda, 0)) is
+        // formed in FP32 and the clamped block as G G^T in FP64, so the block
+        // is positive semidefinite to FP64 rounding (an FP32 product would
+        // leave negative eigenvalues of ~1e-7 of the largest, enough to make
+        // a light body's diagonal block indefinite)
         const float* Kc = W.K32[cur];
         const float* Vc = W.V32[cur];
-        float* Pf = W.K32[cur ^ 1];
-        for (int e = lane; e < N * N; e += 32) {
-          const int a = e / N, b = e - N * (e / N);
+        float* Gv = W.K32[cur ^ 1];
+        for (int e = lane; e < N * N; e += 32) {  // V sqrt(lambda+)
+          const int a = e / N, k = e - N * (e / N);
+          const float lam = Kc[k * N + k];
+          Gv[e] = lam > 0.0f ? Vc[a * N + k] * sqrtf(lam) : 0.0f;
+        }
+        __syncwarp();
+        double* G = W.Vd[0];
+        for (int e = lane; e < N * N; e += 32) {  // (Ri x I) V sqrt(lambda+)
+          const int a = e / N, k = e - N * (e / N);
+          const int Ia = a / 3, i = a - 3 * Ia;
           float t = 0.0f;
-#pragma unroll
-          for (int k = 0; k < N; ++k) {
-            const float lam = Kc[k * N + k];
-            if (lam > 0.0f) t += Vc[a * N + k] * lam * Vc[b * N + k];
-          }
-          Pf[e] = t;
+          for (int c = Ia; c < M; ++c) t += W.Ri32[3 * Ia + c] * Gv[(3 * c + i) * N + k];
+          G[e] = (double)t;
         }
         __syncwarp();
         for (int e = lane; e < N * N; e += 32) {
           const int a = e / N, b = e - N * (e / N);
-          const int Ia = a / 3, i = a - 3 * Ia, Jb = b / 3, j = b - 3 * Jb;
-          float t = 0.0f;
-          for (int c = Ia; c < M; ++c)
-            for (int e2 = Jb; e2 < M; ++e2) t += W.Ri32[3 * Ia + c] * W.Ri32[3 * Jb + e2] * Pf[(3 * c + i) * N + 3 * e2 + j];
-          P[e] = (double)t * mx;
+          double t = 0.0;
+          for (int k = 0; k < N; ++k) t += G[a * N + k] * G[b * N + k];
+          P[e] = t * mx;
         }
         if (lane == 0) atomicAdd(&st->jac[0], (unsigned long long)n32);
       } else {

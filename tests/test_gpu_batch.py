@@ -44,9 +44,10 @@ def test_batched_scenes_bit_identical_to_alone(abd, precision):
     S = _small_batch()
     nsteps = 6
     ref = _alone(abd, S, nsteps, precision=precision)
-    for nw, gd in ((3, 4), (6, 1), (1, 16)):
+    for nw, gd in ((3, 4), (6, 1), (1, 16), (4, "by_size")):
         B = SceneBatch(S, precision=precision)
-        B.set_tuning(nworkers=nw, grid_div=gd)
+        B.nworkers = nw
+        B.set_grid_policy(gd)
         stats = B.step(nsteps)
         assert sum(st["n_active"] for st in stats) >= 0
         for k, (q, qd) in enumerate(B.get_states()):
@@ -69,7 +70,7 @@ def test_tune_restores_state_and_caches(abd, tmp_path, monkeypatch):
     B.step(2)
     before = [(q.clone(), qd.clone()) for q, qd in B.get_states()]
     res = B.tune(trial_steps=1)
-    assert not res["cached"] and res["grid_div"] in (1, 4, 16) and res["nworkers"] >= 1
+    assert not res["cached"] and res["grid_div"] in ("by_size", 1, 4, 16) and res["nworkers"] >= 1
     for (q0, qd0), (q1, qd1) in zip(before, B.get_states()):
         assert torch.equal(q0, q1) and torch.equal(qd0, qd1)
     again = B.tune()
