@@ -94,6 +94,11 @@ typedef struct {
                            step passes the Newton test, the test is repeated at
                            the same iterate with the FP64-refined projection, so
                            both modes stop on the same criterion */
+  int dense_max_dofs;   /* 0: the linear solves use block-Jacobi PCG.  > 0: scenes with
+                           12 x bodies <= dense_max_dofs (at most 3072 after padding to a
+                           multiple of 32) solve by a dense Cholesky factorisation on the
+                           device instead (Newton steps, abd_solve, abd_adjoint_step);
+                           abd_solve_stats then reports 0 iterations and residual 0 */
 } abd_params;
 
 /* Scene description (host arrays, copied).  Vertices, triangles and edges

@@ -34,7 +34,7 @@ class abd_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double), ("gravity", C.c_double * 3),
                 ("mu", C.c_double), ("eps_v", C.c_double), ("newton_tol", C.c_double), ("pcg_rel_tol", C.c_double),
                 ("ls_slack_rel", C.c_double), ("ccd_s", C.c_double), ("newton_max", C.c_int), ("pcg_max", C.c_int),
-                ("ls_max", C.c_int), ("ccd_max", C.c_int), ("precision", C.c_int)]
+                ("ls_max", C.c_int), ("ccd_max", C.c_int), ("precision", C.c_int), ("dense_max_dofs", C.c_int)]
 
 
 class abd_scene_desc(C.Structure):

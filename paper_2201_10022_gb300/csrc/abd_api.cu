@@ -337,8 +337,12 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
       launch_transform(s, s.q.p, s.x.p);
       eval_system(s, s.q.p, 1);
       launch_negate(s, s.g.p, s.qsave.p, 12L * s.nb);
-      pcg_begin(s, s.qsave.p, s.dq.p);
-      pcg_iterate(s, s.dq.p, 2, s.prm.pcg_rel_tol);
+      if (s.dense_n) {
+        launch_dense_solve(s, s.qsave.p, s.dq.p);
+      } else {
+        pcg_begin(s, s.qsave.p, s.dq.p);
+        pcg_iterate(s, s.dq.p, 2, s.prm.pcg_rel_tol);
+      }
       cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
     });
     cudaStreamSynchronize(s.stream);
@@ -546,6 +550,11 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
   try {
     grow(s, s.xbar, nv);
     grow(s, s.red, 4L * kEnergyParts);
+    s.dense_n = dense_order(nb, prm->dense_max_dofs);
+    if (s.dense_n) {
+      grow(s, s.dense, (size_t)s.dense_n * s.dense_n);
+      grow(s, s.dense_dinv, (size_t)s.dense_n);
+    }
     grow(s, s.vbody, nv);
     grow(s, s.tri, 3L * nt + 1);
     grow(s, s.edge, 2L * ne + 1);
@@ -711,7 +720,7 @@ void abd_destroy(abd_scene* S) {
   release(s, s.density);
   for (Buf<double>* b : {&s.q, &s.qdot, &s.qt, &s.qtilde, &s.dq, &s.qtrial, &s.qsave, &s.qdotsave, &s.gb, &s.g, &s.r,
                          &s.z, &s.pv, &s.Ap, &s.Eb, &s.Db, &s.D, &s.Pinv, &s.part, &s.bbox, &s.term, &s.fterm,
-                         &s.pblk, &s.Epair, &s.act_d2, &s.red})
+                         &s.pblk, &s.Epair, &s.act_d2, &s.red, &s.dense, &s.dense_dinv})
     release(s, *b);
   for (Buf<double4>* b : {&s.x, &s.dx, &s.x1, &s.xt}) release(s, *b);
   for (Buf<int>* b : {&s.nbr, &s.ncount, &s.rowoff, &s.in_off, &s.in_cnt, &s.in_list, &s.ccount, &s.acount, &s.aoff,

@@ -212,6 +212,8 @@ struct Scene {
   Buf<int> hfix;            // bodies whose block failed Cholesky (projected)
   Buf<double> D, g, Pinv;   // assembled diagonal, gradient, preconditioner
   Buf<double> red;     // reduction scratch
+  int dense_n = 0;           // order of the dense system (0: PCG)
+  Buf<double> dense, dense_dinv;  // dense_n^2 matrix / factor, reciprocal pivots
   Buf<long long> scan_part;  // tile sums of the two-phase scan
 
   // PCG
@@ -310,6 +312,10 @@ void launch_gather(Scene& s);
 void launch_precond(Scene& s);
 void launch_energy_total(Scene& s, bool with_pairs);
 int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res);
+// dense direct solve (small scenes): order of the padded matrix, 0 if off
+constexpr int kDenseMaxOrder = 3072;
+int dense_order(int nb, int max_dofs);
+void launch_dense_solve(Scene& s, const double* rhs, double* x);
 void pcg_begin(Scene& s, const double* rhs, double* xout);
 void pcg_iterate(Scene& s, double* xout, int n, double rel_tol);
 int pcg_finish(Scene& s, double* xout, int done_iters, int max_iter, double rel_tol, double* rel_res);

@@ -1544,6 +1544,12 @@ int pcg_finish(Scene& s, double* xout, int done_iters, int max_iter, double rel_
 }
 
 int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res) {
+  if (s.dense_n) {
+    launch_dense_solve(s, rhs, xout);
+    cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
+    cudaStreamSynchronize(s.stream);
+    return pcg_finish(s, xout, 0, max_iter, rel_tol, rel_res);
+  }
   pcg_begin(s, rhs, xout);
   pcg_iterate(s, xout, 2, rel_tol);
   cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
