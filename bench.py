@@ -304,6 +304,7 @@ def batched_run(dev, steps=2, pre_steps=10, seed=5, n_scenes=256):
         "scene_steps_per_s_batched_fp64": n_scenes * steps / (ms_b * 1e-3),
         "newton_iters_per_s_batched_fp64": newton / (ms_b * 1e-3),
         "newton_iters_per_scene_step": newton / (n_scenes * steps),
+        "pcg_iters_per_newton": sum(st["pcg_iters"] for st in st_b) / max(newton, 1),
         "tuning": {"nworkers": tune["nworkers"], "grid_div": tune["grid_div"],
                    "trials": [(t["nworkers"], t["grid_div"], round(t["ms"], 1)) for t in tune["trials"]]},
         "gpu_launches": sum(st["kernel_launches"] for st in st_b),
@@ -469,6 +470,7 @@ def run_abd(args, rank, world):
         "contact_evals_per_s": cand / (total_ms * 1e-3),
         "active_evals_per_s": act / (total_ms * 1e-3),
         "newton_iters_per_step": newton / args.steps,
+        "pcg_iters_per_newton": sum(st["pcg_iters"] for st in stats) / max(newton, 1),
         "e2e": {"value": e2e_ms / steps_total, "unit": "ms/step", "h2d_bytes_per_step": 2 * 12 * 8 * s.nb,
                 "d2h_bytes_per_step": 2 * 12 * 8 * s.nb},
         "gpu_launches": launches,

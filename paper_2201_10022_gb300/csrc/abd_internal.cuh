@@ -45,7 +45,8 @@ struct DevStatus {
   unsigned long long step_bits; // max vertex step length (bits of a positive double)
   unsigned long long n_cand;    // candidates of the last enumeration
   unsigned long long bar_terms[4];  // barrier terms evaluated, by reduced dimension m = 1, 2, 3
-  double scal[8];               // PCG scalars: 0 rz, 1 pAp, 2 rr, 3 rr0, 4 alpha, 5 beta, 6 done
+  double scal[10];              // PCG scalars: 0 rz, 1 pAp, 2 rr, 3 rr0, 4 alpha, 5 beta, 6 done,
+                                // 7 iterations, 8 rz of the previous iteration
   double energy[8];             // 0 total, 1 inertia, 2 ortho, 3 barrier, 4 friction
   int bar_cnt[4];               // active terms by working dimension 3, 6, 9 (classification pass)
   unsigned long long jac[3];    // Jacobi sweeps FP32, FP64, terms at the FP64 sweep cap (cumulative)

@@ -1070,43 +1070,47 @@ __global__ void k_spmv(int nb, const uint8_t* is_static, const double* D, const 
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-// fixed-order sum of n partials into st->scal[slot]
-__device__ double block_sum(const double* v, int n) {
-  __shared__ double red[256];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += 256) s += v[i];
-  red[threadIdx.x] = s;
+// p.Ap from the product's partials, by every block in the same fixed order
+// (that of a 256-thread block: thread t sums entries t, t + 256, ..., then a
+// tree), with 128 threads each standing for threads t and t + 128
+__device__ double pap_sum128(const double* v, int n, double* red) {
+  const int t = threadIdx.x;
+  double s0 = 0.0, s1 = 0.0;
+  for (int i = t; i < n; i += 256) s0 += v[i];
+  for (int i = t + 128; i < n; i += 256) s1 += v[i];
+  red[t] = s0 + s1;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+  for (int o = 64; o > 0; o >>= 1) {
+    if (t < o) red[t] += red[t + o];
     __syncthreads();
   }
-  double r = red[0];
+  const double r = red[0];
   __syncthreads();
   return r;
 }
 
-__global__ void k_pcg_alpha(const double* part, int n, DevStatus* st) {
+// alpha = r.z / p.Ap (every block forms it from the product's partials; block
+// 0 records it and the breakdown), x += alpha p; r -= alpha Ap;
+// z = (L L^T)^-1 r from the stored block factors; partial sums of r.z and r.r
+__global__ void k_pcg_update(int nb, const uint8_t* is_static, const double* Pinv, const double* pv,
+                             const double* Ap, const double* spart, int nspart, double* x, double* r, double* z,
+                             double* part, DevStatus* st) {
+  __shared__ double red[2][128];
   if (st->scal[6] != 0.0) return;
-  double pAp = block_sum(part, n);
-  if (threadIdx.x == 0) {
+  const double pAp = pap_sum128(spart, nspart, red[0]);
+  const double rz_old = st->scal[0];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->scal[1] = pAp;
+    st->scal[8] = rz_old;
     if (!(pAp > 0.0)) {
       st->scal[6] = 2.0;  // breakdown
       set_flag(st, ST_PCG_BREAKDOWN);
     } else {
-      st->scal[4] = st->scal[0] / pAp;
+      st->scal[4] = rz_old / pAp;
     }
   }
-}
-
-// x += alpha p; r -= alpha Ap; z = (L L^T)^-1 r from the stored block factors;
-// partial sums of r.z and r.r
-__global__ void k_pcg_update(int nb, const uint8_t* is_static, const double* Pinv, const double* pv,
-                             const double* Ap, double* x, double* r, double* z, double* part, const DevStatus* cst) {
-  __shared__ double red[2][128];
-  if (cst->scal[6] != 0.0) return;
-  const double alpha = cst->scal[4];
+  if (!(pAp > 0.0)) return;
+  const double alpha = rz_old / pAp;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   double rz = 0.0, rr = 0.0;
   if (b < nb && !is_static[b]) {
@@ -1141,7 +1145,11 @@ __global__ void k_pcg_update(int nb, const uint8_t* is_static, const double* Pin
   }
 }
 
-__global__ void k_pcg_beta(const double* part, int n, double tol2, DevStatus* st) {
+// beta = r.z / (r.z)_previous and the convergence test from the update's
+// partials (every block, fixed order), then p = z + beta p on the block's
+// slice; block 0 records the scalars
+__global__ void k_pcg_beta_dir(const double* part, int n, double tol2, long nv, const double* z, double* pv,
+                               DevStatus* st) {
   __shared__ double red[2][256];
   if (st->scal[6] != 0.0) return;
   double a = 0.0, c = 0.0;
@@ -1159,20 +1167,18 @@ __global__ void k_pcg_beta(const double* part, int n, double tol2, DevStatus* st
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    double rz = red[0][0], rr = red[1][0];
-    st->scal[5] = rz / st->scal[0];
+  const double rz = red[0][0], rr = red[1][0];
+  const double beta = rz / st->scal[8];
+  const bool done = rr <= tol2 * st->scal[3];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->scal[5] = beta;
     st->scal[0] = rz;
     st->scal[2] = rr;
     st->scal[7] += 1.0;
-    if (rr <= tol2 * st->scal[3]) st->scal[6] = 1.0;
+    if (done) st->scal[6] = 1.0;
   }
-}
-
-__global__ void k_pcg_dir(long n, const double* z, double* pv, const DevStatus* cst) {
-  if (cst->scal[6] != 0.0) return;
-  const double beta = cst->scal[5];
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+  if (done) return;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nv; i += (long)gridDim.x * blockDim.x)
     pv[i] = z[i] + beta * pv[i];
 }
 
@@ -1511,17 +1517,17 @@ void pcg_iterate(Scene& s, double* xout, int n, double rel_tol) {
   // product written once, the pair list once
   const double spmv_bytes = 8.0 * 144.0 * (s.nb + (double)s.last_np) + 2.0 * 8.0 * 12.0 * s.nb + 8.0 * s.last_np;
   for (int k = 0; k < n; ++k) {
-    counted(s, 5);
+    counted(s, 3);
     {
       ProfScope pv(s, PF_SPMV, spmv_bytes);
       k_spmv<<<sblocks, kPcgThreads, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.rowoff.p, s.in_off.p, s.in_list.p,
                                                     s.P.p, s.pblk.p, s.pv.p, s.Ap.p, s.part.p, s.st);
     }
-    k_pcg_alpha<<<1, 256, 0, s.stream>>>(s.part.p, sblocks, s.st);
-    k_pcg_update<<<nbk, 128, 0, s.stream>>>(s.nb, s.is_static.p, s.Pinv.p, s.pv.p, s.Ap.p, xout, s.r.p, s.z.p,
-                                            s.part.p, s.st);
-    k_pcg_beta<<<1, 256, 0, s.stream>>>(s.part.p, nbk, tol2, s.st);
-    k_pcg_dir<<<blocks(12L * s.nb, 256), 256, 0, s.stream>>>(12L * s.nb, s.z.p, s.pv.p, s.st);
+    // the product's partials and the update's live in two halves of `part`
+    k_pcg_update<<<nbk, 128, 0, s.stream>>>(s.nb, s.is_static.p, s.Pinv.p, s.pv.p, s.Ap.p, s.part.p, sblocks, xout,
+                                            s.r.p, s.z.p, s.part.p + sblocks, s.st);
+    k_pcg_beta_dir<<<blocks(12L * s.nb, 256), 256, 0, s.stream>>>(s.part.p + sblocks, nbk, tol2, 12L * s.nb, s.z.p,
+                                                                   s.pv.p, s.st);
   }
 }
 
