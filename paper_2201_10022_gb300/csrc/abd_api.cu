@@ -185,7 +185,7 @@ void broad_and_enumerate(Scene& s, bool swept, bool ccd) {
 // the body terms and the incoming-pair lists (which need only q and the
 // body pairs) and the friction terms (only x) run beside the active set and
 // the barrier terms, and join before the assembly
-void eval_system(Scene& s, const double* q, int project) {
+void eval_system(Scene& s, const double* q, int project, double* newton_x = nullptr) {
   on_side(s, 0, 0, [&]() {
     launch_body_terms(s, q, true, project != 0);
     launch_incoming(s);
@@ -198,7 +198,10 @@ void eval_system(Scene& s, const double* q, int project) {
   join_side(s, 1, 1);
   launch_assemble(s);
   launch_gather(s);
-  launch_precond(s);
+  if (newton_x)  // and the PCG's start on H dx = -g
+    launch_precond_start(s, newton_x);
+  else
+    launch_precond(s);
   launch_energy_total(s, true);
 }
 
@@ -335,12 +338,12 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
     // clamped counts, so an overflowed system is only discarded)
     run_segment(s, s.seg_sys[s.fp32_proj ? 1 : 0], [&]() {
       launch_transform(s, s.q.p, s.x.p);
-      eval_system(s, s.q.p, 1);
-      launch_negate(s, s.g.p, s.qsave.p, 12L * s.nb);
       if (s.dense_n) {
+        eval_system(s, s.q.p, 1);
+        launch_negate(s, s.g.p, s.qsave.p, 12L * s.nb);
         launch_dense_solve(s, s.qsave.p, s.dq.p);
       } else {
-        pcg_begin(s, s.qsave.p, s.dq.p);
+        eval_system(s, s.q.p, 1, s.dq.p);
         pcg_iterate(s, s.dq.p, 2, s.prm.pcg_rel_tol);
       }
       cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);

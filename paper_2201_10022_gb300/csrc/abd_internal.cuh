@@ -318,6 +318,8 @@ constexpr int kDenseMaxOrder = 3072;
 int dense_order(int nb, int max_dofs);
 void launch_dense_solve(Scene& s, const double* rhs, double* x);
 void pcg_begin(Scene& s, const double* rhs, double* xout);
+// preconditioner factors fused with the start of the Newton solve H dx = -g
+void launch_precond_start(Scene& s, double* xout);
 void pcg_iterate(Scene& s, double* xout, int n, double rel_tol);
 int pcg_finish(Scene& s, double* xout, int done_iters, int max_iter, double rel_tol, double* rel_res);
 void launch_reset_toi(Scene& s);

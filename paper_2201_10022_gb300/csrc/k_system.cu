@@ -1023,6 +1023,74 @@ __device__ __forceinline__ void chol_apply(const double* __restrict__ F, const d
   }
 }
 
+// the Newton solve's start fused with the preconditioner: per body the
+// factor of its diagonal block (as k_precond, stored the same way), then
+// r = -g (dynamic rows), x = 0, z = (L L^T)^-1 r from the factor in registers
+// (the arithmetic of chol_apply), p = z, and the block's partials of r.z and
+// r.r (32 bodies per block) for k_pcg_start
+__global__ void __launch_bounds__(kBodyWarp) k_precond_start(int nb, const uint8_t* is_static, const double* D,
+                                                             double* Pinv, const double* g, double* x, double* r,
+                                                             double* z, double* pv, double* part, DevStatus* st) {
+  __shared__ double S[kBodyWarp][145];
+  const int t = threadIdx.x;
+  const long b0 = (long)blockIdx.x * kBodyWarp, b = b0 + t;
+  for (int k = t; k < kBodyWarp * 144; k += kBodyWarp) {
+    const int bb = k / 144, e = k - 144 * bb;
+    S[bb][e] = b0 + bb < nb ? D[144 * (b0 + bb) + e] : 0.0;
+  }
+  __syncthreads();
+  const bool live = b < nb && !is_static[b];
+  double L[78];
+#pragma unroll
+  for (int i = 0; i < 12; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) L[tri(i, j)] = S[t][12 * i + j];
+  const bool fallback = live && !chol12(L);
+  // the factor into the staging rows, in the stored layout (as k_precond)
+#pragma unroll
+  for (int i = 0; i < 12; ++i)
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      double v = 0.0;
+      if (live && !fallback && j <= i) v = L[tri(i, j)];
+      if (fallback && i == j) v = rsqrt(fabs(S[t][13 * i]));
+      S[t][12 * i + j] = v;
+    }
+  if (fallback) set_flag(st, ST_PCG_BREAKDOWN);
+  double rz = 0.0, rr = 0.0;
+  if (b < nb) {
+    double rb[12], zb[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      rb[i] = live ? -g[12 * b + i] : 0.0;
+      r[12 * b + i] = rb[i];
+      x[12 * b + i] = 0.0;
+      rr += rb[i] * rb[i];
+    }
+    chol_apply(S[t], rb, zb);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      z[12 * b + i] = zb[i];
+      pv[12 * b + i] = zb[i];
+      rz += rb[i] * zb[i];
+    }
+  }
+  __syncthreads();
+  for (int k = t; k < kBodyWarp * 144; k += kBodyWarp) {
+    const int bb = k / 144, e = k - 144 * bb;
+    if (b0 + bb < nb) Pinv[144 * (b0 + bb) + e] = S[bb][e];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    rz += __shfl_down_sync(kFull, rz, o);
+    rr += __shfl_down_sync(kFull, rr, o);
+  }
+  if (t == 0) {
+    part[2 * blockIdx.x] = rz;
+    part[2 * blockIdx.x + 1] = rr;
+  }
+}
+
+
 // ---------------------------------------------------------------------------
 // PCG on the block system: y = H v from the diagonal blocks, the stored
 // upper blocks of the body's rows and the transposed blocks of its incoming
@@ -1476,6 +1544,14 @@ void launch_gather(Scene& s) {
   counted(s);
   k_gather<<<blocks(32L * s.nb, 256), 256, 0, s.stream>>>(s.nb, s.is_static.p, s.rowoff.p, s.in_off.p, s.in_list.p,
                                                           s.pblk.p, s.Db.p, s.gb.p, s.D.p, s.g.p, s.st);
+}
+
+void launch_precond_start(Scene& s, double* xout) {
+  const int nbk = blocks(s.nb, kBodyWarp);
+  counted(s, 2);
+  k_precond_start<<<nbk, kBodyWarp, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.Pinv.p, s.g.p, xout, s.r.p, s.z.p,
+                                                   s.pv.p, s.part.p, s.st);
+  k_pcg_start<<<1, 256, 0, s.stream>>>(s.part.p, nbk, s.st);
 }
 
 void launch_precond(Scene& s) {
