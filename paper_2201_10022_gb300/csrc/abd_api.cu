@@ -1074,7 +1074,8 @@ abd_status abd_step_batch(abd_scene* const* scenes, int n, int nsteps, int nwork
 }
 
 static const char* kSlotNames[PF_COUNT] = {"enumerate_ccd", "active_set", "barrier_terms", "friction_terms",
-                                           "assemble_blocks", "body_terms", "pcg_spmv", "body_pairs"};
+                                           "assemble_blocks", "body_terms", "pcg_spmv", "body_pairs",
+                                           "dense_solve"};
 
 abd_status abd_set_profiling(abd_scene* S, int on) {
   if (!S) return ABD_ERR_INVALID_ARG;
@@ -1107,7 +1108,7 @@ abd_status abd_get_profile(abd_scene* S, abd_kernel_profile* out, int cap, int* 
     out[k].launches = s.prof.slot[k].launches;
     out[k].total_ms = ms;
     out[k].bytes = s.prof.slot[k].bytes;
-    out[k].flops = k == PF_BARRIER ? bar_flops : 0.0;
+    out[k].flops = k == PF_BARRIER ? bar_flops : s.prof.slot[k].flops;
   }
   return check_cuda(s);
 }

@@ -113,7 +113,9 @@ struct FricRec {
 };
 
 // ---- optional per-kernel timing (CUDA events on the scene's stream) -----------
-enum ProfSlot { PF_ENUM = 0, PF_ACTIVE, PF_BARRIER, PF_FRICTION, PF_ASSEMBLE, PF_BODY, PF_SPMV, PF_ROWS, PF_COUNT };
+enum ProfSlot {
+  PF_ENUM = 0, PF_ACTIVE, PF_BARRIER, PF_FRICTION, PF_ASSEMBLE, PF_BODY, PF_SPMV, PF_ROWS, PF_DENSE, PF_COUNT
+};
 
 struct Prof {
   bool on = false;
@@ -123,6 +125,7 @@ struct Prof {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
     long launches = 0;
     double bytes = 0;  // algorithmic bytes of the recorded launches
+    double flops = 0;  // algorithmic flops of the recorded launches (where known on the host)
   } slot[PF_COUNT];
   unsigned long long bar_terms0[4] = {0, 0, 0, 0};  // counters when profiling started
 };
@@ -277,8 +280,8 @@ struct ProfScope {
   Scene& s;
   int slot;
   cudaEvent_t a = nullptr;
-  double bytes;
-  ProfScope(Scene& sc, int sl, double b = 0) : s(sc), slot(sl), bytes(b) {
+  double bytes, flops;
+  ProfScope(Scene& sc, int sl, double b = 0, double f = 0) : s(sc), slot(sl), bytes(b), flops(f) {
     if (s.prof.on) {
       a = prof_event(s);
       cudaEventRecord(a, s.stream);
@@ -291,6 +294,7 @@ struct ProfScope {
       s.prof.slot[slot].ev.emplace_back(a, e);
       s.prof.slot[slot].launches++;
       s.prof.slot[slot].bytes += bytes;
+      s.prof.slot[slot].flops += flops;
     }
   }
 };

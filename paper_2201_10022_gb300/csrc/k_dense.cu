@@ -188,6 +188,8 @@ int dense_order(int nb, int max_dofs) {
 void launch_dense_solve(Scene& s, const double* rhs, double* x) {
   const int N = s.dense_n, nt = N / kT;
   double* A = s.dense.p;
+  // algorithmic flops: the factorisation N^3 / 3 and two substitutions 2 N^2
+  ProfScope pd(s, PF_DENSE, 0.0, (double)N * N * N / 3.0 + 2.0 * N * N);
   counted(s, 3);
   k_dense_begin<<<1, 1, 0, s.stream>>>(s.st);
   cudaMemsetAsync(A, 0, sizeof(double) * N * N, s.stream);

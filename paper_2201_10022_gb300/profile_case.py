@@ -3,9 +3,12 @@ cuda:0 (for profilers: a small, self-terminating case).
 
     python -m paper_2201_10022_gb300.profile_case packed 10 10 10 --evals 2
     python -m paper_2201_10022_gb300.profile_case lattice 25 20 20 --steps 3
+    python -m paper_2201_10022_gb300.profile_case throw 4 10 0 --steps 20 --dense --newton-rel 1e-9 --prof
 
 `packed` evaluates energy, gradient and Hessian of a contact-dense block of
-cubes (every face pair within d-hat); `lattice` advances the lattice pile.
+cubes (every face pair within d-hat); `lattice` advances the lattice pile;
+`throw` advances the throw-into-stack scene (dims: cubes per side of the
+thrown block, stack height, unused).
 """
 import argparse
 
@@ -17,25 +20,53 @@ from .abd import AbdScene
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("scene", choices=["packed", "lattice"])
+    ap.add_argument("scene", choices=["packed", "lattice", "throw"])
     ap.add_argument("dims", type=int, nargs=3)
     ap.add_argument("--evals", type=int, default=1)
     ap.add_argument("--steps", type=int, default=0)
     ap.add_argument("--prof", action="store_true", help="print per-slot kernel times (CUDA events)")
+    ap.add_argument("--dense", action="store_true", help="dense direct solves (dense_max_dofs 3072)")
+    ap.add_argument("--newton-rel", type=float, default=0.0,
+                    help="Newton tolerance relative to the dynamic bodies' box diagonal (0: library default)")
     a = ap.parse_args()
     nx, ny, nz = a.dims
-    s = scenes.packed_cubes(nx=nx, ny=ny, nz=nz) if a.scene == "packed" else scenes.lattice_pile(nx=nx, ny=ny, nz=nz)
-    g = AbdScene(s)
+    if a.scene == "packed":
+        s = scenes.packed_cubes(nx=nx, ny=ny, nz=nz)
+    elif a.scene == "lattice":
+        s = scenes.lattice_pile(nx=nx, ny=ny, nz=nz)
+    else:
+        s = scenes.throw_stack(n_throw=nx ** 3, n_stack=ny)
+    kw = {}
+    if a.dense:
+        kw["dense_max_dofs"] = 3072
+    if a.newton_rel > 0:
+        import numpy as np
+        q = s.q0
+        Am = q[s.vbody, 3:].reshape(-1, 3, 3)
+        x = np.einsum("vij,vj->vi", Am, s.xbar) + q[s.vbody, :3]
+        x = x[s.is_static[s.vbody] == 0]
+        kw["newton_tol"] = a.newton_rel * float(np.linalg.norm(x.max(axis=0) - x.min(axis=0)))
+    g = AbdScene(s, **kw)
     q = torch.tensor(s.q0)
     E, grad, cnt = g.energy_grad_hess(q)  # warm-up (buffer growth)
     if a.prof:
         g.set_profiling(True)
     for _ in range(a.evals):
         E, grad, cnt = g.energy_grad_hess(q)
+    st = None
     if a.steps:
-        g.step(a.steps)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = g.step(a.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        st = dict(st, ms_per_step=e0.elapsed_time(e1) / a.steps)
     torch.cuda.synchronize()
     out = {"bodies": s.nb, "active": cnt["n_active"], "candidates": cnt["n_candidates"], "energy": float(E[0])}
+    if st:
+        out["steps"] = {k: st[k] for k in ("ms_per_step", "newton_iters", "pcg_iters", "ls_halvings", "n_active",
+                                           "kernel_launches")}
     if a.prof:
         out["kernels"] = {k: {"launches": v["launches"], "ms": round(v["total_ms"], 4),
                               "tflops": round(v["flops"] / (v["total_ms"] * 1e-3) / 1e12, 4) if v["total_ms"] > 0 and v["flops"] else None}
