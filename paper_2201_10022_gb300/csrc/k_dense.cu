@@ -40,13 +40,17 @@ __global__ void k_dense_fill(int nb, int N, const uint8_t* is_static, const doub
   }
 }
 
-// Cholesky of the diagonal tile k (lower factor in place; 1 / L_jj in dinv)
+// Cholesky of the diagonal tile k (lower factor in place; 1 / L_jj in dinv).
+// Warp c holds column c of the tile, lane r its row r (the tile is staged
+// transposed): every step's column scaling and rank-1 update are whole-warp
+// instructions, and the pivot's reciprocal square root is one lane's work
 __global__ void __launch_bounds__(1024) k_dense_potrf(double* A, int N, int k, double* dinv, DevStatus* st) {
-  __shared__ double T[kT][kT + 1];
+  __shared__ double T[kT][kT + 1];  // T[c][r] = A(o + r, o + c)
+  __shared__ double inv;
   __shared__ int bad;
-  const int t = threadIdx.x, r = t / kT, c = t - kT * (t / kT);
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const long o = (long)kT * k;
-  T[r][c] = A[(o + r) * N + o + c];
+  T[lane][w] = A[(o + w) * N + o + lane];  // coalesced rows, transposed into columns
   if (t == 0) bad = 0;
   __syncthreads();
   for (int j = 0; j < kT; ++j) {
@@ -56,35 +60,37 @@ __global__ void __launch_bounds__(1024) k_dense_potrf(double* A, int N, int k, d
         bad = 1;
         d = 1.0;  // keep the factor finite; the solve is marked as failed
       }
-      const double s = sqrt(d);
-      T[j][j] = s;
-      dinv[o + j] = 1.0 / s;
+      const double rs = rsqrt(d);
+      T[j][j] = d * rs;
+      inv = rs;
+      dinv[o + j] = rs;
     }
     __syncthreads();
-    if (c == j && r > j) T[r][j] /= T[j][j];
+    if (w == j && lane > j) T[j][lane] *= inv;
     __syncthreads();
-    if (r > j && c > j && c <= r) T[r][c] -= T[r][j] * T[c][j];
+    if (w > j && lane >= w) T[w][lane] -= T[j][lane] * T[j][w];
     __syncthreads();
   }
-  if (r >= c) A[(o + r) * N + o + c] = T[r][c];
+  if (w >= lane) A[(o + w) * N + o + lane] = T[lane][w];
   if (t == 0 && bad) st->scal[6] = 2.0;
 }
 
-// tiles below the diagonal in column k: X = A_ik L_kk^-T
+// tiles below the diagonal in column k: X = A_ik L_kk^-T (warp c holds
+// column c of X and of L, lane r row r)
 __global__ void __launch_bounds__(1024) k_dense_trsm(double* A, int N, int k, const double* dinv) {
-  __shared__ double L[kT][kT + 1], X[kT][kT + 1];
-  const int t = threadIdx.x, r = t / kT, c = t - kT * (t / kT);
+  __shared__ double L[kT][kT + 1], X[kT][kT + 1];  // transposed: [column][row]
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const long o = (long)kT * k, oi = (long)kT * (k + 1 + blockIdx.x);
-  L[r][c] = A[(o + r) * N + o + c];
-  X[r][c] = A[(oi + r) * N + o + c];
+  L[lane][w] = A[(o + w) * N + o + lane];
+  X[lane][w] = A[(oi + w) * N + o + lane];
   __syncthreads();
   for (int j = 0; j < kT; ++j) {
-    if (c == j) X[r][j] *= dinv[o + j];
+    if (w == j) X[j][lane] *= dinv[o + j];
     __syncthreads();
-    if (c > j) X[r][c] -= X[r][j] * L[c][j];
+    if (w > j) X[w][lane] -= X[j][lane] * L[j][w];
     __syncthreads();
   }
-  A[(oi + r) * N + o + c] = X[r][c];
+  A[(oi + w) * N + o + lane] = X[lane][w];
 }
 
 // trailing tiles (i, j), k < j <= i: A_ij -= L_ik L_jk^T
@@ -116,6 +122,7 @@ __global__ void __launch_bounds__(1024) k_dense_trsv(const double* A, int N, int
                                                      const uint8_t* is_static, const double* rhs, double* x,
                                                      const DevStatus* cst) {
   extern __shared__ double y[];
+  __shared__ double Dt[kT][kT + 1];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
   for (int i = t; i < N; i += blockDim.x) y[i] = (i < n && !is_static[i / 12]) ? rhs[i] : 0.0;
   __syncthreads();
@@ -123,12 +130,14 @@ __global__ void __launch_bounds__(1024) k_dense_trsv(const double* A, int N, int
   // L y = b
   for (int k = 0; k < nt; ++k) {
     const long o = (long)kT * k;
+    Dt[w][lane] = A[(o + w) * N + o + lane];  // the diagonal tile, staged
+    __syncthreads();
     if (w == 0) {
       double v = y[o + lane];
       for (int j = 0; j < kT; ++j) {
         const double yj = __shfl_sync(0xffffffffu, v * dinv[o + j], j);
         if (lane == j) v = yj;
-        if (lane > j) v -= A[(o + lane) * N + o + j] * yj;
+        if (lane > j) v -= Dt[lane][j] * yj;
       }
       y[o + lane] = v;
     }
@@ -143,12 +152,14 @@ __global__ void __launch_bounds__(1024) k_dense_trsv(const double* A, int N, int
   // L^T x = y
   for (int k = nt - 1; k >= 0; --k) {
     const long o = (long)kT * k;
+    Dt[w][lane] = A[(o + w) * N + o + lane];
+    __syncthreads();
     if (w == 0) {
       double v = y[o + lane];
       for (int j = kT - 1; j >= 0; --j) {
         const double xj = __shfl_sync(0xffffffffu, v * dinv[o + j], j);
         if (lane == j) v = xj;
-        if (lane < j) v -= A[(o + j) * N + o + lane] * xj;
+        if (lane < j) v -= Dt[j][lane] * xj;
       }
       y[o + lane] = v;
     }
