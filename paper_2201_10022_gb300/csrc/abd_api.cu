@@ -81,6 +81,7 @@ void size_pair_buffers(Scene& s, size_t pcap) {
   grow(s, s.cand, pcap * (size_t)s.maxc);
   grow(s, s.act, pcap * (size_t)s.maxc);
   grow(s, s.act_d2, pcap * (size_t)s.maxc);
+  grow(s, s.amask, pcap * (size_t)energy_chunks(s));
 }
 
 void size_term_buffers(Scene& s, size_t tcap) {
@@ -709,6 +710,7 @@ void abd_destroy(abd_scene* S) {
   release(s, s.l2e);
   release(s, s.scan_part);
   release(s, s.hfix);
+  release(s, s.amask);
   release(s, s.bbox32);
   release(s, s.vbody);
   release(s, s.tri);

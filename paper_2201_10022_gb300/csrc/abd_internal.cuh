@@ -191,6 +191,7 @@ struct Scene {
   Buf<int4> act;       // np*maxc: (i | kind << 31, j, type, unused)
   Buf<int> acount, aoff;
   Buf<double> act_d2;  // np*maxc
+  Buf<unsigned> amask; // np*chunks: active-membership masks of 32-candidate chunks
 
   // per-term energy and derivatives: E, g12, H78 (kTermStride doubles) and
   // the term's four vertices

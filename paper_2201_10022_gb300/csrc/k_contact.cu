@@ -237,40 +237,73 @@ __global__ void k_ccd_chunks(const DevStatus* __restrict__ cst, const int2* cand
   if (lane == 0 && tmin < 1.0) atomicMin(&st->toi_bits, (unsigned long long)__double_as_longlong(tmin));
 }
 
-// active pairs: canonical d^2 < dhat^2, compacted per body pair in slot order
-__global__ void k_active(const int2* __restrict__ P, const DevStatus* __restrict__ cst, const int2* cand,
-                         const int* ccount, const int* tri, const int* edge, const double4* x, double dhat, int maxc,
-                         int4* act, double* act_d2, int* acount, DevStatus* st) {
+// active pairs, pass 1: one warp per (body pair, 32 candidates): canonical
+// d^2, type and membership d^2 < dhat^2 of every candidate in its own slot,
+// and the chunk's membership mask
+__global__ void k_active(const DevStatus* __restrict__ cst, const int2* cand, const int* ccount, const int* tri,
+                         const int* edge, const double4* x, double dhat, int maxc, int nch, int4* act, double* act_d2,
+                         unsigned* amask, DevStatus* st) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+  const long nw = (long)cst->np * nch;
+  const double dh2 = __dmul_rn(dhat, dhat);
+  for (long w = (long)blockIdx.x * (blockDim.x >> 5) + warp; w < nw; w += nwarps) {
+    const int p = (int)(w / nch), c = (int)(w - (long)p * nch);
+    const int n = min(ccount[p], maxc);
+    if (c * 32 >= n) continue;
+    const int k = c * 32 + lane;
+    bool a = false;
+    if (k < n) {
+      const size_t slot = (size_t)p * maxc + k;
+      const int2 cc = cand[slot];
+      const int kind = (unsigned)cc.x >> 31, i = cc.x & 0x7fffffff;
+      int v[4];
+      pair_vertices(kind, i, cc.y, tri, edge, v);
+      v3 xs[4];
+      for (int m = 0; m < 4; ++m) xs[m] = mk(x[v[m]]);
+      int type = 0;
+      const double d2 = pair_dist2(kind, xs, type);
+      a = d2 < dh2;
+      if (a && d2 == 0.0) set_flag(st, ST_INTERSECT);
+      if (!(d2 == d2)) set_flag(st, ST_NONFINITE);
+      act[slot] = make_int4(cc.x, cc.y, type, 0);
+      act_d2[slot] = d2;
+    }
+    const unsigned m = __ballot_sync(kFull, a);
+    if (lane == 0) amask[(size_t)p * nch + c] = m;
+  }
+}
+
+// active pairs, pass 2: one warp per body pair moves the active candidates to
+// the front of the pair's slots in slot order and counts them.  In place: the
+// targets of a chunk lie at or below its own slots (every lane reads before
+// any writes), never in a later chunk.
+__global__ void k_active_compact(const DevStatus* __restrict__ cst, const int* ccount, int maxc, int nch,
+                                 const unsigned* amask, int4* act, double* act_d2, int* acount) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int np = cst->np;
-  const double dh2 = __dmul_rn(dhat, dhat);
   for (int p = blockIdx.x * (blockDim.x >> 5) + warp; p < np; p += nwarps) {
     const int n = min(ccount[p], maxc);
     int base = 0;
-    for (int k0 = 0; k0 < n; k0 += 32) {
-      int k = k0 + lane;
-      bool a = false;
-      int type = 0;
-      double d2 = 0.0;
-      int2 c = make_int2(0, 0);
-      if (k < n) {
-        c = cand[(size_t)p * maxc + k];
-        int kind = (unsigned)c.x >> 31, i = c.x & 0x7fffffff;
-        int v[4];
-        pair_vertices(kind, i, c.y, tri, edge, v);
-        v3 xs[4];
-        for (int m = 0; m < 4; ++m) xs[m] = mk(x[v[m]]);
-        d2 = pair_dist2(kind, xs, type);
-        a = d2 < dh2;
-        if (a && d2 == 0.0) set_flag(st, ST_INTERSECT);
-        if (!(d2 == d2)) set_flag(st, ST_NONFINITE);
-      }
-      unsigned m = __ballot_sync(kFull, a);
-      if (a) {
-        int pos = base + __popc(m & ((1u << lane) - 1u));
-        act[(size_t)p * maxc + pos] = make_int4(c.x, c.y, type, 0);
-        act_d2[(size_t)p * maxc + pos] = d2;
+    for (int c = 0; c * 32 < n; ++c) {
+      const unsigned m = amask[(size_t)p * nch + c];
+      if (m) {
+        const bool bit = (m >> lane) & 1u;
+        const size_t src = (size_t)p * maxc + c * 32 + lane;
+        int4 v = make_int4(0, 0, 0, 0);
+        double d = 0.0;
+        if (bit) {
+          v = act[src];
+          d = act_d2[src];
+        }
+        __syncwarp();
+        if (bit) {
+          const size_t dst = (size_t)p * maxc + base + __popc(m & ((1u << lane) - 1u));
+          act[dst] = v;
+          act_d2[dst] = d;
+        }
+        __syncwarp();
       }
       base += __popc(m);
     }
@@ -468,11 +501,15 @@ void launch_enumerate(Scene& s, bool swept, bool ccd) {
 }
 
 void launch_active(Scene& s, const double4* x) {
-  int grid = grid_for(2L * s.nb, 8, sm_grid(s, 16));  // grid-stride over the device's pair count
-  counted(s);
+  const int nch = energy_chunks(s);
+  counted(s, 2);
   ProfScope ps(s, PF_ACTIVE);
-  k_active<<<grid, 256, 0, s.stream>>>(s.P.p, s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.prm.dhat, s.maxc,
-                                       s.act.p, s.act_d2.p, s.acount.p, s.st);
+  // grid-stride over the device's pair count
+  k_active<<<grid_for(2L * s.nb * nch, 8, sm_grid(s, 32)), 256, 0, s.stream>>>(
+      s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.prm.dhat, s.maxc, nch, s.act.p, s.act_d2.p, s.amask.p,
+      s.st);
+  k_active_compact<<<grid_for(2L * s.nb, 8, sm_grid(s, 16)), 256, 0, s.stream>>>(
+      s.st, s.ccount.p, s.maxc, nch, s.amask.p, s.act.p, s.act_d2.p, s.acount.p);
 }
 
 void launch_friction_lag(Scene& s) {
