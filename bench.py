@@ -158,7 +158,7 @@ def bbox_diag(x):
     return float(np.linalg.norm(x.max(axis=0) - x.min(axis=0)))
 
 
-def adjoint_run(dev, nsteps=100, seed=4, budget_s=150.0):
+def adjoint_run(dev, nsteps=100, seed=4, budget_s=120.0):
     """Throw into a stack (64 thrown cubes, 10-cube stack, FP64): forward and
     implicit-function backward through nsteps steps; loss = squared distance
     of the thrown cubes' mean final translation to a seeded target; gradients
@@ -225,23 +225,25 @@ def adjoint_run(dev, nsteps=100, seed=4, budget_s=150.0):
         return {"horizon": T, "body": b, "component": k, "adjoint": adj, "central_difference": fd,
                 "rel_mismatch": abs(adj - fd) / max(abs(fd), 1e-300)}
 
-    # the full horizon, then a short one (before the thrown block reaches the
-    # stack), whose loss is the same function of the first 20 steps' end state
+    # a short horizon first (the thrown block in flight, its cubes touching
+    # one another, the stack settling): the loss is a smooth function of the
+    # initial velocities there; then the full horizon, whose 64-body
+    # collisions make the loss chaotic (the central difference and the
+    # adjoint derivative need not agree at any practical h; reported)
+    T = 20
+    q0s = torch.tensor(s.q0, device=dev, requires_grad=True)
+    qd0s = torch.tensor(s.qdot0, device=dev, requires_grad=True)
+    kbs = torch.tensor(s.kappa_body, device=dev, requires_grad=True)
+    qKs, _ = Rollout.apply(g, T, q0s, qd0s, kbs)
+    loss_of(qKs).backward()
     for b, k in ((int(thrown[0]), 0), (int(thrown[-1]), 2)):
         if time.perf_counter() - t_start > budget_s:
             break
+        checks.append(fd_check(T, b, k, float(qd0s.grad[b, k].item())))
+    for b, k in ((int(thrown[0]), 0),):
+        if time.perf_counter() - t_start > budget_s:
+            break
         checks.append(fd_check(nsteps, b, k, float(qd0.grad[b, k].item())))
-    T = 20
-    if time.perf_counter() - t_start < budget_s:
-        q0s = torch.tensor(s.q0, device=dev, requires_grad=True)
-        qd0s = torch.tensor(s.qdot0, device=dev, requires_grad=True)
-        kbs = torch.tensor(s.kappa_body, device=dev, requires_grad=True)
-        qKs, _ = Rollout.apply(g, T, q0s, qd0s, kbs)
-        loss_of(qKs).backward()
-        for b, k in ((int(thrown[0]), 0), (int(thrown[-1]), 2)):
-            if time.perf_counter() - t_start > budget_s:
-                break
-            checks.append(fd_check(T, b, k, float(qd0s.grad[b, k].item())))
     out["fd_checks"] = checks
     g.close()
     return out
@@ -435,7 +437,12 @@ def run_abd(args, rank, world):
         gm.close()
 
     log("timed, profiled, e2e and mixed runs done")
-    adjoint = adjoint_run(dev) if args.adjoint else None
+    adjoint = None
+    if not args.no_adjoint:
+        try:
+            adjoint = adjoint_run(dev)
+        except Exception as e:  # reported in the line, not fatal to the headline measurement
+            adjoint = {"error": f"{type(e).__name__}: {e}"}
     batched = None
     if not args.no_batched:
         try:
@@ -518,8 +525,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision run")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-scene batch run")
-    ap.add_argument("--adjoint", action="store_true",
-                    help="also run the throw-into-stack adjoint (slow: block-Jacobi PCG on the 10-cube stack)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the throw-into-stack adjoint run")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
