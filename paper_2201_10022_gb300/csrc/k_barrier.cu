@@ -354,17 +354,106 @@ __device__ __forceinline__ bool jacobi_round(int r, int lane, const T* Kc, T* Kn
     }
   }
   __syncwarp();
-  for (int e = lane; e < N * N; e += 32) {
+  // the lane's entries computed together (independent chains), then stored
+  constexpr int NE = (N * N + 31) / 32;
+  T kn[NE], vn[NE];
+#pragma unroll
+  for (int it = 0; it < NE; ++it) {
+    const int e = min(lane + 32 * it, N * N - 1);
     const int a = e / N, b = e - N * (e / N);
     int pa = rr_partner(r, a, NP), pb = rr_partner(r, b, NP);
     if (pa >= N) pa = a;  // rs[a] == 0 then
     if (pb >= N) pb = b;
     const T ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
-    Kn[e] = ca * (cb * Kc[a * N + b] + sb * Kc[a * N + pb]) + sa * (cb * Kc[pa * N + b] + sb * Kc[pa * N + pb]);
-    Vn[e] = cb * Vc[a * N + b] + sb * Vc[a * N + pb];
+    kn[it] = ca * (cb * Kc[a * N + b] + sb * Kc[a * N + pb]) + sa * (cb * Kc[pa * N + b] + sb * Kc[pa * N + pb]);
+    vn[it] = cb * Vc[a * N + b] + sb * Vc[a * N + pb];
+  }
+#pragma unroll
+  for (int it = 0; it < NE; ++it) {
+    const int e = lane + 32 * it;
+    if (e < N * N) {
+      Kn[e] = kn[it];
+      Vn[e] = vn[it];
+    }
   }
   __syncwarp();
   return __ballot_sync(kAll, took) != 0;
+}
+
+// out[a N + b] = sum_k X[a xa + k xk] Y[k yk + b yb] (k ascending), the
+// lane's entries accumulated together; out must not overlap X or Y
+template <int N>
+__device__ __forceinline__ void mat_prod(int lane, const double* X, int xa, int xk, const double* Y, int yk, int yb,
+                                         double* out) {
+  constexpr int NE = (N * N + 31) / 32;
+  double acc[NE];
+  int ia[NE], ib[NE];
+#pragma unroll
+  for (int it = 0; it < NE; ++it) {
+    const int e = min(lane + 32 * it, N * N - 1);
+    ia[it] = e / N;
+    ib[it] = e - N * (e / N);
+    acc[it] = 0.0;
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+#pragma unroll
+    for (int it = 0; it < NE; ++it) acc[it] += X[ia[it] * xa + k * xk] * Y[k * yk + ib[it] * yb];
+  __syncwarp();
+#pragma unroll
+  for (int it = 0; it < NE; ++it) {
+    const int e = lane + 32 * it;
+    if (e < N * N) out[e] = acc[it];
+  }
+}
+
+// block congruence out = (R x I) X (R^T x I) for an upper-triangular M x M
+// R (3x3 blocks of an N = 3M matrix), per entry in the order c, e2 ascending
+template <int N, typename TR>
+__device__ __forceinline__ void block_congruence(int lane, const TR* R, const double* X, double* out) {
+  constexpr int M = N / 3, NE = (N * N + 31) / 32;
+  double acc[NE];
+#pragma unroll
+  for (int it = 0; it < NE; ++it) {
+    const int e = min(lane + 32 * it, N * N - 1);
+    const int a = e / N, b = e - N * (e / N);
+    const int Ia = a / 3, i = a - 3 * Ia, Jb = b / 3, j = b - 3 * Jb;
+    double t = 0.0;
+    for (int c = Ia; c < M; ++c)
+      for (int e2 = Jb; e2 < M; ++e2) t += R[3 * Ia + c] * R[3 * Jb + e2] * X[(3 * c + i) * N + 3 * e2 + j];
+    acc[it] = t;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int it = 0; it < NE; ++it) {
+    const int e = lane + 32 * it;
+    if (e < N * N) out[e] = acc[it];
+  }
+}
+
+// Newton-Schulz step out = 1.5 V - 0.5 V S (k ascending per entry)
+template <int N>
+__device__ __forceinline__ void ns_step(int lane, const double* V, const double* S, double* out) {
+  constexpr int NE = (N * N + 31) / 32;
+  double acc[NE];
+  int ia[NE], ib[NE];
+#pragma unroll
+  for (int it = 0; it < NE; ++it) {
+    const int e = min(lane + 32 * it, N * N - 1);
+    ia[it] = e / N;
+    ib[it] = e - N * (e / N);
+    acc[it] = 1.5 * V[ia[it] * N + ib[it]];
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+#pragma unroll
+    for (int it = 0; it < NE; ++it) acc[it] -= 0.5 * V[ia[it] * N + k] * S[k * N + ib[it]];
+  __syncwarp();
+#pragma unroll
+  for (int it = 0; it < NE; ++it) {
+    const int e = lane + 32 * it;
+    if (e < N * N) out[e] = acc[it];
+  }
 }
 
 template <typename T>
@@ -462,9 +551,18 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
   __syncwarp();
   double E;
   if (!moll) {
-    for (int e = lane; e < N * N; e += 32) {
-      const int a = e / N, b = e - N * (e / N);
-      W.H[e] = ca * gs[a] * gs[b] + cg * hs_entry(T, gs, gD, gt, a, b);
+    {
+      constexpr int NE = (N * N + 31) / 32;
+      double h[NE];
+#pragma unroll
+      for (int it = 0; it < NE; ++it) {
+        const int e = min(lane + 32 * it, N * N - 1);
+        const int a = e / N, b = e - N * (e / N);
+        h[it] = ca * gs[a] * gs[b] + cg * hs_entry(T, gs, gD, gt, a, b);
+      }
+#pragma unroll
+      for (int it = 0; it < NE; ++it)
+        if (lane + 32 * it < N * N) W.H[lane + 32 * it] = h[it];
     }
     if (lane < N) gr[lane] = cg * gs[lane];
     E = Eb;
@@ -528,14 +626,7 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
   const double* Hr = W.H;
   if (project) {
     double* K = W.Kd[0];
-    for (int e = lane; e < N * N; e += 32) {
-      const int a = e / N, b = e - N * (e / N);
-      const int Ia = a / 3, i = a - 3 * Ia, Jb = b / 3, j = b - 3 * Jb;
-      double t = 0.0;
-      for (int c = Ia; c < M; ++c)
-        for (int e2 = Jb; e2 < M; ++e2) t += W.Rm[3 * Ia + c] * W.Rm[3 * Jb + e2] * W.H[(3 * c + i) * N + 3 * e2 + j];
-      K[e] = t;
-    }
+    block_congruence<N>(lane, W.Rm, W.H, K);
     __syncwarp();
     double mx = 0.0;
     for (int e = lane; e < N * N; e += 32) mx = fmax(mx, fabs(K[e]));
@@ -602,34 +693,14 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
       double *V0 = W.Vd[0], *V1 = W.Vd[1], *S = W.H;
       for (int e = lane; e < N * N; e += 32) V0[e] = (double)W.V32[cur][e];
       __syncwarp();
-      for (int e = lane; e < N * N; e += 32) {
-        const int a = e / N, b = e - N * (e / N);
-        double t = 0.0;
-        for (int k = 0; k < N; ++k) t += V0[k * N + a] * V0[k * N + b];
-        S[e] = t;
-      }
+      mat_prod<N>(lane, V0, 1, N, V0, N, 1, S);  // S = V0^T V0
       __syncwarp();
-      for (int e = lane; e < N * N; e += 32) {
-        const int a = e / N, b = e - N * (e / N);
-        double t = 1.5 * V0[a * N + b];
-        for (int k = 0; k < N; ++k) t -= 0.5 * V0[a * N + k] * S[k * N + b];
-        V1[e] = t;
-      }
+      ns_step<N>(lane, V0, S, V1);
       __syncwarp();
       double* KV = W.H;
-      for (int e = lane; e < N * N; e += 32) {
-        const int a = e / N, b = e - N * (e / N);
-        double t = 0.0;
-        for (int k = 0; k < N; ++k) t += K[a * N + k] * V1[k * N + b];
-        KV[e] = t;
-      }
+      mat_prod<N>(lane, K, N, 1, V1, N, 1, KV);  // K V1
       __syncwarp();
-      for (int e = lane; e < N * N; e += 32) {
-        const int a = e / N, b = e - N * (e / N);
-        double t = 0.0;
-        for (int k = 0; k < N; ++k) t += V1[k * N + a] * KV[k * N + b];
-        W.Kd[1][e] = t;
-      }
+      mat_prod<N>(lane, V1, 1, N, KV, N, 1, W.Kd[1]);  // V1^T (K V1)
       __syncwarp();
       for (int e = lane; e < N * N; e += 32) {
         const int a = e / N, b = e - N * (e / N);
@@ -665,41 +736,16 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
         double* V2 = W.Vd[0];  // free: the first basis lives in V1
         for (int e = lane; e < N * N; e += 32) V2[e] = (double)W.V32[c2][e];
         __syncwarp();
-        for (int e = lane; e < N * N; e += 32) {  // S = V2^T V2 into H
-          const int a = e / N, b = e - N * (e / N);
-          double t = 0.0;
-          for (int k = 0; k < N; ++k) t += V2[k * N + a] * V2[k * N + b];
-          W.H[e] = t;
-        }
+        mat_prod<N>(lane, V2, 1, N, V2, N, 1, W.H);  // S = V2^T V2 into H
         __syncwarp();
         double* V2n = W.Kd[1];
-        for (int e = lane; e < N * N; e += 32) {
-          const int a = e / N, b = e - N * (e / N);
-          double t = 1.5 * V2[a * N + b];
-          for (int k = 0; k < N; ++k) t -= 0.5 * V2[a * N + k] * W.H[k * N + b];
-          V2n[e] = t;
-        }
+        ns_step<N>(lane, V2, W.H, V2n);
         __syncwarp();
-        for (int e = lane; e < N * N; e += 32) {  // K' V2 into H
-          const int a = e / N, b = e - N * (e / N);
-          double t = 0.0;
-          for (int k = 0; k < N; ++k) t += K[a * N + k] * V2n[k * N + b];
-          W.H[e] = t;
-        }
+        mat_prod<N>(lane, K, N, 1, V2n, N, 1, W.H);  // K' V2 into H
         __syncwarp();
-        for (int e = lane; e < N * N; e += 32) {  // K'' = V2^T (K' V2) into Vd[0]
-          const int a = e / N, b = e - N * (e / N);
-          double t = 0.0;
-          for (int k = 0; k < N; ++k) t += V2n[k * N + a] * W.H[k * N + b];
-          V2[e] = t;
-        }
+        mat_prod<N>(lane, V2n, 1, N, W.H, N, 1, V2);  // K'' = V2^T (K' V2) into Vd[0]
         __syncwarp();
-        for (int e = lane; e < N * N; e += 32) {  // V = V' V2 into H
-          const int a = e / N, b = e - N * (e / N);
-          double t = 0.0;
-          for (int k = 0; k < N; ++k) t += V1[a * N + k] * V2n[k * N + b];
-          W.H[e] = t;
-        }
+        mat_prod<N>(lane, V1, N, 1, V2n, N, 1, W.H);  // V = V' V2 into H
         __syncwarp();
         for (int e = lane; e < N * N; e += 32) {
           const int a = e / N, b = e - N * (e / N);
@@ -746,22 +792,10 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
         W.H[e] = t;
       }
       __syncwarp();
-      for (int e = lane; e < N * N; e += 32) {  // T V^T
-        const int a = e / N, b = e - N * (e / N);
-        double t = 0.0;
-        for (int l = 0; l < N; ++l) t += W.H[a * N + l] * Vf[b * N + l];
-        Pk[e] = t;
-      }
+      mat_prod<N>(lane, W.H, N, 1, Vf, 1, N, Pk);  // T V^T
       __syncwarp();
       // back to the difference coordinates: (Ri x I) Proj (Ri^T x I)
-      for (int e = lane; e < N * N; e += 32) {
-        const int a = e / N, b = e - N * (e / N);
-        const int Ia = a / 3, i = a - 3 * Ia, Jb = b / 3, j = b - 3 * Jb;
-        double t = 0.0;
-        for (int c = Ia; c < M; ++c)
-          for (int e2 = Jb; e2 < M; ++e2) t += W.Ri[3 * Ia + c] * W.Ri[3 * Jb + e2] * Pk[(3 * c + i) * N + 3 * e2 + j];
-        P[e] = t;
-      }
+      block_congruence<N>(lane, W.Ri, Pk, P);
       }  // FP64 refinement
     } else {
       for (int e = lane; e < N * N; e += 32) P[e] = 0.0;
