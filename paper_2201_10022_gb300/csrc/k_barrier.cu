@@ -456,80 +456,6 @@ __device__ __forceinline__ void ns_step(int lane, const double* V, const double*
   }
 }
 
-// Register-resident FP32 Jacobi: lane a < N holds row a of K and of V.  The
-// rounds of the circle schedule are unrolled, so every column's partner is a
-// compile-time index; the lane's own partner (run time) only selects shuffle
-// sources.  Same rotations and update formulas as jacobi_round.
-template <int N>
-__device__ __forceinline__ float sel_reg(const float (&x)[N], int i) {
-  float r = x[0];
-#pragma unroll
-  for (int j = 1; j < N; ++j) r = i == j ? x[j] : r;
-  return r;
-}
-
-template <int N, bool REL, int R>
-__device__ __forceinline__ bool jacobi_round_reg(int lane, float (&k)[N], float (&v)[N]) {
-  constexpr int NP = N + (N & 1);
-  const int pr = lane < NP ? rr_partner(R, lane, NP) : lane;
-  const bool live = lane < N && pr < N;
-  const int pa = live ? pr : lane;  // shuffle source: the partner, or itself
-  const float kaa = sel_reg<N>(k, lane);
-  const float kap = sel_reg<N>(k, pa);
-  const float kpp = __shfl_sync(kAll, kaa, pa);
-  const float kpa = __shfl_sync(kAll, kap, pa);  // the partner's entry toward this row
-  float c = 1.0f, sg = 0.0f;
-  bool took = false;
-  if (live) {
-    const bool isp = lane < pa;  // this row is p of the pair (p, q), p < q
-    const float app = isp ? kaa : kpp, aqq = isp ? kpp : kaa, apq = isp ? kap : kpa;
-    float s = 0.0f;
-    if (REL && fabsf(apq) <= 1e-7f * sqrtf(fabsf(app * aqq))) {
-      c = 1.0f;
-    } else {
-      rot32(app, aqq, apq, c, s);
-    }
-    took = s != 0.0f;
-    sg = isp ? -s : s;  // J_{partner, row}
-  }
-  float kp[N], cb[N], sb[N];
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-    kp[j] = __shfl_sync(kAll, k[j], pa);
-    cb[j] = __shfl_sync(kAll, c, j);
-    sb[j] = __shfl_sync(kAll, sg, j);
-  }
-  if (lane < N) {
-    float kn[N], vn[N];
-#pragma unroll
-    for (int b = 0; b < N; ++b) {
-      int pb = rr_partner(R, b, NP);
-      if (pb >= N) pb = b;  // sb[b] == 0 then
-      kn[b] = c * (cb[b] * k[b] + sb[b] * k[pb]) + sg * (cb[b] * kp[b] + sb[b] * kp[pb]);
-      vn[b] = cb[b] * v[b] + sb[b] * v[pb];
-    }
-#pragma unroll
-    for (int b = 0; b < N; ++b) {
-      k[b] = kn[b];
-      v[b] = vn[b];
-    }
-  }
-  return __ballot_sync(kAll, took) != 0;
-}
-
-// one sweep (all rounds); whether any rotation was taken
-template <int N, bool REL, int R = 0>
-__device__ __forceinline__ bool sweep_reg(int lane, float (&k)[N], float (&v)[N]) {
-  constexpr int NP = N + (N & 1);
-  if constexpr (R < NP - 1) {
-    const bool t = jacobi_round_reg<N, REL, R>(lane, k, v);
-    const bool u = sweep_reg<N, REL, R + 1>(lane, k, v);
-    return t || u;
-  } else {
-    return false;
-  }
-}
-
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kAll, v, o);
@@ -715,40 +641,20 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
       }
       __syncwarp();
       constexpr int NP = N + (N & 1);
-      const int cur = 0;
-      int n32 = 0, n64 = 0, capped = 0;
-      {
-        float kr[N], vr[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          kr[j] = lane < N ? W.K32[0][lane * N + j] : 0.0f;
-          vr[j] = lane < N ? W.V32[0][lane * N + j] : 0.0f;
+      int cur = 0, n32 = 0, n64 = 0, capped = 0;
+      float prev = INFINITY;
+      for (int sweep = 0; sweep < 12; ++sweep) {
+        float off, tot;
+        off_tot<N>(W.K32[cur], lane, off, tot);
+        if (!(off > 1e-13f * tot)) break;
+        if (off < 1e-9f * tot && off > 0.25f * prev) break;  // at the FP32 rounding floor
+        prev = off;
+        ++n32;
+        for (int r = 0; r < NP - 1; ++r) {
+          jacobi_round<N, float>(r, lane, W.K32[cur], W.K32[cur ^ 1], W.V32[cur], W.V32[cur ^ 1], W.rc32, W.rs32,
+                                 1.0);
+          cur ^= 1;
         }
-        float prev = INFINITY;
-        for (int sweep = 0; sweep < 12; ++sweep) {
-          float off = 0.0f, tot = 0.0f;
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            const float q2 = kr[j] * kr[j];
-            tot += q2;
-            off += j == lane ? 0.0f : q2;
-          }
-          off = warp_sum(off);
-          tot = warp_sum(tot);
-          if (!(off > 1e-13f * tot)) break;
-          if (off < 1e-9f * tot && off > 0.25f * prev) break;  // at the FP32 rounding floor
-          prev = off;
-          ++n32;
-          sweep_reg<N, false>(lane, kr, vr);
-        }
-        __syncwarp();
-        if (lane < N)
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            W.K32[0][lane * N + j] = kr[j];
-            W.V32[0][lane * N + j] = vr[j];
-          }
-        __syncwarp();
       }
       if (mixed) {
         // mixed precision: the clamp from the FP32 eigenpairs, no FP64
@@ -816,27 +722,16 @@ __device__ void warp_term(int f, int lane, WarpScratch& W, const int4* __restric
           W.V32[0][e] = (e / N == e - N * (e / N)) ? 1.0f : 0.0f;
         }
         __syncwarp();
-        const int c2 = 0;
-        {
-          float kr[N], vr[N];
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            kr[j] = lane < N ? W.K32[0][lane * N + j] : 0.0f;
-            vr[j] = lane < N ? W.V32[0][lane * N + j] : 0.0f;
+        int c2 = 0;
+        for (int sweep = 0; sweep < 5; ++sweep) {
+          bool any = false;
+          for (int r = 0; r < NP - 1; ++r) {
+            any |= jacobi_round<N, float, true>(r, lane, W.K32[c2], W.K32[c2 ^ 1], W.V32[c2], W.V32[c2 ^ 1], W.rc32,
+                                                W.rs32, 1.0);
+            c2 ^= 1;
           }
-          for (int sweep = 0; sweep < 5; ++sweep) {
-            const bool any = sweep_reg<N, true>(lane, kr, vr);
-            ++n32;
-            if (!any) break;
-          }
-          __syncwarp();
-          if (lane < N)
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-              W.K32[0][lane * N + j] = kr[j];
-              W.V32[0][lane * N + j] = vr[j];
-            }
-          __syncwarp();
+          ++n32;
+          if (!any) break;
         }
         double* V2 = W.Vd[0];  // free: the first basis lives in V1
         for (int e = lane; e < N * N; e += 32) V2[e] = (double)W.V32[c2][e];
