@@ -443,14 +443,16 @@ def run_abd(args, rank, world):
         gm.close()
 
     log("timed, profiled, e2e and mixed runs done")
+    # the adjoint and the many-scene batch are single-GPU figures: under
+    # torchrun (N > 1) the replicas time the headline step only
     adjoint = None
-    if not args.no_adjoint:
+    if not args.no_adjoint and world == 1:
         try:
             adjoint = adjoint_run(dev)
         except Exception as e:  # reported in the line, not fatal to the headline measurement
             adjoint = {"error": f"{type(e).__name__}: {e}"}
     batched = None
-    if not args.no_batched:
+    if not args.no_batched and world == 1:
         try:
             batched = batched_run(dev)
         except Exception as e:  # reported in the line, not fatal to the headline measurement
