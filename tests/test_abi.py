@@ -34,3 +34,23 @@ def test_binding_signatures_load():
     L = abd.load()
     for n in abd.EXPORTS:
         assert getattr(L, n).argtypes is not None or n == "abd_last_error"
+
+
+def test_default_params_through_the_struct_layout():
+    """abd_default_params is host-only: reading its fields back through the
+    binding's ctypes mirror checks the struct layout field by field"""
+    p = abd.abd_default_params()
+    assert p.dt == 0.01 and p.dhat == 1e-3 and p.kappa == 1e8
+    assert list(p.gravity) == [0.0, 0.0, -9.8]
+    assert p.mu == 0.0 and p.eps_v == 1e-3 and p.newton_tol == 0.0 and p.pcg_rel_tol == 1e-4
+    assert p.ls_slack_rel == 1e-12 and p.ccd_s == 0.1
+    assert (p.newton_max, p.pcg_max, p.ls_max, p.ccd_max) == (500, 20000, 30, 10000)
+    assert p.precision == 0 and p.dense_max_dofs == 0
+
+
+def test_host_side_argument_checks():
+    L = abd.load()
+    t = abd.abd_tuning()
+    assert L.abd_get_tuning(None, ctypes.byref(t)) == 1  # ABD_ERR_INVALID_ARG
+    t.grid_div = 0
+    assert L.abd_set_tuning(None, ctypes.byref(t)) == 1
