@@ -195,7 +195,9 @@ ABD_API abd_status abd_get_pairs(abd_scene* s, int which, int* kind, int* i, int
                          long* n);
 
 /* Solve H dq = rhs with block-Jacobi PCG on the Hessian of the last
- * abd_energy_grad_hess (the linear solve of each Newton iteration). */
+ * abd_energy_grad_hess (the linear solve of each Newton iteration), or by the
+ * dense Cholesky when dense_max_dofs covers the scene (stats: 0 iterations,
+ * residual 0).  Static bodies' rows of dq are zero. */
 ABD_API abd_status abd_solve(abd_scene* s, const double* rhs_dev, double* dq_dev, abd_solve_stats* stats);
 
 /* Largest step alpha in (0, 1] such that the linear vertex trajectories from
@@ -250,7 +252,9 @@ ABD_API abd_status abd_get_profile(abd_scene* s, abd_kernel_profile* out, int ca
  * at q_next (body blocks M + dt^2 hess V_ortho, barrier terms without the PSD
  * clamp, friction with its lagged quantities held fixed) and
  *   rhs = dL/dq_next + dL/dqdot_next / dt   (qdot_next = (q_next - q_t)/dt),
- * it solves H lam = rhs by the block-Jacobi PCG to rel_tol and, since
+ * it solves H lam = rhs by the block-Jacobi PCG to rel_tol (or by the dense
+ * Cholesky when the scene was created with dense_max_dofs covering it; a
+ * non-positive pivot is ABD_ERR_PCG_BREAKDOWN) and, since
  * dL/dq~ = M lam (q~ = q_t + dt qdot_t + dt^2 g):
  *   gq    <- M lam - dL/dqdot_next / dt          (dL/dq_t)
  *   gqdot <- dt M lam                            (dL/dqdot_t)
