@@ -90,6 +90,7 @@ def lib():
             "orc_sym_eig": (None, [i, vp, vp, vp]), "orc_project_psd": (None, [i, vp]),
             "orc_accd": (i, [i, vp, vp, d, d, i, vp]),
             "orc_friction_pair": (d, [vp, vp, vp, vp, d, d, vp, vp]),
+            "orc_closest_weights": (d, [i, vp, vp, vp]),
             "orc_candidates": (l, [vp, vp, vp, i, vp, vp, vp, l]),
             "orc_energy_grad_hess": (i, [vp, vp, vp, vp, i]), "orc_energy": (d, [vp, vp]),
             "orc_hess_nblocks": (l, [vp]), "orc_hess_copy": (None, [vp, vp, vp, vp]),
@@ -191,6 +192,15 @@ def accd(kind, x12, dx12, s=0.1, tmax=1.0, max_iter=10000):
     t = np.zeros(1)
     st = lib().orc_accd(kind, _p(x), _p(dx), s, tmax, max_iter, _p(t))
     return t[0], st
+
+
+def closest_weights(kind, x12):
+    """(d2, type, gamma): the friction closest-point weights of a pair"""
+    x = _f64(x12, 12)
+    ga = np.zeros(4)
+    t = C.c_int()
+    d2 = lib().orc_closest_weights(int(kind), _p(x), _p(ga), C.byref(t))
+    return d2, t.value, ga
 
 
 def friction_pair(x12, gamma, n, r, mu_lambda, eps):

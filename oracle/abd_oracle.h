@@ -90,6 +90,10 @@ void orc_project_psd(int n, double* A);
 int orc_accd(int kind, const double x[12], const double dx[12], double s, double tmax, int max_iter, double* toi);
 double orc_friction_pair(const double x[12], const double gamma[4], const double nrm[3], const double r[3],
                          double mu_lambda, double eps, double g[12], double H[144]);
+/* friction closest-point weights (Sec. 4 lagged friction): returns d^2 and the
+ * type; gamma such that sum_v gamma_v x_v = point on the first primitive minus
+ * point on the second */
+double orc_closest_weights(int kind, const double x[12], double gamma[4], int* type);
 
 /* --- candidate sets ------------------------------------------------------------ */
 /* x1 == NULL: proximity set at x0; otherwise swept set over segments x0 -> x1.

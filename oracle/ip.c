@@ -365,8 +365,9 @@ double orc_ortho(const double q[12], double kappa, double vol, double g[12], dou
 }
 
 /* Per-body IP term E_b = 1/2 (q-qt)^T M (q-qt) + dt^2 V.  Hessian reading:
- * M + dt^2 * PSD(Hess V) (the orthogonality Hessian is projected on its own,
- * as IPC does for elastic terms, so the block stays positive definite). */
+ * the whole block M + dt^2 Hess V, used as it is when a Cholesky
+ * factorisation succeeds (the block is positive definite) and eigen-clamped
+ * to the PSD cone as one 12x12 block only when it fails. */
 static double body_terms(orc_ctx* c, int b, const double* q, double* g, double* H, int project, double* Eo) {
   const double* M = c->M + 144 * b;
   const double* qt = c->qtilde + 12 * b;
@@ -661,6 +662,17 @@ static void closest_weights(int kind, int type, const double x[12], double gam[4
     gam[2] = -(1 - t);
     gam[3] = -t;
   }
+}
+
+/* closest-point weights of a pair (test hook): the distance type from the
+ * canonical classification, then gamma with sum_v gamma_v x_v = (closest
+ * point on the first primitive) - (closest point on the second) */
+double orc_closest_weights(int kind, const double x[12], double gamma[4], int* type) {
+  int t = 0;
+  double d2 = orc_pair_dist2(kind, x, &t);
+  closest_weights(kind, t, x, gamma);
+  if (type) *type = t;
+  return d2;
 }
 
 /* derivative of the clamped barrier in d */
