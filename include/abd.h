@@ -131,13 +131,19 @@ typedef struct {
 } abd_solve_stats;
 
 typedef struct {
-  int newton_iters, pcg_iters, ls_halvings;
+  int newton_iters, pcg_iters;
+  int ls_halvings;     /* line-search rounds after the first trial of each Newton iteration */
   long n_candidates, n_active, n_swept;
   double toi_min;      /* smallest CCD step bound seen in the step */
   double last_step;    /* max vertex |J dq| of the last Newton step */
   long kernel_launches;       /* kernels the library launched for the step(s) */
   long candidates_tested;     /* candidate pairs distance-tested in the step(s) */
   long active_evaluated;      /* barrier terms (E, gradient, Hessian) evaluated */
+  int ccd_limited;     /* Newton iterations whose smallest island CCD bound was < 1 */
+  int toi_hist[6];     /* Newton iterations by that bound: 1, [0.1,1), [0.01,0.1),
+                          [1e-3,0.01), [1e-4,1e-3), below 1e-4 */
+  int n_islands;       /* contact islands of the last Newton iteration */
+  int ls_island_halvings_max;  /* most halvings any island needed in one Newton iteration */
 } abd_step_stats;
 
 /* Per-kernel timing of one kernel class, accumulated while profiling is on. */
@@ -193,6 +199,15 @@ ABD_API abd_status abd_get_hessian(abd_scene* s, double* diag, int* bi, int* bj,
  * Arrays may be NULL to query the count only. */
 ABD_API abd_status abd_get_pairs(abd_scene* s, int which, int* kind, int* i, int* j, int* type, double* d2, long cap,
                          long* n);
+
+/* Copy the lagged friction records of the current step start (Sec. 4,
+ * friction potential V_F with lambda, the closest points and the normal
+ * frozen at q^t), in the order of abd_get_pairs(which = 2): gamma (4 per
+ * pair: the closest-point weights, so that sum_v gamma_v x_v is the point on
+ * the first primitive minus the point on the second), normal (3 per pair,
+ * unit) and offset (3 per pair, sum_v gamma_v x_v at q^t).  Host arrays, at
+ * most cap records each; any may be NULL; *n receives the count. */
+ABD_API abd_status abd_get_friction(abd_scene* s, double* gamma, double* normal, double* offset, long cap, long* n);
 
 /* Solve H dq = rhs with block-Jacobi PCG on the Hessian of the last
  * abd_energy_grad_hess (the linear solve of each Newton iteration), or by the
@@ -297,14 +312,24 @@ ABD_API abd_status abd_get_counters(abd_scene* s, abd_counters* out);
  *                  abd_get_pairs (point then triangle, or edge then edge)
  *   kind_dev       npairs bytes (device): 0 point-triangle, 1 edge-edge
  *   ccd_s, ccd_max ACCD gap fraction and iteration cap (as abd_params)
- *   toi_host       receives min over pairs of the time of impact in (0, 1]
+ *   toi_host       receives min over pairs of the time of impact in [0, 1]
+ *                  (0: a pair starts at zero distance); when a pair reaches
+ *                  ccd_max the call returns ABD_ERR_CCD_MAXITER and toi_host
+ *                  still receives the minimum, in which such a pair counts
+ *                  with the time it had advanced to (a conservative lower
+ *                  bound: its trajectory is intersection-free up to there)
  * Scratch is a file-scope device array of 262,144 pair slots (2 MiB) that
  * every GPU loading the library holds until exit; npairs beyond that returns
- * ABD_ERR_CAPACITY, an out-of-range vertex or kind ABD_ERR_INVALID_ARG.
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  All calls share the one array, so
- * calls that overlap on the GPU (other streams, other threads) race.  The
- * call synchronises `stream` (a cudaStream_t, NULL = legacy default). */
+ * ABD_ERR_CAPACITY, an out-of-range vertex or kind ABD_ERR_INVALID_ARG (the
+ * kernel checks each index before it loads through it).
+ * The first call in each CUDA context (per device: the primary context, or
+ * a driver-API context current on the calling thread; again after
+ * cudaDeviceReset) looks up the array's device address and caches it under
+ * the context's id; make that first call before any stream capture.  All
+ * calls share the one array, so calls that overlap on the GPU (other
+ * streams, other threads) race.  The call synchronises `stream` (a
+ * cudaStream_t, NULL = legacy default) and reports only errors of its own
+ * launches and copies. */
 ABD_API abd_status abd_ccd_toi_pairs_noalloc(const double* x_dev, const double* dx_dev, int nv, const int* verts_dev,
                                              const unsigned char* kind_dev, long npairs, double ccd_s, int ccd_max,
                                              void* stream, double* toi_host);

@@ -97,6 +97,7 @@ def lib():
             "orc_active_pairs": (l, [vp, vp, vp, vp, vp, vp, vp, l]),
             "orc_grad_rows": (i, [vp, vp, i, vp, vp]),
             "orc_pairs_count": (l, [vp, i]), "orc_pairs_copy": (None, [vp, i, vp, vp, vp, vp, vp]),
+            "orc_friction_copy": (None, [vp, vp, vp, vp]),
             "orc_solve": (i, [vp, vp, vp, vp]), "orc_ccd_toi": (i, [vp, vp, vp, vp]),
             "orc_step": (i, [vp, i, vp]),
         }
@@ -364,6 +365,16 @@ class Oracle:
         d2 = np.zeros(m)
         L.orc_pairs_copy(self.ctx, which, _p(kind), _p(pi), _p(pj), _p(ty), _p(d2))
         return dict(kind=kind[:n], i=pi[:n], j=pj[:n], type=ty[:n], val=d2[:n])
+
+    def friction_records(self):
+        """lagged friction records (order of pairs(2)): gamma (n x 4), unit
+        normal (n x 3), lagged offset r (n x 3)"""
+        L = lib()
+        n = L.orc_pairs_count(self.ctx, 2)
+        m = max(n, 1)
+        ga, nn, rr = np.zeros((m, 4)), np.zeros((m, 3)), np.zeros((m, 3))
+        L.orc_friction_copy(self.ctx, _p(ga), _p(nn), _p(rr))
+        return ga[:n], nn[:n], rr[:n]
 
     def dense_hessian(self):
         diag, bp, blocks = self.hessian()

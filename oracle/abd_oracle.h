@@ -114,6 +114,9 @@ long orc_hess_nblocks(const orc_ctx* c);
 void orc_hess_copy(const orc_ctx* c, double* diag, int* bpairs, double* blocks);
 long orc_pairs_count(const orc_ctx* c, int which); /* 0 candidates, 1 active, 2 friction */
 void orc_pairs_copy(const orc_ctx* c, int which, int* kind, int* pi, int* pj, int* type, double* d2);
+/* lagged friction records in the order of orc_pairs_copy(which = 2): closest-
+ * point weights (4 per pair), unit normal and lagged offset (3 each) */
+void orc_friction_copy(const orc_ctx* c, double* gamma, double* nrm, double* r);
 
 /* --- solve, CCD, step ------------------------------------------------------ */
 int orc_solve(orc_ctx* c, const double* rhs, double* dq, int* iters); /* H dq = rhs, last H */

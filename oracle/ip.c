@@ -1117,6 +1117,16 @@ void orc_pairs_copy(const orc_ctx* c, int which, int* kind, int* pi, int* pj, in
   }
 }
 
+void orc_friction_copy(const orc_ctx* c, double* gamma, double* nrm, double* r) {
+  for (long k = 0; k < c->nfr; ++k) {
+    for (int m = 0; m < 4; ++m) gamma[4 * k + m] = c->fr[k].gamma[m];
+    for (int m = 0; m < 3; ++m) {
+      nrm[3 * k + m] = c->fr[k].n[m];
+      r[3 * k + m] = c->fr[k].r[m];
+    }
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* linear solve of the last Hessian: dense Cholesky (the paper's direct LLT) */
 /* for small systems, block-Jacobi preconditioned CG otherwise.             */

@@ -57,7 +57,8 @@ class abd_step_stats(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("pcg_iters", C.c_int), ("ls_halvings", C.c_int),
                 ("n_candidates", C.c_long), ("n_active", C.c_long), ("n_swept", C.c_long),
                 ("toi_min", C.c_double), ("last_step", C.c_double), ("kernel_launches", C.c_long),
-                ("candidates_tested", C.c_long), ("active_evaluated", C.c_long)]
+                ("candidates_tested", C.c_long), ("active_evaluated", C.c_long), ("ccd_limited", C.c_int),
+                ("toi_hist", C.c_int * 6), ("n_islands", C.c_int), ("ls_island_halvings_max", C.c_int)]
 
 
 class abd_kernel_profile(C.Structure):
@@ -83,7 +84,8 @@ def _as_dict(st):
 
 _lib = None
 EXPORTS = ["abd_default_params", "abd_create_scene", "abd_destroy", "abd_set_state", "abd_get_state",
-           "abd_energy_grad_hess", "abd_get_hessian", "abd_get_pairs", "abd_solve", "abd_ccd_toi", "abd_step",
+           "abd_energy_grad_hess", "abd_get_hessian", "abd_get_pairs", "abd_get_friction", "abd_solve",
+           "abd_ccd_toi", "abd_step",
            "abd_set_profiling", "abd_get_profile", "abd_get_counters", "abd_adjoint_step",
            "abd_ccd_toi_pairs_noalloc", "abd_set_tuning", "abd_get_tuning", "abd_step_batch", "abd_last_error"]
 
@@ -111,6 +113,7 @@ def load(build_if_missing: bool = True):
         "abd_energy_grad_hess": (i, [vp, vp, vp, vp, vp]),
         "abd_get_hessian": (i, [vp, vp, vp, vp, vp, l, vp]),
         "abd_get_pairs": (i, [vp, i, vp, vp, vp, vp, vp, l, vp]),
+        "abd_get_friction": (i, [vp, vp, vp, vp, l, vp]),
         "abd_solve": (i, [vp, vp, vp, vp]),
         "abd_ccd_toi": (i, [vp, vp, vp, vp]),
         "abd_step": (i, [vp, i, vp]),
@@ -177,6 +180,10 @@ def abd_get_hessian(h, diag, bi, bj, blocks, cap, nblocks):
 
 def abd_get_pairs(h, which, kind, i, j, type_, d2, cap, n):
     return load().abd_get_pairs(h, which, kind, i, j, type_, d2, cap, n)
+
+
+def abd_get_friction(h, gamma, normal, offset, cap, n):
+    return load().abd_get_friction(h, gamma, normal, offset, cap, n)
 
 
 def abd_solve(h, rhs_ptr, dq_ptr, stats):
@@ -370,6 +377,17 @@ class AbdScene:
                                   m, C.byref(n)))
         k = n.value
         return dict(kind=kind[:k], i=pi[:k], j=pj[:k], type=ty[:k], val=d2[:k])
+
+    def friction_records(self):
+        """lagged friction records (order of pairs(2)): gamma (n x 4), unit
+        normal (n x 3), lagged offset (n x 3)"""
+        n = C.c_long()
+        self._check(abd_get_friction(self.h, None, None, None, 0, C.byref(n)))
+        m = max(n.value, 1)
+        ga, nn, rr = np.zeros((m, 4)), np.zeros((m, 3)), np.zeros((m, 3))
+        self._check(abd_get_friction(self.h, _np_ptr(ga), _np_ptr(nn), _np_ptr(rr), m, C.byref(n)))
+        k = n.value
+        return ga[:k], nn[:k], rr[:k]
 
     def solve(self, rhs):
         rhs = self._dev(rhs)

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libabd.so")
-SOURCES = ["k_contact.cu", "k_barrier.cu", "k_system.cu", "k_dense.cu", "abd_api.cu", "noalloc.cu"]
+SOURCES = ["k_contact.cu", "k_barrier.cu", "k_system.cu", "k_pcg.cu", "k_island.cu", "k_dense.cu", "abd_api.cu", "noalloc.cu"]
 HEADERS = ["abd_internal.cuh", "geom.cuh", "derivs.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

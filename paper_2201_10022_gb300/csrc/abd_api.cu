@@ -179,6 +179,7 @@ void broad_and_enumerate(Scene& s, bool swept, bool ccd) {
   cudaMemsetAsync(&s.st->n_cand, 0, sizeof(unsigned long long), s.stream);
   launch_body_boxes(s, swept);
   launch_body_pairs(s);
+  if (ccd) launch_islands(s);  // the CCD bound is taken per contact island
   launch_enumerate(s, swept, ccd);
 }
 
@@ -333,7 +334,7 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
   for (int it = 0; it < s.prm.newton_max; ++it) {
     s.fp32_proj = !hp;
     // system at q and the Newton direction H dq = -g, enqueued as one
-    // sequence with the solver's first two iterations; the status word read
+    // sequence with the whole PCG solve (one persistent launch); the status word read
     // back at its end also carries the system's flags and energies, checked
     // before the direction is used (every kernel bounds its work by the
     // clamped counts, so an overflowed system is only discarded)
@@ -345,13 +346,14 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
         launch_dense_solve(s, s.qsave.p, s.dq.p);
       } else {
         eval_system(s, s.q.p, 1, s.dq.p);
-        pcg_iterate(s, s.dq.p, 2, s.prm.pcg_rel_tol);
+        launch_pcg_solve(s, s.dq.p, s.prm.pcg_max, s.prm.pcg_rel_tol);
       }
       cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
     });
     cudaStreamSynchronize(s.stream);
     double rel;
-    int its = pcg_finish(s, s.dq.p, 2, s.prm.pcg_max, s.prm.pcg_rel_tol, &rel);
+    int its = pcg_result(s, &rel);
+    pcg_account(s, its);
     if (s.st_host->flags & kCapFlags) return ABD_ERR_CAPACITY;
     if (abd_status r = flags_to_status(s, s.st_host->flags)) return r;
     loc.n_active = s.st_host->nact;
@@ -362,9 +364,7 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
       s.err = "PCG breakdown";
       return ABD_ERR_PCG_BREAKDOWN;
     }
-    loc.pcg_iters += its < 0 ? s.prm.pcg_max : its;
-    // E(q) over the active set of this iteration: the line search's reference
-    const double E0 = s.st_host->energy[5];
+    loc.pcg_iters += its == -1 ? s.prm.pcg_max : std::max(its, 0);
     // step length for the convergence test, then (in the same batch) the CCD
     // bound over the swept candidates and the first trial at alpha = bound;
     // the swept candidates also serve the next iteration
@@ -376,9 +376,16 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
       on_side(s, 0, 0, [&]() { launch_max_step(s); });
       launch_reset_toi(s);
       broad_and_enumerate(s, true, true);
-      launch_trial(s, 1.0, true);
+      // per contact island: E at q from the system's terms (before the
+      // trial's energy pass overwrites the body and friction energies), the
+      // step = the island's CCD bound, the first trial and its acceptance
+      launch_island_energy(s, 0);
+      launch_island_start(s);
+      launch_island_trial(s);
       launch_transform(s, s.qtrial.p, s.xt.p);
       eval_energy(s, s.qtrial.p);
+      launch_island_energy(s, 1);
+      launch_island_accept(s);
       cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
     });
     cudaStreamSynchronize(s.stream);
@@ -403,33 +410,35 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
     s.last_np = s.st_host->np;
     if (s.st_host->flags & kCapFlags) return ABD_ERR_CAPACITY;
     if (abd_status r = flags_to_status(s, s.st_host->flags & ~ST_INTERSECT)) return r;
-    double alpha = bits_to_double(s.st_host->toi_bits);
+    const double alpha = bits_to_double(s.st_host->toi_bits);  // smallest island bound
     loc.n_swept = (long)s.st_host->n_cand;
     loc.candidates_tested += (long)s.st_host->n_cand;
     loc.toi_min = std::min(loc.toi_min, alpha);
-    // line search: E(q + alpha dq) <= E(q) + slack over the swept candidates
-    const double slack = s.prm.ls_slack_rel * (fabs(E0) + 1.0);
-    bool ok = false;
-    for (int ls = 0; ls <= s.prm.ls_max; ++ls) {
-      if (ls > 0) {
-        launch_trial(s, alpha, false);
-        launch_transform(s, s.qtrial.p, s.xt.p);
-        eval_energy(s, s.qtrial.p);
-        read_status(s);
-      }
-      if (s.st_host->flags & ST_INTERSECT) {
-        s.err = "line search reached zero distance";
-        return ABD_ERR_INITIAL_INTERSECTION;
-      }
-      double E = s.st_host->energy[0];
-      if (E <= E0 + slack) {
-        ok = true;
-        break;
-      }
-      alpha *= 0.5;
+    if (alpha < 1.0) loc.ccd_limited++;
+    {
+      int bin = 0;
+      for (double edge = 1.0; bin < 5 && alpha < edge; edge *= 0.1) ++bin;
+      loc.toi_hist[bin]++;
+    }
+    loc.n_islands = s.st_host->n_islands;
+    // line search per island: E_i(q + alpha_i dq) <= E_i(q) + slack; islands
+    // that fail halve their own step and are tried again
+    for (int round = 0; s.st_host->ls_pending > 0 && !s.st_host->ls_failed; ++round) {
+      if (s.st_host->flags & ST_INTERSECT) break;
+      launch_island_trial(s);
+      launch_transform(s, s.qtrial.p, s.xt.p);
+      eval_energy(s, s.qtrial.p);
+      launch_island_energy(s, 1);
+      launch_island_accept(s);
+      read_status(s);
       loc.ls_halvings++;
     }
-    if (!ok) {
+    if (s.st_host->flags & ST_INTERSECT) {
+      s.err = "line search reached zero distance";
+      return ABD_ERR_INITIAL_INTERSECTION;
+    }
+    loc.ls_island_halvings_max = std::max(loc.ls_island_halvings_max, s.st_host->ls_halv_max);
+    if (s.st_host->ls_failed) {
       s.err = "line search did not decrease the energy";
       return ABD_ERR_LINESEARCH;
     }
@@ -535,6 +544,10 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
   s.stream = (cudaStream_t)stream;
   s.alloc.stream = s.stream;
   cudaGetDevice(&s.device);
+  if (cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, s.device) != cudaSuccess || s.num_sms < 1) {
+    cudaGetLastError();
+    s.num_sms = kNumSMs;
+  }
   for (cudaStream_t& x : s.side)
     if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
@@ -572,12 +585,19 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
     grow(s, s.kappa_b, nb);
     grow(s, s.density, nb);
     for (Buf<double>* b : {&s.q, &s.qdot, &s.qt, &s.qtilde, &s.dq, &s.qtrial, &s.qsave, &s.qdotsave, &s.gb, &s.g,
-                           &s.r, &s.z, &s.pv, &s.Ap})
+                           &s.r, &s.z, &s.pv, &s.pv2, &s.Ap})
       grow(s, *b, 12L * nb);
+    grow(s, s.pcg_bar, 4);
+    grow(s, s.uf, nb);
+    grow(s, s.isl, nb);
+    grow(s, s.isl_state, 2L * nb);
+    grow(s, s.isl_toi, nb);
+    grow(s, s.isl_E, 16L * nb);
+    grow(s, s.isl_alpha, nb);
     grow(s, s.Eb, 2L * nb);
     for (Buf<double>* b : {&s.Db, &s.D, &s.Pinv}) grow(s, *b, 144L * nb);
     grow(s, s.hfix, nb);
-    grow(s, s.part, 2L * nb + 1024);
+    grow(s, s.part, 3L * pcg_chunks(nb) + 1024);
     for (Buf<double4>* b : {&s.x, &s.dx, &s.x1, &s.xt}) grow(s, *b, nv);
     grow(s, s.bbox, 6L * nb);
     grow(s, s.bbox32, 6L * nb);
@@ -723,8 +743,15 @@ void abd_destroy(abd_scene* S) {
   release(s, s.vol);
   release(s, s.kappa_b);
   release(s, s.density);
+  release(s, s.pcg_bar);
+  release(s, s.uf);
+  release(s, s.isl);
+  release(s, s.isl_state);
+  release(s, s.isl_toi);
+  release(s, s.isl_E);
+  release(s, s.isl_alpha);
   for (Buf<double>* b : {&s.q, &s.qdot, &s.qt, &s.qtilde, &s.dq, &s.qtrial, &s.qsave, &s.qdotsave, &s.gb, &s.g, &s.r,
-                         &s.z, &s.pv, &s.Ap, &s.Eb, &s.Db, &s.D, &s.Pinv, &s.part, &s.bbox, &s.term, &s.fterm,
+                         &s.z, &s.pv, &s.pv2, &s.Ap, &s.Eb, &s.Db, &s.D, &s.Pinv, &s.part, &s.bbox, &s.term, &s.fterm,
                          &s.pblk, &s.Epair, &s.act_d2, &s.red, &s.dense, &s.dense_dinv})
     release(s, *b);
   for (Buf<double4>* b : {&s.x, &s.dx, &s.x1, &s.xt}) release(s, *b);
@@ -894,6 +921,26 @@ abd_status abd_get_pairs(abd_scene* S, int which, int* kind, int* i, int* j, int
   return check_cuda(s);
 }
 
+abd_status abd_get_friction(abd_scene* S, double* gamma, double* normal, double* offset, long cap, long* n) {
+  if (!S || cap < 0) return ABD_ERR_INVALID_ARG;
+  Scene& s = S->s;
+  read_status(s);
+  const long nf = s.st_host->nfr;
+  if (n) *n = nf;
+  if (!gamma && !normal && !offset) return check_cuda(s);
+  std::vector<FricRec> F(nf);
+  if (nf) cudaMemcpy(F.data(), s.fric.p, sizeof(FricRec) * nf, cudaMemcpyDeviceToHost);
+  for (long k = 0; k < std::min(nf, cap); ++k) {
+    for (int m = 0; m < 4; ++m)
+      if (gamma) gamma[4 * k + m] = F[k].gam[m];
+    for (int m = 0; m < 3; ++m) {
+      if (normal) normal[3 * k + m] = F[k].n[m];
+      if (offset) offset[3 * k + m] = F[k].r[m];
+    }
+  }
+  return check_cuda(s);
+}
+
 abd_status abd_solve(abd_scene* S, const double* rhs_dev, double* dq_dev, abd_solve_stats* stats) {
   if (!S || !rhs_dev || !dq_dev) return ABD_ERR_INVALID_ARG;
   Scene& s = S->s;
@@ -960,7 +1007,14 @@ abd_status abd_step(abd_scene* S, int nsteps, abd_step_stats* stats) {
           int ni = acc.newton_iters + one.newton_iters, pi = acc.pcg_iters + one.pcg_iters;
           int lh = acc.ls_halvings + one.ls_halvings;
           double tmin = k ? std::min(acc.toi_min, one.toi_min) : one.toi_min;
+          int cl = acc.ccd_limited + one.ccd_limited;
+          int hist[6];
+          for (int m = 0; m < 6; ++m) hist[m] = acc.toi_hist[m] + one.toi_hist[m];
+          int lhm = std::max(acc.ls_island_halvings_max, one.ls_island_halvings_max);
           acc = one;
+          acc.ccd_limited = cl;
+          for (int m = 0; m < 6; ++m) acc.toi_hist[m] = hist[m];
+          acc.ls_island_halvings_max = lhm;
           acc.candidates_tested = tested;
           acc.active_evaluated = evald;
           acc.newton_iters = ni;
@@ -1076,7 +1130,7 @@ abd_status abd_step_batch(abd_scene* const* scenes, int n, int nsteps, int nwork
 }
 
 static const char* kSlotNames[PF_COUNT] = {"enumerate_ccd", "active_set", "barrier_terms", "friction_terms",
-                                           "assemble_blocks", "body_terms", "pcg_spmv", "body_pairs",
+                                           "assemble_blocks", "body_terms", "pcg_solve", "body_pairs",
                                            "dense_solve"};
 
 abd_status abd_set_profiling(abd_scene* S, int on) {

@@ -56,6 +56,10 @@ struct DevStatus {
   // pairs, pairs left after restricting each side to the other body's box,
   // candidates passing the exact primitive box test
   unsigned long long cull[3];
+  // per-island line search (k_island.cu): islands still pending after the
+  // last acceptance pass, islands, islands past the halving cap, the largest
+  // halving count of any island
+  int ls_pending, n_islands, ls_failed, ls_halv_max;
 };
 
 // ---- small device helpers shared by the kernel files -----------------------
@@ -221,8 +225,21 @@ struct Scene {
   Buf<double> dense, dense_dinv;  // dense_n^2 matrix / factor, reciprocal pivots
   Buf<long long> scan_part;  // tile sums of the two-phase scan
 
-  // PCG
-  Buf<double> r, z, pv, Ap, part;
+  // contact islands (k_island.cu): union-find parents, labels (smallest body
+  // id of the island), per-island CCD bound (bits), exact energy accumulators
+  // (16 per island: 4 digits each of the positive and negative parts of E at
+  // the iterate, then of the trial), line-search
+  // state (accepted, halvings) and step
+  Buf<int> uf, isl, isl_state;
+  Buf<unsigned long long> isl_toi, isl_E;
+  Buf<double> isl_alpha;
+
+  // PCG: residual, preconditioned residual, two alternating directions, H p,
+  // chunk partial sums, the solve kernel's grid-barrier words
+  Buf<double> r, z, pv, pv2, Ap, part;
+  Buf<unsigned> pcg_bar;
+  int num_sms = 152;          // multiprocessors of the scene's device
+  int pcg_blocks_per_sm = 0;  // co-resident blocks of the solve kernel (0: not yet queried)
 
   long nlaunch = 0;              // kernels launched by the library
   long cand_last = 0;            // candidates of the last enumeration
@@ -317,16 +334,25 @@ void launch_adjoint_out(Scene& s, const double* q, const double* lam, double* gq
 void launch_gather(Scene& s);
 void launch_precond(Scene& s);
 void launch_energy_total(Scene& s, bool with_pairs);
+// block-Jacobi PCG (k_pcg.cu): r = sign * rhs, x = 0, z, p and the partial
+// sums of the start (launch_pcg_init); the whole solve in one persistent
+// launch (launch_pcg_solve); its outcome from the status word read back
+// (pcg_result: iterations, -1 at the cap, -2 breakdown); run_pcg does all
+// three and synchronises
+void launch_pcg_init(Scene& s, const double* rhs, double sign, double* xout);
+void launch_pcg_solve(Scene& s, double* xout, int max_iter, double rel_tol);
+int pcg_result(Scene& s, double* rel_res);
+void pcg_account(Scene& s, int its);
 int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res);
+int pcg_chunks(int nb);
+double pcg_iter_bytes(const Scene& s, long np);
+double pcg_iter_flops(const Scene& s, long np);
 // dense direct solve (small scenes): order of the padded matrix, 0 if off
 constexpr int kDenseMaxOrder = 3072;
 int dense_order(int nb, int max_dofs);
 void launch_dense_solve(Scene& s, const double* rhs, double* x);
-void pcg_begin(Scene& s, const double* rhs, double* xout);
-// preconditioner factors fused with the start of the Newton solve H dx = -g
+// the preconditioner (inverse diagonal blocks), then the PCG start on H dx = -g
 void launch_precond_start(Scene& s, double* xout);
-void pcg_iterate(Scene& s, double* xout, int n, double rel_tol);
-int pcg_finish(Scene& s, double* xout, int done_iters, int max_iter, double rel_tol, double* rel_res);
 void launch_reset_toi(Scene& s);
 void launch_max_step(Scene& s);
 void launch_trial(Scene& s, double alpha, bool alpha_from_ccd);
@@ -345,5 +371,12 @@ void launch_barrier(Scene& s, int project, long cap);
 void launch_friction_lag(Scene& s);
 void launch_friction_eval(Scene& s, const double4* x, bool derivs);
 void launch_pair_energy(Scene& s, const double4* x);   // energy only, over candidates
+
+// ---- launchers (k_island.cu) -------------------------------------------------
+void launch_islands(Scene& s);                 // labels of the current body-pair list
+void launch_island_energy(Scene& s, int which); // 0: E at the iterate from the terms; 1: the trial's
+void launch_island_start(Scene& s);            // each island's step = its CCD bound
+void launch_island_trial(Scene& s);            // qtrial = q + alpha_island dq
+void launch_island_accept(Scene& s);           // accept or halve each pending island
 
 }  // namespace abd

@@ -206,10 +206,13 @@ __global__ void k_enumerate(const int2* __restrict__ P, const DevStatus* __restr
 
 // additive CCD (Sec. 4.1) over the stored swept candidates: one warp per
 // (body pair, 32 candidates), the minimum time of impact by an atomic
-// minimum on the bits of the positive double (exact, order-independent)
+// minimum on the bits of the positive double (exact, order-independent):
+// over the scene, and over the body pair's contact island (the island of its
+// dynamic body; every island's bound starts at 1)
 __global__ void k_ccd_chunks(const DevStatus* __restrict__ cst, const int2* cand, const int* ccount, const int* tri,
                              const int* edge, const double4* x, const double4* dx, int maxc, int nch, double ccd_s,
-                             int ccd_max, DevStatus* st) {
+                             int ccd_max, const int2* __restrict__ P, const uint8_t* __restrict__ is_static,
+                             const int* __restrict__ isl, unsigned long long* isl_toi, DevStatus* st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
   const long nw = (long)cst->np * nch;
@@ -218,6 +221,7 @@ __global__ void k_ccd_chunks(const DevStatus* __restrict__ cst, const int2* cand
     const int p = (int)(w / nch), c = (int)(w - (long)p * nch);
     const int n = min(ccount[p], maxc);
     const int k = c * 32 + lane;
+    double t = 1.0;
     if (k < n) {
       const int2 cc = cand[(size_t)p * maxc + k];
       const int kind = (unsigned)cc.x >> 31, i = cc.x & 0x7fffffff;
@@ -228,12 +232,16 @@ __global__ void k_ccd_chunks(const DevStatus* __restrict__ cst, const int2* cand
         xs[m] = mk(x[v[m]]);
         ds[m] = mk(dx[v[m]]);
       }
-      double toi;
-      if (accd(kind, xs, ds, ccd_s, 1.0, ccd_max, toi)) set_flag(st, ST_CCD_MAXITER);
-      tmin = fmin(tmin, toi);
+      if (accd(kind, xs, ds, ccd_s, 1.0, ccd_max, t)) set_flag(st, ST_CCD_MAXITER);
     }
+    for (int o = 16; o > 0; o >>= 1) t = fmin(t, __shfl_xor_sync(kFull, t, o));
+    if (lane == 0 && t < 1.0) {
+      const int2 pr = P[p];
+      const int is = is_static[pr.x] ? isl[pr.y] : isl[pr.x];
+      atomicMin(&isl_toi[is], (unsigned long long)__double_as_longlong(t));
+    }
+    tmin = fmin(tmin, t);
   }
-  for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_xor_sync(kFull, tmin, o));
   if (lane == 0 && tmin < 1.0) atomicMin(&st->toi_bits, (unsigned long long)__double_as_longlong(tmin));
 }
 
@@ -496,7 +504,8 @@ void launch_enumerate(Scene& s, bool swept, bool ccd) {
     const int nch = energy_chunks(s);
     counted(s);
     k_ccd_chunks<<<grid_for(2L * s.nb * nch, 8, sm_grid(s, 32)), 256, 0, s.stream>>>(
-        s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, s.x.p, s.dx.p, s.maxc, nch, s.prm.ccd_s, s.prm.ccd_max, s.st);
+        s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, s.x.p, s.dx.p, s.maxc, nch, s.prm.ccd_s, s.prm.ccd_max, s.P.p,
+        s.is_static.p, s.isl.p, s.isl_toi.p, s.st);
   }
 }
 

@@ -1,0 +1,337 @@
+// Contact islands and the per-island line search of a Newton iteration.
+//
+// The incremental potential (Sec. 4) is a sum of body terms and of pair terms
+// (barrier and lagged friction), each pair term coupling two bodies.  Take the
+// graph whose nodes are the dynamic bodies and whose edges are the body pairs
+// of the swept broad phase (every pair whose d-hat-dilated boxes over the
+// whole step x(q) -> x(q + dq) overlap) and the lagged friction pairs.  Its
+// connected components -- islands -- share no term anywhere on the segment
+// from q to q + dq: E(q + diag(alpha_i) dq) = sum_i E_i(q_i + alpha_i dq_i).
+// So the CCD step bound and the backtracking line search (Sec. 4.1, the
+// filtered Newton step) are taken per island: each island gets the minimum
+// time of impact over its own swept pairs and halves its own step until its
+// own energy does not increase.  An island that needs a short step no longer
+// shortens the step of every other body in the scene; each island's sequence
+// of iterates is the one a Newton loop on that island alone would produce, so
+// the converged point is the same minimiser.
+//
+// Islands are labelled by union-find with the smaller root kept on every link,
+// so each island's label is its smallest body id whatever the order of the
+// links.  Island energies are accumulated exactly: every contribution is a
+// non-negative double (inertia, orthogonality energy, barrier energy and
+// friction energy are all >= 0 up to rounding), converted to a 128-bit
+// fixed-point integer (units of 2^-64) whose four 32-bit digits are added
+// with 64-bit integer atomics (negative ones into a second sum), so the sums
+// are exact and independent of the order of the additions (bit-identical
+// runs).
+#include <stddef.h>
+
+#include <algorithm>
+
+#include "abd_internal.cuh"
+
+namespace abd {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int uf_find(int* parent, int x) {
+  volatile int* p = parent;
+  int px = p[x];
+  while (px != x) {
+    const int gp = p[px];
+    if (gp != px) p[x] = gp;  // path halving: a grandparent is still an ancestor
+    x = px;
+    px = p[x];
+  }
+  return x;
+}
+
+__device__ __forceinline__ void uf_union(int* parent, int a, int b) {
+  while (true) {
+    a = uf_find(parent, a);
+    b = uf_find(parent, b);
+    if (a == b) return;
+    const int lo = min(a, b), hi = max(a, b);
+    if (atomicCAS(&parent[hi], hi, lo) == hi) return;
+  }
+}
+
+// ---- exact non-negative sums ------------------------------------------------
+// digits of floor(v * 2^64) (v >= 0, finite, < 2^64); false if v is out of range
+__device__ __forceinline__ bool fx_digits(double v, unsigned long long d[4]) {
+  d[0] = d[1] = d[2] = d[3] = 0ull;
+  if (v == 0.0) return true;
+  if (!(v > 0.0) || !(v < 18446744073709551616.0)) return false;
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  int ex = (int)((bits >> 52) & 0x7ff);
+  unsigned long long m = bits & ((1ull << 52) - 1);
+  if (ex == 0) ex = 1;
+  else m |= 1ull << 52;
+  const int sh = ex - 1075 + 64;  // floor(v 2^64) = m 2^sh
+  unsigned long long lo = 0, hi = 0;
+  if (sh >= 64) {
+    hi = m << (sh - 64);
+  } else if (sh > 0) {
+    lo = m << sh;
+    hi = m >> (64 - sh);
+  } else if (sh == 0) {
+    lo = m;
+  } else if (sh > -64) {
+    lo = m >> (-sh);
+  }
+  d[0] = lo & 0xffffffffull;
+  d[1] = lo >> 32;
+  d[2] = hi & 0xffffffffull;
+  d[3] = hi >> 32;
+  return true;
+}
+
+// value of four digit accumulators (each < 2^64): carries, then the double
+// (the same integer always gives the same double)
+__device__ __forceinline__ double fx_value(const unsigned long long* acc) {
+  unsigned long long c = 0, dig[5];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const unsigned long long t = acc[k] + c;
+    dig[k] = t & 0xffffffffull;
+    c = t >> 32;
+  }
+  dig[4] = c;
+  return ldexp((double)dig[4], 64) + ldexp((double)dig[3], 32) + (double)dig[2] + ldexp((double)dig[1], -32) +
+         ldexp((double)dig[0], -64);
+}
+
+// add v to an island's accumulator: |v| to base[16 key + 4 (v < 0) + 0..3]
+// (separate sums of the positive and the negative contributions, so that a
+// contribution that rounding made slightly negative is still exact); lanes
+// with the same key and sign first add their digits (integer adds, exact),
+// so that each takes one atomic per digit and warp.  Called by whole warps
+// (on selects the lanes that contribute); the loop over the contributing
+// lanes has the same trip count in every lane.
+__device__ __forceinline__ void fx_add(unsigned long long* base, int island, double v, bool on, DevStatus* st) {
+  unsigned long long d[4];
+  const bool neg = v < 0.0;
+  const int key = 2 * island + (neg ? 1 : 0);
+  if (on && !fx_digits(fabs(v), d)) {
+    set_flag(st, ST_NONFINITE);
+    on = false;
+  }
+  if (!on) d[0] = d[1] = d[2] = d[3] = 0ull;
+  const unsigned act = __ballot_sync(kFull, on && v != 0.0);
+  if (!act) return;
+  const int lane = threadIdx.x & 31;
+  const int mykey = ((act >> lane) & 1) ? key : -1;
+  unsigned long long s[4] = {0ull, 0ull, 0ull, 0ull};
+  unsigned lead = 0;  // lanes that lead a group of equal keys
+  for (unsigned m = act; m; m &= m - 1) {
+    const int src = __ffs(m) - 1;
+    const int k = __shfl_sync(kFull, mykey, src);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned long long x = __shfl_sync(kFull, d[j], src);
+      if (k == mykey) s[j] += x;
+    }
+    // the first contributing lane with this key leads its group
+    const unsigned same = __ballot_sync(kFull, k == mykey) & act;
+    if ((same & ((1u << src) - 1u)) == 0) lead |= 1u << src;
+  }
+  if (((lead >> lane) & 1) && ((act >> lane) & 1)) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (s[j]) atomicAdd(base + 16L * island + 4 * (neg ? 1 : 0) + j, s[j]);
+  }
+}
+
+}  // namespace
+
+// ---- kernels ------------------------------------------------------------------
+// every body its own root; per-root island state cleared
+__global__ void k_isl_init(int nb, int* parent, unsigned long long* toi, unsigned long long* E, int* lstate) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    parent[b] = b;
+    toi[b] = 0x3ff0000000000000ull;  // bits of 1.0
+    for (int k = 0; k < 16; ++k) E[16L * b + k] = 0ull;
+    lstate[2 * b] = 0;
+    lstate[2 * b + 1] = 0;
+  }
+}
+
+// links: dynamic-dynamic body pairs of the list and the lagged friction pairs
+__global__ void k_isl_link(const DevStatus* __restrict__ cst, const int2* P, const int2* fpairs,
+                           const uint8_t* is_static, int* parent) {
+  const int np = cst->np, nfp = cst->nfp;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np + nfp; p += gridDim.x * blockDim.x) {
+    const int2 e = p < np ? P[p] : fpairs[p - np];
+    if (is_static[e.x] || is_static[e.y]) continue;
+    uf_union(parent, e.x, e.y);
+  }
+}
+
+// island label (smallest body id of the island) of every body
+__global__ void k_isl_label(int nb, int* parent, int* isl) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) isl[b] = uf_find(parent, b);
+}
+
+// island of a body pair: that of its dynamic body (pairs of two static bodies
+// are never listed)
+__device__ __forceinline__ int pair_island(const int* isl, const uint8_t* is_static, int a, int b) {
+  return is_static[a] ? isl[b] : isl[a];
+}
+
+// exact per-island energies.  which = 0: the reference energies E0 of the
+// iterate, from the system's stored terms (body energies, barrier terms with
+// their vertices, friction records); which = 1: the trial's, from the
+// energy-only pass (body energies, per body pair and chunk barrier partials,
+// friction records).  One thread per contribution.
+__global__ void k_isl_energy(int which, int nb, const uint8_t* __restrict__ is_static, const int* __restrict__ isl,
+                             const int* __restrict__ vbody, const double* __restrict__ Eb,
+                             const DevStatus* __restrict__ cst, const double* __restrict__ term,
+                             const int4* __restrict__ termv, const double* __restrict__ Epair, int nch,
+                             const int2* __restrict__ P, const double* __restrict__ fterm,
+                             const FricRec* __restrict__ fr, unsigned long long* E, DevStatus* st) {
+  const long nbar = which == 0 ? (long)cst->nact : (long)cst->np * nch;
+  const long nfr = cst->nfr;
+  const long n = 2L * nb + nbar + nfr;
+  unsigned long long* base = E + 8 * which;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long i0 = (long)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+    const long i = i0 + threadIdx.x;
+    bool on = i < n;
+    int key = 0;
+    double v = 0.0;
+    if (on) {
+      if (i < 2L * nb) {
+        const int b = (int)(i >> 1);
+        on = !is_static[b];
+        if (on) {
+          key = isl[b];
+          v = Eb[i];
+        }
+      } else if (i < 2L * nb + nbar) {
+        const long t = i - 2L * nb;
+        if (which == 0) {
+          const int4 vv = termv[t];
+          key = pair_island(isl, is_static, vbody[vv.x], vbody[vv.w]);
+          v = term[t * kTermStride];
+        } else {
+          const int2 pr = P[t / nch];
+          key = pair_island(isl, is_static, pr.x, pr.y);
+          v = Epair[t];
+        }
+      } else {
+        const long f = i - 2L * nb - nbar;
+        key = pair_island(isl, is_static, fr[f].a, fr[f].b);
+        v = fterm[f * kTermStride];
+      }
+    }
+    fx_add(base, key, v, on, st);
+  }
+}
+
+// start of the line search: each island's step = its CCD bound
+__global__ void k_isl_start(int nb, const uint8_t* is_static, const int* isl, const unsigned long long* toi,
+                            double* alpha, int* lstate) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    if (is_static[b] || isl[b] != b) continue;
+    alpha[b] = __longlong_as_double((long long)toi[b]);
+    lstate[2 * b] = 0;      // 0 pending, 1 accepted
+    lstate[2 * b + 1] = 0;  // halvings
+  }
+}
+
+// trial state: q + alpha_island dq (static bodies keep q)
+__global__ void k_isl_trial(int nb, const uint8_t* is_static, const int* isl, const double* alpha, const double* q,
+                            const double* dq, double* qtrial) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 12 * nb; i += gridDim.x * blockDim.x) {
+    const int b = i / 12;
+    qtrial[i] = is_static[b] ? q[i] : fma(alpha[isl[b]], dq[i], q[i]);
+  }
+}
+
+// acceptance of each pending island: E_i(trial) <= E_i(q) + slack (|E_i(q)| + 1)
+// accepts; otherwise the island's step is halved (at most ls_max times).  The
+// trial accumulators are cleared for the next trial; the counts of pending
+// islands, of islands and of failed islands go to the status word.
+__global__ void k_isl_accept(int nb, const uint8_t* is_static, const int* isl, double slack_rel, int ls_max,
+                             unsigned long long* E, double* alpha, int* lstate, DevStatus* st) {
+  int pending = 0, islands = 0, failed = 0, halv = 0;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    if (is_static[b] || isl[b] != b) continue;
+    ++islands;
+    if (lstate[2 * b] == 0) {
+      const double e0 = fx_value(E + 16L * b) - fx_value(E + 16L * b + 4);
+      const double et = fx_value(E + 16L * b + 8) - fx_value(E + 16L * b + 12);
+      if (et <= e0 + slack_rel * (fabs(e0) + 1.0)) {
+        lstate[2 * b] = 1;
+      } else if (lstate[2 * b + 1] >= ls_max) {
+        ++failed;
+      } else {
+        alpha[b] *= 0.5;
+        lstate[2 * b + 1] += 1;
+        ++pending;
+      }
+    }
+    halv = max(halv, lstate[2 * b + 1]);
+#pragma unroll
+    for (int k = 8; k < 16; ++k) E[16L * b + k] = 0ull;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    pending += __shfl_xor_sync(kFull, pending, o);
+    islands += __shfl_xor_sync(kFull, islands, o);
+    failed += __shfl_xor_sync(kFull, failed, o);
+    halv = max(halv, __shfl_xor_sync(kFull, halv, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (pending) atomicAdd(&st->ls_pending, pending);
+    if (islands) atomicAdd(&st->n_islands, islands);
+    if (failed) atomicAdd(&st->ls_failed, failed);
+    if (halv) atomicMax(&st->ls_halv_max, halv);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int grid_n(long n, int t, int cap) {
+  long g = (n + t - 1) / t;
+  return (int)std::max(1L, std::min(g, (long)cap));
+}
+
+// islands of the current body-pair list (and the lagged friction pairs)
+void launch_islands(Scene& s) {
+  counted(s, 3);
+  const int g = grid_n(s.nb, 256, sm_grid(s, 8));
+  k_isl_init<<<g, 256, 0, s.stream>>>(s.nb, s.uf.p, s.isl_toi.p, s.isl_E.p, s.isl_state.p);
+  k_isl_link<<<sm_grid(s, 4), 256, 0, s.stream>>>(s.st, s.P.p, s.fpairs.p, s.is_static.p, s.uf.p);
+  k_isl_label<<<g, 256, 0, s.stream>>>(s.nb, s.uf.p, s.isl.p);
+}
+
+void launch_island_energy(Scene& s, int which) {
+  counted(s);
+  k_isl_energy<<<sm_grid(s, 8), 256, 0, s.stream>>>(which, s.nb, s.is_static.p, s.isl.p, s.vbody.p, s.Eb.p, s.st,
+                                                      s.term.p, s.termv.p, s.Epair.p, energy_chunks(s), s.P.p,
+                                                      s.fterm.p, s.fric.p, s.isl_E.p, s.st);
+}
+
+void launch_island_start(Scene& s) {
+  counted(s);
+  k_isl_start<<<grid_n(s.nb, 256, sm_grid(s, 8)), 256, 0, s.stream>>>(s.nb, s.is_static.p, s.isl.p, s.isl_toi.p,
+                                                                       s.isl_alpha.p, s.isl_state.p);
+}
+
+void launch_island_trial(Scene& s) {
+  counted(s);
+  k_isl_trial<<<grid_n(12L * s.nb, 256, sm_grid(s, 8)), 256, 0, s.stream>>>(
+      s.nb, s.is_static.p, s.isl.p, s.isl_alpha.p, s.q.p, s.dq.p, s.qtrial.p);
+}
+
+void launch_island_accept(Scene& s) {
+  counted(s, 2);
+  cudaMemsetAsync(&s.st->ls_pending, 0, 4 * sizeof(int), s.stream);
+  k_isl_accept<<<grid_n(s.nb, 256, sm_grid(s, 4)), 256, 0, s.stream>>>(
+      s.nb, s.is_static.p, s.isl.p, s.prm.ls_slack_rel, s.prm.ls_max, s.isl_E.p, s.isl_alpha.p, s.isl_state.p, s.st);
+}
+
+}  // namespace abd

@@ -964,14 +964,13 @@ __global__ void k_gather(int nb, const uint8_t* is_static, const int* rowoff, co
   }
 }
 
-// block-Jacobi preconditioner: Cholesky factor of each dynamic diagonal
-// block, stored per body as 144 doubles with L below the diagonal
-// (row-major), 1 / L_ii on it and zeros above; the solver applies
-// (L L^T)^-1 by forward and back substitution (chol_apply).  A block that is
-// not positive definite falls back to its diagonal (flagged); static bodies
-// get a zero factor (their rows stay zero).
+// block-Jacobi preconditioner: the explicit inverse of each dynamic diagonal
+// block, from its Cholesky factor (L^-1 in place, then L^-T L^-1), stored per
+// body as a full symmetric 144-double block.  A block that is not positive
+// definite falls back to the inverse of its diagonal (flagged); static bodies
+// get a zero block (their rows stay zero).
 __global__ void __launch_bounds__(kBodyWarp) k_precond(int nb, const uint8_t* is_static, const double* D,
-                                                       double* Pinv, DevStatus* st) {
+                                                       double* Minv, DevStatus* st) {
   __shared__ double S[kBodyWarp][145];
   const int t = threadIdx.x;
   const long b0 = (long)blockIdx.x * kBodyWarp, b = b0 + t;
@@ -987,332 +986,39 @@ __global__ void __launch_bounds__(kBodyWarp) k_precond(int nb, const uint8_t* is
 #pragma unroll
     for (int j = 0; j <= i; ++j) L[tri(i, j)] = S[t][12 * i + j];
   const bool fallback = live && !chol12(L);
+  // L^-1 in place, column by column: the diagonal already holds 1 / L_jj;
+  // entry (i, j) needs L(i, k) of columns k > j (not yet overwritten) and the
+  // inverse's entries (k, j), k < i, of its own column (already written)
+#pragma unroll
+  for (int j = 0; j < 12; ++j)
+#pragma unroll
+    for (int i = j + 1; i < 12; ++i) {
+      double acc = L[tri(i, j)] * L[tri(j, j)];
+#pragma unroll
+      for (int k = j + 1; k < i; ++k) acc += L[tri(i, k)] * L[tri(k, j)];
+      L[tri(i, j)] = -acc * L[tri(i, i)];
+    }
+  // M^-1 = L^-T L^-1: entry (i, j), i >= j, = sum_{k >= i} Li(k, i) Li(k, j)
 #pragma unroll
   for (int i = 0; i < 12; ++i)
 #pragma unroll
-    for (int j = 0; j < 12; ++j) {
+    for (int j = 0; j <= i; ++j) {
       double v = 0.0;
-      if (live && !fallback && j <= i) v = L[tri(i, j)];
-      if (fallback && i == j) v = rsqrt(fabs(S[t][13 * i]));
+#pragma unroll
+      for (int k = i; k < 12; ++k) v += L[tri(k, i)] * L[tri(k, j)];
+      if (!live) v = 0.0;
+      if (fallback) {
+        const double d = S[t][13 * i];
+        v = i == j ? (d != 0.0 ? 1.0 / fabs(d) : 1.0) : 0.0;
+      }
       S[t][12 * i + j] = v;
+      S[t][12 * j + i] = v;
     }
   if (fallback) set_flag(st, ST_PCG_BREAKDOWN);
   __syncthreads();
   for (int k = t; k < kBodyWarp * 144; k += kBodyWarp) {
     const int bb = k / 144, e = k - 144 * bb;
-    if (b0 + bb < nb) Pinv[144 * (b0 + bb) + e] = S[bb][e];
-  }
-}
-
-// z = (L L^T)^-1 r for one body from its stored factor F (see k_precond)
-__device__ __forceinline__ void chol_apply(const double* __restrict__ F, const double* rb, double* z) {
-  double y[12];
-#pragma unroll
-  for (int i = 0; i < 12; ++i) {
-    double t = rb[i];
-#pragma unroll
-    for (int k = 0; k < i; ++k) t -= F[12 * i + k] * y[k];
-    y[i] = t * F[13 * i];
-  }
-#pragma unroll
-  for (int i = 11; i >= 0; --i) {
-    double t = y[i];
-#pragma unroll
-    for (int k = i + 1; k < 12; ++k) t -= F[12 * k + i] * z[k];
-    z[i] = t * F[13 * i];
-  }
-}
-
-// the Newton solve's start fused with the preconditioner: per body the
-// factor of its diagonal block (as k_precond, stored the same way), then
-// r = -g (dynamic rows), x = 0, z = (L L^T)^-1 r from the factor in registers
-// (the arithmetic of chol_apply), p = z, and the block's partials of r.z and
-// r.r (32 bodies per block) for k_pcg_start
-__global__ void __launch_bounds__(kBodyWarp) k_precond_start(int nb, const uint8_t* is_static, const double* D,
-                                                             double* Pinv, const double* g, double* x, double* r,
-                                                             double* z, double* pv, double* part, DevStatus* st) {
-  __shared__ double S[kBodyWarp][145];
-  const int t = threadIdx.x;
-  const long b0 = (long)blockIdx.x * kBodyWarp, b = b0 + t;
-  for (int k = t; k < kBodyWarp * 144; k += kBodyWarp) {
-    const int bb = k / 144, e = k - 144 * bb;
-    S[bb][e] = b0 + bb < nb ? D[144 * (b0 + bb) + e] : 0.0;
-  }
-  __syncthreads();
-  const bool live = b < nb && !is_static[b];
-  double L[78];
-#pragma unroll
-  for (int i = 0; i < 12; ++i)
-#pragma unroll
-    for (int j = 0; j <= i; ++j) L[tri(i, j)] = S[t][12 * i + j];
-  const bool fallback = live && !chol12(L);
-  // the factor into the staging rows, in the stored layout (as k_precond)
-#pragma unroll
-  for (int i = 0; i < 12; ++i)
-#pragma unroll
-    for (int j = 0; j < 12; ++j) {
-      double v = 0.0;
-      if (live && !fallback && j <= i) v = L[tri(i, j)];
-      if (fallback && i == j) v = rsqrt(fabs(S[t][13 * i]));
-      S[t][12 * i + j] = v;
-    }
-  if (fallback) set_flag(st, ST_PCG_BREAKDOWN);
-  double rz = 0.0, rr = 0.0;
-  if (b < nb) {
-    double rb[12], zb[12];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-      rb[i] = live ? -g[12 * b + i] : 0.0;
-      r[12 * b + i] = rb[i];
-      x[12 * b + i] = 0.0;
-      rr += rb[i] * rb[i];
-    }
-    chol_apply(S[t], rb, zb);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-      z[12 * b + i] = zb[i];
-      pv[12 * b + i] = zb[i];
-      rz += rb[i] * zb[i];
-    }
-  }
-  __syncthreads();
-  for (int k = t; k < kBodyWarp * 144; k += kBodyWarp) {
-    const int bb = k / 144, e = k - 144 * bb;
-    if (b0 + bb < nb) Pinv[144 * (b0 + bb) + e] = S[bb][e];
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    rz += __shfl_down_sync(kFull, rz, o);
-    rr += __shfl_down_sync(kFull, rr, o);
-  }
-  if (t == 0) {
-    part[2 * blockIdx.x] = rz;
-    part[2 * blockIdx.x + 1] = rr;
-  }
-}
-
-
-// ---------------------------------------------------------------------------
-// PCG on the block system: y = H v from the diagonal blocks, the stored
-// upper blocks of the body's rows and the transposed blocks of its incoming
-// pairs; scalars live in the status word so no host round trip is needed
-// ---------------------------------------------------------------------------
-constexpr int kPcgThreads = 192;  // 16 bodies x 12 rows
-
-__global__ void k_spmv(int nb, const uint8_t* is_static, const double* D, const int* rowoff, const int* in_off,
-                       const int* in_list, const int2* P, const double* pblk, const double* v, double* y,
-                       double* part, const DevStatus* cst) {
-  __shared__ double red[kPcgThreads];
-  if (cst->scal[6] != 0.0) return;
-  const int np = cst->np;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = t / 12, i = t % 12;
-  double acc = 0.0, pd = 0.0;
-  if (b < nb && !is_static[b]) {
-    const double* Di = D + 144 * b + 12 * i;
-    for (int j = 0; j < 12; ++j) acc += Di[j] * v[12 * b + j];
-    for (int p = rowoff[b]; p < min(rowoff[b + 1], np); ++p) {
-      int o = P[p].y;
-      if (is_static[o]) continue;
-      const double* Hr = pblk + (size_t)p * kBlkStride + 12 * i;
-      for (int j = 0; j < 12; ++j) acc += Hr[j] * v[12 * o + j];
-    }
-    for (int k = in_off[b]; k < in_off[b + 1]; ++k) {
-      int p = in_list[k];
-      int o = P[p].x;
-      if (is_static[o]) continue;
-      const double* Hc = pblk + (size_t)p * kBlkStride + i;
-      for (int j = 0; j < 12; ++j) acc += Hc[12 * j] * v[12 * o + j];
-    }
-    pd = acc * v[12 * b + i];
-  }
-  if (b < nb) y[t] = acc;
-  // block sum in fixed order: warp shuffles, then the warp partials in order
-  for (int o = 16; o > 0; o >>= 1) pd += __shfl_down_sync(kFull, pd, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = pd;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double sum = 0.0;
-    for (int w = 0; w < kPcgThreads / 32; ++w) sum += red[w];
-    red[0] = sum;
-  }
-  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
-}
-
-// p.Ap from the product's partials, by every block in the same fixed order
-// (that of a 256-thread block: thread t sums entries t, t + 256, ..., then a
-// tree), with 128 threads each standing for threads t and t + 128
-__device__ double pap_sum128(const double* v, int n, double* red) {
-  const int t = threadIdx.x;
-  double s0 = 0.0, s1 = 0.0;
-  for (int i = t; i < n; i += 256) s0 += v[i];
-  for (int i = t + 128; i < n; i += 256) s1 += v[i];
-  red[t] = s0 + s1;
-  __syncthreads();
-  for (int o = 64; o > 0; o >>= 1) {
-    if (t < o) red[t] += red[t + o];
-    __syncthreads();
-  }
-  const double r = red[0];
-  __syncthreads();
-  return r;
-}
-
-// alpha = r.z / p.Ap (every block forms it from the product's partials; block
-// 0 records it and the breakdown), x += alpha p; r -= alpha Ap;
-// z = (L L^T)^-1 r from the stored block factors; partial sums of r.z and r.r
-__global__ void k_pcg_update(int nb, const uint8_t* is_static, const double* Pinv, const double* pv,
-                             const double* Ap, const double* spart, int nspart, double* x, double* r, double* z,
-                             double* part, DevStatus* st) {
-  __shared__ double red[2][128];
-  if (st->scal[6] != 0.0) return;
-  const double pAp = pap_sum128(spart, nspart, red[0]);
-  const double rz_old = st->scal[0];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->scal[1] = pAp;
-    st->scal[8] = rz_old;
-    if (!(pAp > 0.0)) {
-      st->scal[6] = 2.0;  // breakdown
-      set_flag(st, ST_PCG_BREAKDOWN);
-    } else {
-      st->scal[4] = rz_old / pAp;
-    }
-  }
-  if (!(pAp > 0.0)) return;
-  const double alpha = rz_old / pAp;
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  double rz = 0.0, rr = 0.0;
-  if (b < nb && !is_static[b]) {
-    double rb[12];
-    for (int k = 0; k < 12; ++k) {
-      x[12 * b + k] += alpha * pv[12 * b + k];
-      rb[k] = r[12 * b + k] - alpha * Ap[12 * b + k];
-      r[12 * b + k] = rb[k];
-      rr += rb[k] * rb[k];
-    }
-    double zb[12];
-    chol_apply(Pinv + 144 * b, rb, zb);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-      z[12 * b + i] = zb[i];
-      rz += rb[i] * zb[i];
-    }
-  }
-  red[0][threadIdx.x] = rz;
-  red[1][threadIdx.x] = rr;
-  __syncthreads();
-  for (int o = 64; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + o];
-      red[1][threadIdx.x] += red[1][threadIdx.x + o];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = red[0][0];
-    part[2 * blockIdx.x + 1] = red[1][0];
-  }
-}
-
-// beta = r.z / (r.z)_previous and the convergence test from the update's
-// partials (every block, fixed order), then p = z + beta p on the block's
-// slice; block 0 records the scalars
-__global__ void k_pcg_beta_dir(const double* part, int n, double tol2, long nv, const double* z, double* pv,
-                               DevStatus* st) {
-  __shared__ double red[2][256];
-  if (st->scal[6] != 0.0) return;
-  double a = 0.0, c = 0.0;
-  for (int i = threadIdx.x; i < n; i += 256) {
-    a += part[2 * i];
-    c += part[2 * i + 1];
-  }
-  red[0][threadIdx.x] = a;
-  red[1][threadIdx.x] = c;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + o];
-      red[1][threadIdx.x] += red[1][threadIdx.x + o];
-    }
-    __syncthreads();
-  }
-  const double rz = red[0][0], rr = red[1][0];
-  const double beta = rz / st->scal[8];
-  const bool done = rr <= tol2 * st->scal[3];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->scal[5] = beta;
-    st->scal[0] = rz;
-    st->scal[2] = rr;
-    st->scal[7] += 1.0;
-    if (done) st->scal[6] = 1.0;
-  }
-  if (done) return;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nv; i += (long)gridDim.x * blockDim.x)
-    pv[i] = z[i] + beta * pv[i];
-}
-
-// r = rhs (dynamic rows), x = 0, z = (L L^T)^-1 r, p = z; partials of r.z and r.r
-__global__ void k_pcg_init(int nb, const uint8_t* is_static, const double* Pinv, const double* rhs, double* x,
-                           double* r, double* z, double* pv, double* part) {
-  __shared__ double red[2][128];
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  double rz = 0.0, rr = 0.0;
-  if (b < nb) {
-    const bool st = is_static[b];
-    double rb[12];
-    for (int k = 0; k < 12; ++k) {
-      rb[k] = st ? 0.0 : rhs[12 * b + k];
-      r[12 * b + k] = rb[k];
-      x[12 * b + k] = 0.0;
-      rr += rb[k] * rb[k];
-    }
-    double zb[12];
-    chol_apply(Pinv + 144 * b, rb, zb);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-      z[12 * b + i] = zb[i];
-      pv[12 * b + i] = zb[i];
-      rz += rb[i] * zb[i];
-    }
-  }
-  red[0][threadIdx.x] = rz;
-  red[1][threadIdx.x] = rr;
-  __syncthreads();
-  for (int o = 64; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + o];
-      red[1][threadIdx.x] += red[1][threadIdx.x + o];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = red[0][0];
-    part[2 * blockIdx.x + 1] = red[1][0];
-  }
-}
-
-__global__ void k_pcg_start(const double* part, int n, DevStatus* st) {
-  __shared__ double red[2][256];
-  double a = 0.0, c = 0.0;
-  for (int i = threadIdx.x; i < n; i += 256) {
-    a += part[2 * i];
-    c += part[2 * i + 1];
-  }
-  red[0][threadIdx.x] = a;
-  red[1][threadIdx.x] = c;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + o];
-      red[1][threadIdx.x] += red[1][threadIdx.x + o];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    st->scal[0] = red[0][0];
-    st->scal[2] = red[1][0];
-    st->scal[3] = red[1][0];
-    st->scal[7] = 0.0;
-    st->scal[6] = red[1][0] == 0.0 ? 1.0 : 0.0;
+    if (b0 + bb < nb) Minv[144 * (b0 + bb) + e] = S[bb][e];
   }
 }
 
@@ -1546,17 +1252,15 @@ void launch_gather(Scene& s) {
                                                           s.pblk.p, s.Db.p, s.gb.p, s.D.p, s.g.p, s.st);
 }
 
-void launch_precond_start(Scene& s, double* xout) {
-  const int nbk = blocks(s.nb, kBodyWarp);
-  counted(s, 2);
-  k_precond_start<<<nbk, kBodyWarp, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.Pinv.p, s.g.p, xout, s.r.p, s.z.p,
-                                                   s.pv.p, s.part.p, s.st);
-  k_pcg_start<<<1, 256, 0, s.stream>>>(s.part.p, nbk, s.st);
-}
-
 void launch_precond(Scene& s) {
   counted(s);
   k_precond<<<blocks(s.nb, kBodyWarp), kBodyWarp, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.Pinv.p, s.st);
+}
+
+// the preconditioner, then the start of the Newton solve H dx = -g
+void launch_precond_start(Scene& s, double* xout) {
+  launch_precond(s);
+  launch_pcg_init(s, s.g.p, -1.0, xout);
 }
 
 // energies of the last evaluation into st->energy: bodies, barrier terms or
@@ -1571,72 +1275,6 @@ void launch_energy_total(Scene& s, bool from_terms) {
     k_energies<<<grid, 256, 0, s.stream>>>(s.Eb.p, s.nb, s.Epair.p, 1, &s.st->np, energy_chunks(s), s.fterm.p,
                                            &s.st->nfr, s.red.p);
   k_energy_sum<<<1, 128, 0, s.stream>>>(s.red.p, s.st, from_terms ? 1 : 0);
-}
-
-// PCG in three pieces so that its first iterations can join a captured launch
-// sequence: pcg_begin (r = rhs, x = 0, first direction), pcg_iterate (n
-// iterations, each a no-op once converged), pcg_finish (further chunks with a
-// status read-back after each, until converged or the cap)
-void pcg_begin(Scene& s, const double* rhs, double* xout) {
-  const int nbk = blocks(s.nb, 128);
-  counted(s, 2);
-  k_pcg_init<<<nbk, 128, 0, s.stream>>>(s.nb, s.is_static.p, s.Pinv.p, rhs, xout, s.r.p, s.z.p, s.pv.p, s.part.p);
-  k_pcg_start<<<1, 256, 0, s.stream>>>(s.part.p, nbk, s.st);
-}
-
-void pcg_iterate(Scene& s, double* xout, int n, double rel_tol) {
-  const int nbk = blocks(s.nb, 128);
-  const int sblocks = blocks(12L * s.nb, kPcgThreads);
-  const double tol2 = rel_tol * rel_tol;
-  // algorithmic bytes of one product: every stored block once (diagonal and
-  // upper off-diagonal, 144 doubles each), the vector read once and the
-  // product written once, the pair list once
-  const double spmv_bytes = 8.0 * 144.0 * (s.nb + (double)s.last_np) + 2.0 * 8.0 * 12.0 * s.nb + 8.0 * s.last_np;
-  for (int k = 0; k < n; ++k) {
-    counted(s, 3);
-    {
-      ProfScope pv(s, PF_SPMV, spmv_bytes);
-      k_spmv<<<sblocks, kPcgThreads, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.rowoff.p, s.in_off.p, s.in_list.p,
-                                                    s.P.p, s.pblk.p, s.pv.p, s.Ap.p, s.part.p, s.st);
-    }
-    // the product's partials and the update's live in two halves of `part`
-    k_pcg_update<<<nbk, 128, 0, s.stream>>>(s.nb, s.is_static.p, s.Pinv.p, s.pv.p, s.Ap.p, s.part.p, sblocks, xout,
-                                            s.r.p, s.z.p, s.part.p + sblocks, s.st);
-    k_pcg_beta_dir<<<blocks(12L * s.nb, 256), 256, 0, s.stream>>>(s.part.p + sblocks, nbk, tol2, 12L * s.nb, s.z.p,
-                                                                   s.pv.p, s.st);
-  }
-}
-
-int pcg_finish(Scene& s, double* xout, int done_iters, int max_iter, double rel_tol, double* rel_res) {
-  int it = done_iters;
-  int chunk = std::max(2, 2 * done_iters);
-  while (s.st_host->scal[6] == 0.0 && it < max_iter) {
-    pcg_iterate(s, xout, std::min(chunk, 16), rel_tol);
-    it += std::min(chunk, 16);
-    cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
-    cudaStreamSynchronize(s.stream);
-    chunk = 2 * chunk;
-  }
-  double rr = s.st_host->scal[2], rr0 = s.st_host->scal[3];
-  *rel_res = rr0 > 0 ? sqrt(rr / rr0) : 0.0;
-  int iters = (int)s.st_host->scal[7];
-  if (s.st_host->scal[6] == 2.0) return -2;
-  if (s.st_host->scal[6] == 0.0) return -1;
-  return iters;
-}
-
-int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res) {
-  if (s.dense_n) {
-    launch_dense_solve(s, rhs, xout);
-    cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
-    cudaStreamSynchronize(s.stream);
-    return pcg_finish(s, xout, 0, max_iter, rel_tol, rel_res);
-  }
-  pcg_begin(s, rhs, xout);
-  pcg_iterate(s, xout, 2, rel_tol);
-  cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
-  cudaStreamSynchronize(s.stream);
-  return pcg_finish(s, xout, 2, max_iter, rel_tol, rel_res);
 }
 
 __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }

@@ -11,7 +11,10 @@
 // until the process exits.
 #include <string.h>
 
+#include <cuda.h>
+
 #include <mutex>
+#include <vector>
 
 #include "../../include/abd.h"
 #include "geom.cuh"
@@ -65,22 +68,82 @@ __global__ void k_toi_min(long n, double* scratch) {
   if (threadIdx.x == 0) scratch[kResultSlot] = red[0];
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current.  In host code the array's name only stands in for the
-// symbol; kernels must be given this address.
+// Device address of the scratch array.  In host code the array's name only
+// stands in for the symbol; kernels must be given the address that
+// cudaGetSymbolAddress returns for the CUDA context that launches them.  That
+// address belongs to one context: after cudaDeviceReset, or in a driver-API
+// context other than the device's primary one, the module is loaded again at
+// another address.  The cache is therefore keyed on the device and on the
+// context's unique id (cuCtxGetId, reached through the runtime's driver
+// entry-point query, so the library does not link libcuda directly).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+struct ScratchEntry {
+  int dev;
+  unsigned long long ctx_id;
+  double* addr;
+};
+
 std::mutex g_mu;
-double* g_addr[256] = {};
+std::vector<ScratchEntry> g_cache;
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_entry_points_tried = false;
+
+// id of the calling thread's current context; false if there is none yet
+// (the runtime creates the primary context on its first device call) or the
+// driver entry points are unavailable.  Called with g_mu held.
+bool current_context_id(unsigned long long* id) {
+  if (!g_entry_points_tried) {
+    g_entry_points_tried = true;
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess && f1 && f2) {
+      g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+      g_ctx_id = reinterpret_cast<CtxGetIdFn>(f2);
+    } else {
+      cudaGetLastError();  // a failed query leaves nothing pending for the caller
+    }
+  }
+  if (!g_ctx_current || !g_ctx_id) return false;
+  CUcontext c = nullptr;
+  if (g_ctx_current(&c) != CUDA_SUCCESS || !c) return false;
+  return g_ctx_id(c, id) == CUDA_SUCCESS;
+}
 
 abd_status scratch_address(double** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return ABD_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ABD_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_ccd_scratch) != cudaSuccess || !p) return ABD_ERR_CUDA;
-    g_addr[dev] = static_cast<double*>(p);
+  unsigned long long id = 0;
+  bool have_id = current_context_id(&id);
+  if (have_id)
+    for (const ScratchEntry& e : g_cache)
+      if (e.dev == dev && e.ctx_id == id) {
+        *out = e.addr;
+        return ABD_OK;
+      }
+  // set-up for this device and context: look the address up with the
+  // device current (the lookup also creates the primary context if needed)
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_ccd_scratch) != cudaSuccess || !p) return ABD_ERR_CUDA;
+  if (!have_id) have_id = current_context_id(&id);
+  if (have_id) {
+    bool replaced = false;
+    for (ScratchEntry& e : g_cache)
+      if (e.dev == dev) {  // a context of this device that is gone or not current: keep one entry per device
+        e.ctx_id = id;
+        e.addr = static_cast<double*>(p);
+        replaced = true;
+      }
+    if (!replaced) g_cache.push_back(ScratchEntry{dev, id, static_cast<double*>(p)});
   }
-  *out = g_addr[dev];
+  // without a context id nothing is cached: every call looks the address up
+  *out = static_cast<double*>(p);
   return ABD_OK;
 }
 
@@ -104,12 +167,23 @@ extern "C" ABD_API abd_status abd_ccd_toi_pairs_noalloc(const double* x_dev, con
   if (cudaMemsetAsync(scratch + kStatusSlot, 0, sizeof(unsigned long long), st) != cudaSuccess) return ABD_ERR_CUDA;
   long blocks = (npairs + 127) / 128;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  k_toi_pairs<<<(int)blocks, 128, 0, st>>>(x_dev, dx_dev, nv, verts_dev, kind_dev, npairs, ccd_s, ccd_max, scratch);
-  k_toi_min<<<1, 1024, 0, st>>>(npairs, scratch);
+  // each launch's own error is returned by cudaLaunchKernel; the caller's
+  // unrelated pending errors are neither reported nor consumed here
+  {
+    void* args[] = {(void*)&x_dev, (void*)&dx_dev, (void*)&nv, (void*)&verts_dev, (void*)&kind_dev,
+                    (void*)&npairs, (void*)&ccd_s, (void*)&ccd_max, (void*)&scratch};
+    if (cudaLaunchKernel((const void*)k_toi_pairs, dim3((unsigned)blocks), dim3(128), args, 0, st) != cudaSuccess)
+      return ABD_ERR_CUDA;
+  }
+  {
+    void* args[] = {(void*)&npairs, (void*)&scratch};
+    if (cudaLaunchKernel((const void*)k_toi_min, dim3(1), dim3(1024), args, 0, st) != cudaSuccess)
+      return ABD_ERR_CUDA;
+  }
   double res[2];
   if (cudaMemcpyAsync(res, scratch + kResultSlot, sizeof(res), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return ABD_ERR_CUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return ABD_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return ABD_ERR_CUDA;
   unsigned long long status;
   memcpy(&status, &res[1], sizeof(status));
   if (status & (kBadIndex | kBadKind)) return ABD_ERR_INVALID_ARG;
