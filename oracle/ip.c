@@ -365,9 +365,43 @@ double orc_ortho(const double q[12], double kappa, double vol, double g[12], dou
 }
 
 /* Per-body IP term E_b = 1/2 (q-qt)^T M (q-qt) + dt^2 V.  Hessian reading:
- * the whole block M + dt^2 Hess V, used as it is when a Cholesky
- * factorisation succeeds (the block is positive definite) and eigen-clamped
- * to the PSD cone as one 12x12 block only when it fails. */
+ * the block M + dt^2 Hess V, used as it is when a Cholesky factorisation
+ * succeeds (the block is positive definite).  When it fails, Hess V is
+ * replaced by a positive semidefinite surrogate: V = kappa nu |C|_F^2 with
+ * C = A A^T - I is a sum of squares, so its Hessian is the Gauss-Newton part
+ * (positive semidefinite) plus the residual-curvature part 4 kappa nu C (x) I
+ * (over the rows a_k of A); the surrogate keeps the first and clamps the
+ * eigenvalues of the 3x3 C in the second, giving
+ *   d2/da_k da_l = 4 kappa nu [C+_kl I + delta_kl A^T A + a_l a_k^T],
+ * and the block M + dt^2 (surrogate) is positive definite because M is.  It
+ * equals the true Hessian whenever C is positive semidefinite. */
+static void ortho_hess_psd(const double q[12], double kappa, double vol, double H[144]) {
+  double A[3][3], C[9], w[3], V[9], Cp[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int c = 0; c < 3; ++c) A[i][c] = q[3 + 3 * i + c];
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l)
+      C[3 * k + l] = A[k][0] * A[l][0] + A[k][1] * A[l][1] + A[k][2] * A[l][2] - (k == l ? 1.0 : 0.0);
+  orc_sym_eig(3, C, w, V);
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      double t = 0.0;
+      for (int c = 0; c < 3; ++c)
+        if (w[c] > 0.0) t += V[3 * k + c] * w[c] * V[3 * l + c];
+      Cp[k][l] = t;
+    }
+  const double s4 = 4.0 * kappa * vol;
+  for (int i = 0; i < 144; ++i) H[i] = 0.0;
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l)
+      for (int ck = 0; ck < 3; ++ck)
+        for (int cl = 0; cl < 3; ++cl) {
+          double h = A[l][ck] * A[k][cl];            /* a_l a_k^T */
+          if (ck == cl) h += Cp[k][l];               /* C+_kl I */
+          if (k == l) h += A[0][ck] * A[0][cl] + A[1][ck] * A[1][cl] + A[2][ck] * A[2][cl];  /* A^T A */
+          H[12 * (3 + 3 * k + ck) + 3 + 3 * l + cl] = s4 * h;
+        }
+}
 static double body_terms(orc_ctx* c, int b, const double* q, double* g, double* H, int project, double* Eo) {
   const double* M = c->M + 144 * b;
   const double* qt = c->qtilde + 12 * b;
@@ -386,13 +420,17 @@ static double body_terms(orc_ctx* c, int b, const double* q, double* g, double* 
   if (g)
     for (int k = 0; k < 12; ++k) g[k] = Mdq[k] + dt2 * gv[k];
   if (H) {
-    /* the whole body block M + dt^2 hess V; projected to the PSD cone only
-     * when it is not positive definite (Cholesky fails) */
+    /* the body block M + dt^2 hess V; when it is not positive definite
+     * (Cholesky fails), M + dt^2 (the surrogate above) */
     for (int k = 0; k < 144; ++k) H[k] = M[k] + dt2 * Hv[k];
     if (project) {
       double L[144];
       memcpy(L, H, sizeof(L));
-      if (chol(12, L)) orc_project_psd(12, H);
+      if (chol(12, L)) {
+        double P[144];
+        ortho_hess_psd(q, c->kappa_body[b], c->vol[b], P);
+        for (int k = 0; k < 144; ++k) H[k] = M[k] + dt2 * P[k];
+      }
     }
   }
   *Eo = dt2 * V;

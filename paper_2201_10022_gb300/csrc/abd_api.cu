@@ -76,6 +76,7 @@ void size_pair_buffers(Scene& s, size_t pcap) {
   grow(s, s.fpairs, pcap);
   grow(s, s.fpoff, pcap + 1);
   grow(s, s.flagbuf, pcap);
+  if (s.prm.precision == 1) grow(s, s.H32, pcap * 144);
   grow(s, s.posbuf, pcap + 1);
   grow(s, s.Epair, pcap * (size_t)energy_chunks(s));
   grow(s, s.cand, pcap * (size_t)s.maxc);
@@ -169,6 +170,103 @@ abd_status check_cuda(Scene& s) {
     return ABD_ERR_CUDA;
   }
   return ABD_OK;
+}
+
+// Preconditioner clusters from the island labels in s.isl_host (and the
+// body pairs, read here): the dynamic bodies of each island in breadth-first
+// order over the island's dynamic body pairs (from its smallest body id,
+// neighbours in pair order), cut into consecutive runs of at most
+// kClusterMax bodies, so that a cluster is a compact piece of the contact
+// graph (a stack of bodies rather than a row of neighbours).  Deterministic;
+// uploaded with the cluster count; the factor pool grows when needed.
+void build_clusters_host(Scene& s) {
+  const int nb = s.nb;
+  int* perm = s.clu_host;
+  int* off = perm + nb;
+  int* cof = off + nb + 1;
+  int* loc = cof + nb;
+  int* ncl = loc + nb;
+  long long* foff = reinterpret_cast<long long*>(s.clu_host + 4 * nb + 2);
+  const long np = std::max(0, s.st_host->np);
+  s.pairs_host.resize(np);
+  if (np) cudaMemcpy(s.pairs_host.data(), s.P.p, sizeof(int2) * np, cudaMemcpyDeviceToHost);
+  // adjacency of the dynamic bodies (pair order)
+  std::vector<int> deg(nb + 1, 0), adj;
+  for (const int2& e : s.pairs_host)
+    if (!s.is_static_host[e.x] && !s.is_static_host[e.y]) {
+      deg[e.x + 1]++;
+      deg[e.y + 1]++;
+    }
+  for (int b = 0; b < nb; ++b) deg[b + 1] += deg[b];
+  adj.resize(deg[nb]);
+  {
+    std::vector<int> fill(deg.begin(), deg.end() - 1);
+    for (const int2& e : s.pairs_host)
+      if (!s.is_static_host[e.x] && !s.is_static_host[e.y]) {
+        adj[fill[e.x]++] = e.y;
+        adj[fill[e.y]++] = e.x;
+      }
+  }
+  // breadth-first order of each island from its label (its smallest body)
+  std::vector<char> seen(nb, 0);
+  int nd = 0;
+  for (int b = 0; b < nb; ++b) {
+    cof[b] = -1;
+    loc[b] = 0;
+  }
+  std::vector<int> island_start;
+  for (int b = 0; b < nb; ++b) {
+    if (s.is_static_host[b] || s.isl_host[b] != b) continue;  // b is an island's label
+    island_start.push_back(nd);
+    int head = nd;
+    perm[nd++] = b;
+    seen[b] = 1;
+    while (head < nd) {
+      const int u = perm[head++];
+      for (int k = deg[u]; k < deg[u + 1]; ++k)
+        if (!seen[adj[k]]) {
+          seen[adj[k]] = 1;
+          perm[nd++] = adj[k];
+        }
+    }
+  }
+  island_start.push_back(nd);
+  int nc = 0;
+  long long fo = 0;
+  for (size_t k = 0; k + 1 < island_start.size(); ++k) {
+    for (int c0 = island_start[k]; c0 < island_start[k + 1]; c0 += kClusterMax) {
+      const int n = std::min(kClusterMax, island_start[k + 1] - c0);
+      off[nc] = c0;
+      foff[nc] = fo;
+      if (n >= 2) fo += (long long)(12 * n) * (12 * n + 1) / 2;
+      for (int i = 0; i < n; ++i) {
+        cof[perm[c0 + i]] = nc;
+        loc[perm[c0 + i]] = i;
+      }
+      ++nc;
+    }
+  }
+  off[nc] = nd;
+  foff[nc] = fo;
+  *ncl = nc;
+  s.nclu = nc;
+  if ((size_t)fo > s.c_fac.cap) grow(s, s.c_fac, std::max<size_t>((size_t)fo, 2 * s.c_fac.cap));
+  cudaMemcpyAsync(s.c_perm.p, perm, sizeof(int) * nb, cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.c_off.p, off, sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.c_of.p, cof, sizeof(int) * nb, cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.c_loc.p, loc, sizeof(int) * nb, cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.c_foff.p, foff, sizeof(long long) * (nc + 1), cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(&s.st->n_clusters, ncl, sizeof(int), cudaMemcpyHostToDevice, s.stream);
+}
+
+// islands of the current body-pair list, their labels to the host, and the
+// preconditioner clusters built from them (synchronises the stream)
+void prepare_clusters(Scene& s) {
+  launch_islands(s);
+  cudaMemcpyAsync(s.isl_host, s.isl.p, sizeof(int) * s.nb, cudaMemcpyDeviceToHost, s.stream);
+  cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
+  cudaStreamSynchronize(s.stream);
+  build_clusters_host(s);
 }
 
 // ---- pipeline stages --------------------------------------------------------
@@ -323,6 +421,7 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
   loc.toi_min = 1.0;
   launch_transform(s, s.q.p, s.x.p);
   broad_and_enumerate(s, false, false);
+  prepare_clusters(s);  // the clusters of the first system
   read_status(s);
   s.cand_last = (long)s.st_host->n_cand;
   s.last_np = s.st_host->np;
@@ -331,6 +430,7 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
   // passes the convergence test, the test is repeated with the FP64-refined
   // projection at the same iterate, so both modes stop on the same criterion
   bool hp = s.prm.precision == 0;
+  s.pcg_mixed = s.prm.precision == 1;  // FP32 blocks and inner PCG, FP64 refinement
   for (int it = 0; it < s.prm.newton_max; ++it) {
     s.fp32_proj = !hp;
     // system at q and the Newton direction H dq = -g, enqueued as one
@@ -361,7 +461,7 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
     loc.active_evaluated += s.st_host->nact;
     loc.n_candidates = cand_total(s);
     if (its == -2) {
-      s.err = "PCG breakdown";
+      s.err = s.st_host->scal[6] == 3.0 ? "PCG grid barrier timed out" : "PCG breakdown (p.Hp <= 0)";
       return ABD_ERR_PCG_BREAKDOWN;
     }
     loc.pcg_iters += its == -1 ? s.prm.pcg_max : std::max(its, 0);
@@ -386,9 +486,13 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
       eval_energy(s, s.qtrial.p);
       launch_island_energy(s, 1);
       launch_island_accept(s);
+      cudaMemcpyAsync(s.isl_host, s.isl.p, sizeof(int) * s.nb, cudaMemcpyDeviceToHost, s.stream);
       cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
     });
     cudaStreamSynchronize(s.stream);
+    // the islands of this swept pair list are those of the next system:
+    // its preconditioner clusters
+    build_clusters_host(s);
     double step = bits_to_double(s.st_host->step_bits);
     loc.last_step = step;
     if (!(step == step)) {
@@ -589,6 +693,10 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
       grow(s, *b, 12L * nb);
     grow(s, s.pcg_bar, 4);
     grow(s, s.uf, nb);
+    for (Buf<int>* b : {&s.c_perm, &s.c_of, &s.c_loc, &s.c_ok}) grow(s, *b, nb);
+    grow(s, s.c_off, nb + 1L);
+    grow(s, s.c_foff, nb + 1L);
+    grow(s, s.c_fac, 576L * nb);
     grow(s, s.isl, nb);
     grow(s, s.isl_state, 2L * nb);
     grow(s, s.isl_toi, nb);
@@ -596,8 +704,13 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
     grow(s, s.isl_alpha, nb);
     grow(s, s.Eb, 2L * nb);
     for (Buf<double>* b : {&s.Db, &s.D, &s.Pinv}) grow(s, *b, 144L * nb);
-    grow(s, s.hfix, nb);
-    grow(s, s.part, 3L * pcg_chunks(nb) + 1024);
+    grow(s, s.part, 4L * nb + 1024);
+    if (prm->precision == 1) {
+      grow(s, s.D32, 144L * nb);
+      grow(s, s.Minv32, 144L * nb);
+      grow(s, s.vf, 72L * nb);
+      grow(s, s.rhs64, 12L * nb);
+    }
     for (Buf<double4>* b : {&s.x, &s.dx, &s.x1, &s.xt}) grow(s, *b, nv);
     grow(s, s.bbox, 6L * nb);
     grow(s, s.bbox32, 6L * nb);
@@ -626,6 +739,9 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
     size_term_buffers(s, std::max<size_t>(4096, 16L * nb));
     if (cudaMalloc(&s.st, sizeof(DevStatus)) != cudaSuccess) throw OomError{};
     if (cudaMallocHost(&s.st_host, sizeof(DevStatus)) != cudaSuccess) throw OomError{};
+    if (cudaMallocHost(&s.isl_host, sizeof(int) * nb) != cudaSuccess) throw OomError{};
+    if (cudaMallocHost(&s.clu_host, sizeof(int) * (4L * nb + 2) + sizeof(long long) * (nb + 1L)) != cudaSuccess)
+      throw OomError{};
   } catch (OomError&) {
     abd_destroy(S);
     return ABD_ERR_OOM;
@@ -659,6 +775,7 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
   cudaMemcpyAsync(s.tbeg.p, tbeg.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, s.stream);
   cudaMemcpyAsync(s.ebeg.p, ebeg.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, s.stream);
   cudaMemcpyAsync(s.is_static.p, d->is_static, nb, cudaMemcpyHostToDevice, s.stream);
+  s.is_static_host.assign(d->is_static, d->is_static + nb);
   cudaMemcpyAsync(s.kappa_b.p, d->kappa_body, sizeof(double) * nb, cudaMemcpyHostToDevice, s.stream);
   cudaMemcpyAsync(s.density.p, d->density, sizeof(double) * nb, cudaMemcpyHostToDevice, s.stream);
   DevStatus z;
@@ -729,7 +846,6 @@ void abd_destroy(abd_scene* S) {
   release(s, s.xbar);
   release(s, s.l2e);
   release(s, s.scan_part);
-  release(s, s.hfix);
   release(s, s.amask);
   release(s, s.bbox32);
   release(s, s.vbody);
@@ -744,7 +860,12 @@ void abd_destroy(abd_scene* S) {
   release(s, s.kappa_b);
   release(s, s.density);
   release(s, s.pcg_bar);
+  for (Buf<float>* b : {&s.D32, &s.Minv32, &s.H32, &s.vf}) release(s, *b);
+  release(s, s.rhs64);
   release(s, s.uf);
+  for (Buf<int>* b : {&s.c_perm, &s.c_of, &s.c_loc, &s.c_ok, &s.c_off}) release(s, *b);
+  release(s, s.c_foff);
+  release(s, s.c_fac);
   release(s, s.isl);
   release(s, s.isl_state);
   release(s, s.isl_toi);
@@ -773,6 +894,8 @@ void abd_destroy(abd_scene* S) {
   for (cudaEvent_t e : s.prof.pool) cudaEventDestroy(e);
   if (s.st) cudaFree(s.st);
   if (s.st_host) cudaFreeHost(s.st_host);
+  if (s.isl_host) cudaFreeHost(s.isl_host);
+  if (s.clu_host) cudaFreeHost(s.clu_host);
   delete S;
 }
 
@@ -813,6 +936,7 @@ abd_status abd_energy_grad_hess(abd_scene* S, const double* q_dev, double* E_hos
   abd_status r = with_capacity(s, [&]() {
     launch_transform(s, q_dev, s.x.p);
     broad_and_enumerate(s, false, false);
+    prepare_clusters(s);
     s.fp32_proj = s.prm.precision == 1;
     eval_system(s, q_dev, 1);
     return ABD_OK;
@@ -949,6 +1073,7 @@ abd_status abd_solve(abd_scene* S, const double* rhs_dev, double* dq_dev, abd_so
     return ABD_ERR_INVALID_ARG;
   }
   double rel;
+  s.pcg_mixed = s.prm.precision == 1;
   int its = run_pcg(s, rhs_dev, dq_dev, s.prm.pcg_max, s.prm.pcg_rel_tol, &rel);
   if (stats) {
     stats->iterations = its < 0 ? s.prm.pcg_max : its;
@@ -1178,6 +1303,7 @@ abd_status abd_adjoint_step(abd_scene* S, const double* q_t, const double* qdot_
   abd_status r = with_capacity(s, [&]() {
     launch_transform(s, q_next, s.x.p);
     broad_and_enumerate(s, false, false);
+    prepare_clusters(s);
     s.fp32_proj = false;
     eval_system(s, q_next, 0);
     return ABD_OK;
@@ -1188,6 +1314,7 @@ abd_status abd_adjoint_step(abd_scene* S, const double* q_t, const double* qdot_
   s.last_np = s.st_host->np;
   launch_adjoint_rhs(s, gq, gqdot, s.qsave.p);
   double rel;
+  s.pcg_mixed = false;  // the adjoint's solves stay FP64
   const int its = run_pcg(s, s.qsave.p, s.dq.p, s.prm.pcg_max, rel_tol, &rel);
   launch_adjoint_out(s, q_next, s.dq.p, gq, gqdot, gkappa);
   cudaStreamSynchronize(s.stream);

@@ -50,7 +50,7 @@ struct DevStatus {
   double energy[8];             // 0 total, 1 inertia, 2 ortho, 3 barrier, 4 friction
   int bar_cnt[4];               // active terms by working dimension 3, 6, 9 (classification pass)
   unsigned long long jac[3];    // Jacobi sweeps FP32, FP64, terms at the FP64 sweep cap (cumulative)
-  int bh_fix;                   // body blocks to project (not positive definite)
+  int bh_fix;                   // body blocks that took the orthogonality surrogate (not positive definite)
   int pad3;
   // culling of the enumeration (cumulative): primitive pairs of the body
   // pairs, pairs left after restricting each side to the other body's box,
@@ -60,6 +60,8 @@ struct DevStatus {
   // last acceptance pass, islands, islands past the halving cap, the largest
   // halving count of any island
   int ls_pending, n_islands, ls_failed, ls_halv_max;
+  int n_clusters;               // preconditioner clusters of the current body-pair list
+  int clu_fail;                 // clusters whose Cholesky factorisation failed (block-Jacobi used)
 };
 
 // ---- small device helpers shared by the kernel files -----------------------
@@ -218,7 +220,6 @@ struct Scene {
   // assembly
   Buf<double> pblk;    // np * (3*144 + 24 + 2): Hab, Dlo, Dhi, glo, ghi, Eb, Ef
   Buf<double> Db, gb, Eb;   // body terms
-  Buf<int> hfix;            // bodies whose block failed Cholesky (projected)
   Buf<double> D, g, Pinv;   // assembled diagonal, gradient, preconditioner
   Buf<double> red;     // reduction scratch
   int dense_n = 0;           // order of the dense system (0: PCG)
@@ -238,6 +239,27 @@ struct Scene {
   // chunk partial sums, the solve kernel's grid-barrier words
   Buf<double> r, z, pv, pv2, Ap, part;
   Buf<unsigned> pcg_bar;
+  // mixed-precision solve (precision = 1): FP32 copies of the diagonal, the
+  // inverse diagonal and the upper pair blocks, the FP64 right-hand side, and
+  // six FP32 vectors (r, z, two directions, H p, the inner solution)
+  bool pcg_mixed = false;
+  Buf<float> D32, Minv32, H32, vf;
+  Buf<double> rhs64;
+  // preconditioner clusters (k_pcg.cu): the dynamic bodies of every contact
+  // island in body order, cut into runs of at most kClusterMax bodies; per
+  // cluster its members (c_off into c_perm), per body its cluster and local
+  // index, per cluster the offset of its dense Cholesky factor in c_fac and a
+  // flag (factorisation succeeded); host staging of the island labels and of
+  // the cluster arrays
+  int nclu = 0;
+  Buf<int> c_perm, c_off, c_of, c_loc, c_ok;
+  Buf<long long> c_foff;
+  Buf<double> c_fac;
+  int* isl_host = nullptr;
+  int* clu_host = nullptr;       // c_perm | c_off | c_of | c_loc | count, then c_foff (long long)
+  std::vector<int2> pairs_host;  // the body pairs (cluster adjacency)
+  std::vector<uint8_t> is_static_host;
+  bool cluster_attr_set = false;
   int num_sms = 152;          // multiprocessors of the scene's device
   int pcg_blocks_per_sm = 0;  // co-resident blocks of the solve kernel (0: not yet queried)
 
@@ -344,7 +366,10 @@ void launch_pcg_solve(Scene& s, double* xout, int max_iter, double rel_tol);
 int pcg_result(Scene& s, double* rel_res);
 void pcg_account(Scene& s, int its);
 int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res);
-int pcg_chunks(int nb);
+void launch_pcg_fp32_blocks(Scene& s);  // mixed precision: FP32 copies of the blocks
+// factors of the preconditioner clusters (after the assembly)
+void launch_cluster_factor(Scene& s);
+constexpr int kClusterMax = 16;         // bodies per preconditioner cluster
 double pcg_iter_bytes(const Scene& s, long np);
 double pcg_iter_flops(const Scene& s, long np);
 // dense direct solve (small scenes): order of the padded matrix, 0 if off

@@ -3,20 +3,36 @@
 // LLT of Sec. 5 replaced by an iterative solve on the device).
 //
 // H is symmetric block-sparse with 12x12 blocks: the diagonal blocks D_b,
-// and for every body pair (a, b), a < b, the upper block H_ab stored once in
-// the pair's assembly record (rows = DOFs of a).  Row b of the product is
-//   y_b = D_b v_b + sum_{(b,c) upper} H_bc v_c + sum_{(c,b) incoming} H_cb^T v_b'
+// and for every body pair (a, b), a < b, the upper block H_ab stored once
+// (rows = DOFs of a).  Row b of the product is
+//   y_b = D_b v_b + sum_{(b,c) upper} H_bc v_c + sum_{(c,b) incoming} H_cb^T v_c
 // The preconditioner is the explicit inverse of each diagonal block.
 //
 // One persistent cooperative kernel runs the whole solve: every iteration is
 // two phases separated by a grid barrier, and every block derives the
-// scalars (alpha, beta, the convergence test) from the same chunk partial
-// sums in the same order, so no host round trip is needed and the result is
-// bit-identical run to run.  Partial sums are formed per chunk of kChunk
-// bodies in body order (not per block), so the arithmetic does not depend on
-// the grid size.  The grid barrier's wait is bounded: a block that waits
-// longer than kBarrierTimeout cycles raises an abort word that releases
-// every other block, and the solve reports the failure in the status word.
+// scalars (alpha, beta, the convergence test) from the same per-body partial
+// sums in the same order, so no host round trip is needed, the result is
+// bit-identical run to run and independent of the grid size.  The grid
+// barrier's wait is bounded: a block that waits longer than kBarrierTimeout
+// cycles raises an abort word that releases every other block, and the solve
+// reports the failure in the status word.
+//
+// Two precisions (the paper states none for its solve):
+//  * FP64: blocks, vectors and products in FP64;
+//  * mixed: the blocks and the preconditioner stored in FP32 and the inner
+//    iterations in FP32 (FP32 blocks and vectors, FP64 dot products), inside
+//    an FP64 iterative refinement: x (FP64) += the inner solution of
+//    H32 d = r, then r = rhs - H32 x recomputed in FP64 arithmetic, until the
+//    FP64 residual meets the tolerance.  The gradient, and so the Newton
+//    minimiser, stay FP64; only the direction's solve uses the FP32 blocks.
+//
+// Layout of a block product: a warp takes one body row; lanes 0..11 and
+// 16..27 are two groups of 12, one row DOF per lane, taking the row's blocks
+// alternately.  Lane l of a group forms y_l = sum_i B(l, i) v_i (a block as
+// stored: 12 consecutive entries) or sum_i B(i, l) v_i (transposed: the group
+// reads 12 consecutive entries per i), with v_i broadcast by shuffles, so no
+// cross-lane reduction of products is needed; the two groups' sums are added
+// at the end of the row.
 #include <stddef.h>
 
 #include <algorithm>
@@ -28,32 +44,53 @@ namespace abd {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kChunk = 4;           // bodies per reduction chunk
 constexpr int kThreads = 256;       // threads per block of the solve kernel
 constexpr int kWarps = kThreads / 32;
 constexpr long long kBarrierTimeout = 4000000000LL;  // cycles (about 2 s at 2 GHz)
+constexpr int kRefineMax = 8;       // FP64 refinement rounds of the mixed solve
+constexpr double kInnerTolMin = 1e-5;  // smallest relative reduction asked of one FP32 inner solve
 
 struct PcgArgs {
-  int nb, nchunk, max_iter;
-  const int* np;                    // body pairs in the list (device count; clamps the rows)
+  int nb, max_iter, mixed;
   double tol2;                      // squared relative residual tolerance
+  const int* np;                    // body pairs in the list (device count; clamps the rows)
   const uint8_t* __restrict__ is_static;
-  const double* __restrict__ D;     // nb x 144 diagonal blocks, row-major
-  const double* __restrict__ Minv;  // nb x 144 inverse diagonal blocks
+  const double* __restrict__ D;     // nb x 144 diagonal blocks, row-major (FP64)
+  const double* __restrict__ Minv;  // nb x 144 inverse diagonal blocks (FP64)
+  const double* __restrict__ pblk;  // per pair kBlkStride doubles, H_ab first (FP64)
+  const float* __restrict__ D32;    // mixed: the same blocks in FP32, pairs 144 apart
+  const float* __restrict__ Minv32;
+  const float* __restrict__ H32;
   const int* __restrict__ rowoff;   // nb + 1: upper pairs of each row in P
   const int* __restrict__ in_off;   // nb + 1: incoming pairs of each row
   const int* __restrict__ in_list;
   const int2* __restrict__ P;
-  const double* __restrict__ pblk;  // per pair kBlkStride doubles, H_ab first
-  double* x;
+  const double* rhs;                // mixed: the right-hand side (FP64)
+  double* x;                        // the solution (FP64)
+  // FP64 solve: residual, preconditioned residual, two alternating
+  // directions, H p; mixed: the same five in FP32 (..f), r being the FP64
+  // refinement residual
   double* r;
   double* z;
-  double* p0;                       // search directions, alternating by iteration
+  double* p0;
   double* p1;
   double* Ap;
-  double* cpart;                    // 3 x nchunk chunk partials: p.Ap, r.z, r.r
+  float* rf;
+  float* zf;
+  float* p0f;
+  float* p1f;
+  float* Apf;
+  float* xf;                        // mixed: the inner solution
+  double* cpart;                    // 4 x nb per-body partials: p.Ap, r.z, r.r, FP64 r.r
   unsigned* bar;                    // grid barrier: arrivals, generation, abort
   DevStatus* st;
+  // preconditioner clusters: members, bounds, factor offsets, factors, flags
+  const int* nclu;
+  const int* __restrict__ c_perm;
+  const int* __restrict__ c_off;
+  const long long* __restrict__ c_foff;
+  const double* __restrict__ c_fac;
+  const int* __restrict__ c_ok;
 };
 
 // ---- grid barrier ------------------------------------------------------------
@@ -84,7 +121,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned& gen) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     if (ld_volatile(&bar[2])) ok = 0;
@@ -97,35 +134,33 @@ __device__ bool grid_barrier(unsigned* bar, unsigned& gen) {
 }
 
 // ---- fixed-order sums --------------------------------------------------------
-// sum of the first 12 lanes' values (tree, fixed order); valid in lane 0
+// sum over lanes 0..11 of v (fixed tree); valid in lane 0
 __device__ __forceinline__ double sum12(double v) {
   const int lane = threadIdx.x & 31;
   double t = lane < 12 ? v : 0.0;
-  t += __shfl_down_sync(kFull, t, 8);   // lanes 0..3 gather 8..11
+  t += __shfl_down_sync(kFull, t, 8);
   t += __shfl_down_sync(kFull, t, 4);
   t += __shfl_down_sync(kFull, t, 2);
   t += __shfl_down_sync(kFull, t, 1);
   return t;
 }
 
-// the totals of K partial arrays (each nchunk long), by every thread of the
-// block: thread t adds entries t, t + kThreads, ... (loads independent of one
-// another), then a fixed tree over the block; the order depends only on
-// nchunk, so every block of the grid forms the same totals
+// totals of K per-body partial arrays (stride n), by every thread of the
+// block in an order that depends only on n: thread t adds entries t,
+// t + kThreads, ...; a fixed butterfly in each warp; the warps in order
 template <int K>
-__device__ void block_totals(const double* part, int nchunk, double* out) {
-  __shared__ double s_red[K][kWarps];
+__device__ void block_totals(const double* part, int n, double* out) {
+  __shared__ double s_red[4][kWarps];
   const int t = threadIdx.x;
   double acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = 0.0;
 #pragma unroll 4
-  for (int i = t; i < nchunk; i += kThreads)
+  for (int i = t; i < n; i += kThreads)
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] += part[(size_t)k * nchunk + i];
+    for (int k = 0; k < K; ++k) acc[k] += part[(size_t)k * n + i];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    // within the warp (fixed butterfly), then across the warps in order
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(kFull, acc[k], o);
     if ((t & 31) == 0) s_red[k][t >> 5] = acc[k];
@@ -141,231 +176,499 @@ __device__ void block_totals(const double* part, int nchunk, double* out) {
   __syncthreads();
 }
 
-// ---- warp-cooperative 12x12 block products --------------------------------
-// Lane l holds entries e = l + 32 k (k < 5, e < 144) of every block it reads,
-// so each block is read by the warp as contiguous 256-byte rows.  acc[k]
-// collects entry e's products for row e / 12 (a block used as stored) and
-// acct[k] for row e % 12 (a block used transposed); the 12 column values come
-// from lanes 0..11 by shuffles.
-struct BlockAcc {
-  double acc[5], acct[5];
-};
-
-__device__ __forceinline__ void acc_block(BlockAcc& A, const double* __restrict__ blk, double vlane,
-                                          bool transposed) {
+// ---- one body row of a block product ----------------------------------------
+// The row's blocks: the diagonal (index 0), the upper pairs, the incoming
+// pairs (transposed).  Group g = lane / 16 takes blocks g, g + 2, ...; lane
+// l = lane % 16 < 12 holds row DOF l.  For block j with column body c the
+// column values v_i = vcol(c, i) are produced by lane i of the group and
+// broadcast.  Returns y_l in lanes 0..11 (both groups' sums added).
+template <typename TB, typename TA, typename VF>
+__device__ __forceinline__ TA row_product(int b, int np, const PcgArgs& a, const TB* __restrict__ Dblk,
+                                          const TB* __restrict__ Hblk, long hstride, bool diag_only, VF vcol) {
   const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const int e = lane + 32 * k;
-    const int src = transposed ? e / 12 : e % 12;
-    const double v = __shfl_sync(kFull, vlane, src < 12 ? src : 0);
-    if (e < 144) {
-      const double h = __ldg(blk + e);
-      if (transposed) A.acct[k] = fma(h, v, A.acct[k]);
-      else A.acc[k] = fma(h, v, A.acc[k]);
+  const int g = lane >> 4, l = lane & 15;
+  const int up0 = a.rowoff[b], nup = diag_only ? 0 : max(0, min(a.rowoff[b + 1], np) - up0);
+  const int in0 = a.in_off[b], nin = diag_only ? 0 : a.in_off[b + 1] - in0;
+  const int nblk = 1 + nup + nin;
+  TA y = TA(0);
+  for (int j0 = 0; j0 < nblk; j0 += 2) {
+    const int j = j0 + g;
+    // the block, its column body and orientation (uniform within a group)
+    int c = b;
+    bool trans = false;
+    const TB* B = Dblk + (size_t)144 * b;
+    if (j >= 1 && j < nblk) {
+      int p;
+      if (j - 1 < nup) {
+        p = up0 + j - 1;
+        c = a.P[p].y;
+      } else {
+        p = a.in_list[in0 + j - 1 - nup];
+        c = a.P[p].x;
+        trans = true;
+      }
+      B = Hblk + (size_t)p * hstride;
     }
-  }
-}
-
-// row sums of the accumulated entries: lanes 0..11 receive y_l
-__device__ __forceinline__ double row_sums(const BlockAcc& A, double* sbuf) {
-  const int lane = threadIdx.x & 31;
+    const bool live = j < nblk && !a.is_static[c];
+    const TA vi = (live && l < 12) ? vcol(c, l) : TA(0);
+    // every lane of the warp takes part in the shuffles (both groups)
+    TA acc = TA(0);
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const int e = lane + 32 * k;
-    if (e < 144) {
-      sbuf[e] = A.acc[k];
-      sbuf[144 + e] = A.acct[k];
+    for (int i = 0; i < 12; ++i) {
+      const TA v = __shfl_sync(kFull, vi, (g << 4) + i);
+      if (live && l < 12) {
+        const TB h = trans ? __ldg(B + 12 * i + l) : __ldg(B + 12 * l + i);
+        acc = fma((TA)h, v, acc);
+      }
     }
+    y += acc;
   }
-  __syncwarp();
-  double y = 0.0;
-  if (lane < 12) {
-#pragma unroll
-    for (int j = 0; j < 12; ++j) y += sbuf[12 * lane + j];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) y += sbuf[144 + 12 * i + lane];
-  }
-  __syncwarp();
+  y += __shfl_down_sync(kFull, y, 16);
   return y;
 }
 
-// ---- the two phases of an iteration ------------------------------------------
+// ---- the phases ---------------------------------------------------------------
 // Phase A of iteration k: p_k = z_k + beta p_{k-1} (formed on the fly for the
 // row and every column it reads; p_0 = z_0 is given), Ap = H p_k, and the
-// chunk partials of p_k . Ap.  Warp w of the grid takes chunks w, w + W, ...
-__device__ void phase_spmv(const PcgArgs& a, int k, double beta, double* sbuf) {
+// per-body partials of p_k . Ap.  Warp w of the grid takes rows w, w + W, ...
+template <typename T>
+__device__ void phase_spmv(const PcgArgs& a, int k, T beta, const T* __restrict__ Dblk,
+                           const T* __restrict__ Hblk, long hstride, const T* z, T* p0, T* p1, T* Ap,
+                           double* part) {
   const int lane = threadIdx.x & 31;
   const int wgrid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const int np = *a.np;
-  const double* pold = (k & 1) ? a.p0 : a.p1;  // p_{k-1}
-  double* pnew = (k & 1) ? a.p1 : a.p0;        // p_k
+  const T* pold = (k & 1) ? p0 : p1;  // p_{k-1}
+  T* pnew = (k & 1) ? p1 : p0;        // p_k
   const bool fly = k > 0;
-  for (int c = wgrid; c < a.nchunk; c += nw) {
-    double pap = 0.0;
-    for (int b = c * kChunk; b < min(a.nb, (c + 1) * kChunk); ++b) {
-      if (a.is_static[b]) {
-        if (lane < 12) {
-          a.Ap[12 * b + lane] = 0.0;
-          pnew[12 * b + lane] = 0.0;
-        }
-        continue;
-      }
-      // this row's direction (lanes 0..11)
-      double pb = 0.0;
+  for (int b = wgrid; b < a.nb; b += nw) {
+    if (a.is_static[b]) {
       if (lane < 12) {
-        pb = fly ? fma(beta, pold[12 * b + lane], a.z[12 * b + lane]) : pnew[12 * b + lane];
+        Ap[12 * b + lane] = T(0);
+        pnew[12 * b + lane] = T(0);
       }
-      BlockAcc A;
-#pragma unroll
-      for (int q = 0; q < 5; ++q) A.acc[q] = A.acct[q] = 0.0;
-      acc_block(A, a.D + (size_t)144 * b, pb, false);
-      for (int p = a.rowoff[b]; p < min(a.rowoff[b + 1], np); ++p) {
-        const int o = a.P[p].y;
-        if (a.is_static[o]) continue;
-        double po = 0.0;
-        if (lane < 12) po = fly ? fma(beta, pold[12 * o + lane], a.z[12 * o + lane]) : pnew[12 * o + lane];
-        acc_block(A, a.pblk + (size_t)p * kBlkStride, po, false);
-      }
-      for (int q = a.in_off[b]; q < a.in_off[b + 1]; ++q) {
-        const int p = a.in_list[q];
-        const int o = a.P[p].x;
-        if (a.is_static[o]) continue;
-        double po = 0.0;
-        if (lane < 12) po = fly ? fma(beta, pold[12 * o + lane], a.z[12 * o + lane]) : pnew[12 * o + lane];
-        acc_block(A, a.pblk + (size_t)p * kBlkStride, po, true);
-      }
-      const double y = row_sums(A, sbuf);
-      if (lane < 12) {
-        a.Ap[12 * b + lane] = y;
-        if (fly) pnew[12 * b + lane] = pb;
-      }
-      const double t = sum12(pb * y);
-      pap += t;  // lane 0's value is the one used
+      if (lane == 0) part[b] = 0.0;
+      continue;
     }
-    if (lane == 0) a.cpart[c] = pap;
+    auto vcol = [&](int c, int i) -> T {
+      return fly ? fma(beta, pold[12 * c + i], z[12 * c + i]) : pnew[12 * c + i];
+    };
+    const T y = row_product<T, T>(b, np, a, Dblk, Hblk, hstride, false, vcol);
+    T pb = T(0);
+    if (lane < 12) {
+      pb = vcol(b, lane);
+      Ap[12 * b + lane] = y;
+    }
+    // p_k of this row is written after the row's reads (other rows read only
+    // p_{k-1} and z, never p_k, in this phase)
+    __syncwarp();
+    if (lane < 12 && fly) pnew[12 * b + lane] = pb;
+    const double t = sum12((double)pb * (double)y);
+    if (lane == 0) part[b] = t;
   }
 }
 
-// Phase B of iteration k: x += alpha p_k, r -= alpha Ap, z = Minv r, and the
-// chunk partials of r.z and r.r
-__device__ void phase_update(const PcgArgs& a, int k, double alpha, double* sbuf) {
+// z = (L L^T)^-1 r over the N = 12 n DOFs of a cluster of n >= 2 bodies, L
+// its Cholesky factor (packed lower rows: entry (i, j), j <= i, at
+// i (i + 1) / 2 + j, reciprocal pivots on the diagonal); one warp, r and z in
+// the rows of the members; ybuf: N doubles of the warp's shared memory.
+// Forward substitution row by row (lane sums in a fixed order), back
+// substitution column by column.
+__device__ __forceinline__ long ptri(int i, int j) { return (long)i * (i + 1) / 2 + j; }
+
+template <typename T>
+__device__ void cluster_solve(const PcgArgs& a, int c, const T* r, T* z, double* ybuf) {
+  const int lane = threadIdx.x & 31;
+  const int m0 = a.c_off[c], n = a.c_off[c + 1] - m0, N = 12 * n;
+  const double* L = a.c_fac + a.c_foff[c];
+  for (int i = lane; i < N; i += 32) ybuf[i] = (double)r[12 * a.c_perm[m0 + i / 12] + i % 12];
+  __syncwarp();
+  for (int i = 0; i < N; ++i) {
+    const double* Li = L + ptri(i, 0);
+    double t = 0.0;
+    for (int j = lane; j < i; j += 32) t = fma(Li[j], ybuf[j], t);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    if (lane == 0) ybuf[i] = (ybuf[i] - t) * Li[i];
+    __syncwarp();
+  }
+  for (int i = N - 1; i >= 0; --i) {
+    const double* Li = L + ptri(i, 0);
+    const double zi = ybuf[i] * Li[i];
+    __syncwarp();
+    for (int j = lane; j < i; j += 32) ybuf[j] = fma(-Li[j], zi, ybuf[j]);
+    if (lane == 0) ybuf[i] = zi;
+    __syncwarp();
+  }
+  for (int i = lane; i < N; i += 32) z[12 * a.c_perm[m0 + i / 12] + i % 12] = (T)ybuf[i];
+  __syncwarp();
+}
+
+// z = M^-1 r for the members of cluster c (r already in place): a singleton
+// (or a cluster whose factorisation failed) by the inverse diagonal blocks,
+// a larger cluster by its factor; then the members' partials of r.z and r.r
+template <typename T>
+__device__ void cluster_precond(const PcgArgs& a, int c, const T* __restrict__ Minv, const T* r, T* z,
+                                double* part_rz, double* part_rr, double* ybuf) {
+  const int lane = threadIdx.x & 31;
+  const int m0 = a.c_off[c], n = a.c_off[c + 1] - m0;
+  if (n >= 2 && a.c_ok[c]) {
+    cluster_solve<T>(a, c, r, z, ybuf);
+  } else {
+    for (int i = 0; i < n; ++i) {
+      const int b = a.c_perm[m0 + i];
+      const T rb = lane < 12 ? r[12 * b + lane] : T(0);
+      auto vcol = [&](int, int) -> T { return rb; };
+      const T zb = row_product<T, T>(b, 0, a, Minv, Minv, 0, true, vcol);
+      if (lane < 12) z[12 * b + lane] = zb;
+    }
+    __syncwarp();
+  }
+  for (int i = 0; i < n; ++i) {
+    const int b = a.c_perm[m0 + i];
+    const T rb = lane < 12 ? r[12 * b + lane] : T(0);
+    const T zb = lane < 12 ? z[12 * b + lane] : T(0);
+    const double rz = sum12((double)rb * (double)zb), rr = sum12((double)rb * (double)rb);
+    if (lane == 0) {
+      part_rz[b] = rz;
+      part_rr[b] = rr;
+    }
+  }
+}
+
+// Phase B of iteration k: x += alpha p_k, r -= alpha Ap, z = M^-1 r, and the
+// per-body partials of r.z (part[0..nb)) and r.r (part[nb..2nb)); warps take
+// clusters (static bodies are in none; their partials stay zero)
+template <typename T>
+__device__ void phase_update(const PcgArgs& a, int k, T alpha, const T* __restrict__ Minv, T* x, T* r, T* z,
+                             const T* p0, const T* p1, const T* Ap, double* part, double* ybuf) {
   const int lane = threadIdx.x & 31;
   const int wgrid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  const double* pk = (k & 1) ? a.p1 : a.p0;
-  for (int c = wgrid; c < a.nchunk; c += nw) {
-    double rz = 0.0, rr = 0.0;
-    for (int b = c * kChunk; b < min(a.nb, (c + 1) * kChunk); ++b) {
-      if (a.is_static[b]) continue;
-      double rb = 0.0;
+  const T* pk = (k & 1) ? p1 : p0;
+  const int nclu = *a.nclu;
+  for (int c = wgrid; c < nclu; c += nw) {
+    const int m0 = a.c_off[c], n = a.c_off[c + 1] - m0;
+    for (int i = 0; i < n; ++i) {
+      const int b = a.c_perm[m0 + i];
       if (lane < 12) {
-        const int i = 12 * b + lane;
-        a.x[i] = fma(alpha, pk[i], a.x[i]);
-        rb = fma(-alpha, a.Ap[i], a.r[i]);
-        a.r[i] = rb;
+        const int q = 12 * b + lane;
+        x[q] = fma(alpha, pk[q], x[q]);
+        r[q] = fma(-alpha, Ap[q], r[q]);
       }
-      BlockAcc A;
-#pragma unroll
-      for (int q = 0; q < 5; ++q) A.acc[q] = A.acct[q] = 0.0;
-      acc_block(A, a.Minv + (size_t)144 * b, rb, false);
-      const double zb = row_sums(A, sbuf);
-      if (lane < 12) a.z[12 * b + lane] = zb;
-      rz += sum12(rb * zb);
-      rr += sum12(rb * rb);
     }
-    if (lane == 0) {
-      a.cpart[a.nchunk + c] = rz;
-      a.cpart[2 * a.nchunk + c] = rr;
+    __syncwarp();
+    cluster_precond<T>(a, c, Minv, r, z, part, part + a.nb, ybuf);
+  }
+}
+
+// start of a solve: r = sign rhs (as T), x = 0, z = M^-1 r, p0 = z, and the
+// per-body r.z (part[nb..2nb)) and r.r (part[2nb..3nb)); static bodies' rows
+// and partials zero
+template <typename T, typename TR>
+__device__ void phase_start(const PcgArgs& a, const TR* rhs, double sign, const T* __restrict__ Minv, T* x, T* r,
+                            T* z, T* p0, double* part, double* ybuf) {
+  const int lane = threadIdx.x & 31;
+  const int wgrid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int b = wgrid; b < a.nb; b += nw) {
+    if (!a.is_static[b]) continue;
+    if (lane < 12) {
+      const int i = 12 * b + lane;
+      r[i] = x[i] = z[i] = p0[i] = T(0);
+    }
+    if (lane == 0) part[a.nb + b] = part[2 * a.nb + b] = 0.0;
+  }
+  const int nclu = *a.nclu;
+  for (int c = wgrid; c < nclu; c += nw) {
+    const int m0 = a.c_off[c], n = a.c_off[c + 1] - m0;
+    for (int i = 0; i < n; ++i) {
+      const int b = a.c_perm[m0 + i];
+      if (lane < 12) {
+        const int q = 12 * b + lane;
+        r[q] = (T)(sign * (double)rhs[q]);
+        x[q] = T(0);
+      }
+    }
+    __syncwarp();
+    cluster_precond<T>(a, c, Minv, r, z, part + a.nb, part + 2 * a.nb, ybuf);
+    for (int i = 0; i < n; ++i) {
+      const int b = a.c_perm[m0 + i];
+      if (lane < 12) p0[12 * b + lane] = z[12 * b + lane];
     }
   }
 }
 
-// The whole solve.  On entry x, r, z, p0 = z hold the start (x = 0, r = rhs,
-// z = Minv r) and cpart[nchunk..3 nchunk) the chunk partials of r.z and r.r.
-// On exit st->scal: [0] r.z, [2] r.r, [3] r.r at the start, [6] 1 converged /
-// 0 iteration cap / 2 breakdown (p.Ap <= 0) / 3 barrier timeout, [7] iterations.
-__global__ void __launch_bounds__(kThreads) k_pcg_solve(PcgArgs a) {
-  __shared__ double sbuf[kWarps][288];
-  double* wbuf = sbuf[threadIdx.x >> 5];
-  unsigned gen = 0;
-  double tot[3];
-  block_totals<2>(a.cpart + a.nchunk, a.nchunk, tot);
+// iterations of one PCG solve from the state phase_start left; stops when
+// r.r <= tol2 r.r_0 or after max_iter.  state: 1 converged, 0 cap,
+// 2 breakdown, 3 barrier timeout.  Returns the iterations.
+template <typename T>
+__device__ int pcg_loop(const PcgArgs& a, double tol2, int max_iter, const T* Dblk, const T* Hblk, long hstride,
+                        const T* Minv, T* x, T* r, T* z, T* p0, T* p1, T* Ap, double* part, double* ybuf,
+                        unsigned& gen, int& state, double& rz_out, double& rr_out, double& rr0_out) {
+  double tot[2];
+  block_totals<2>(part + a.nb, a.nb, tot);
   double rz = tot[0], rr = tot[1], rz_prev = 0.0;
   const double rr0 = rr;
   int k = 0;
-  int state = rr0 == 0.0 ? 1 : 0;
-  bool alive = true;
+  state = rr0 == 0.0 ? 1 : 0;
   // Hazards: phase_spmv of iteration k+1 overwrites the p.Ap partials and
   // phase_update of k+1 the r.z / r.r partials; every block has finished
   // reading them before the barrier that precedes each of those phases.
-  while (state == 0 && k < a.max_iter) {
-    phase_spmv(a, k, k > 0 ? rz / rz_prev : 0.0, wbuf);
-    if (!(alive = grid_barrier(a.bar, gen))) break;
-    block_totals<1>(a.cpart, a.nchunk, tot);
+  while (state == 0 && k < max_iter) {
+    phase_spmv<T>(a, k, (T)(k > 0 ? rz / rz_prev : 0.0), Dblk, Hblk, hstride, z, p0, p1, Ap, part);
+    if (!grid_barrier(a.bar, gen)) {
+      state = 3;
+      break;
+    }
+    block_totals<1>(part, a.nb, tot);
     const double pap = tot[0];
     if (!(pap > 0.0)) {
       state = 2;
       break;
     }
-    phase_update(a, k, rz / pap, wbuf);
-    if (!(alive = grid_barrier(a.bar, gen))) break;
-    block_totals<2>(a.cpart + a.nchunk, a.nchunk, tot);
+    phase_update<T>(a, k, (T)(rz / pap), Minv, x, r, z, p0, p1, Ap, part + a.nb, ybuf);
+    if (!grid_barrier(a.bar, gen)) {
+      state = 3;
+      break;
+    }
+    block_totals<2>(part + a.nb, a.nb, tot);
     rz_prev = rz;
     rz = tot[0];
     rr = tot[1];
     ++k;
-    if (rr <= a.tol2 * rr0) state = 1;
+    if (rr <= tol2 * rr0) state = 1;
   }
-  if (!alive) state = 3;
+  rz_out = rz;
+  rr_out = rr;
+  rr0_out = rr0;
+  return k;
+}
+
+// FP64 refinement residual of the mixed solve: r = rhs - H32 x (FP64
+// arithmetic on the FP32-stored blocks), per-body partials of r.r in part
+__device__ void phase_residual64(const PcgArgs& a, double* part) {
+  const int lane = threadIdx.x & 31;
+  const int wgrid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int np = *a.np;
+  for (int b = wgrid; b < a.nb; b += nw) {
+    if (a.is_static[b]) {
+      if (lane < 12) a.r[12 * b + lane] = 0.0;
+      if (lane == 0) part[b] = 0.0;
+      continue;
+    }
+    auto vcol = [&](int c, int i) -> double { return a.x[12 * c + i]; };
+    const double y = row_product<float, double>(b, np, a, a.D32, a.H32, 144, false, vcol);
+    double rb = 0.0;
+    if (lane < 12) {
+      rb = a.rhs[12 * b + lane] - y;
+      a.r[12 * b + lane] = rb;
+    }
+    const double rr = sum12(rb * rb);
+    if (lane == 0) part[b] = rr;
+  }
+}
+
+// x += (FP64) inner solution
+__device__ void phase_accumulate(const PcgArgs& a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int i = t; i < 12 * a.nb; i += gridDim.x * blockDim.x) a.x[i] += (double)a.xf[i];
+}
+
+// The whole solve.  FP64: on entry x, r, z, p0 = z hold the start (x = 0,
+// r = rhs, z = Minv r) and part[nb..3nb) the partials of r.z and r.r.  Mixed:
+// x = 0, r = rhs (FP64), part[3nb..4nb) the partials of rhs.rhs.  On exit
+// st->scal: [0] r.z, [2] r.r, [3] r.r at the start, [6] 1 converged / 0 cap /
+// 2 breakdown (p.Ap <= 0) / 3 barrier timeout, [7] iterations (inner
+// iterations summed over the refinement rounds when mixed), [8] refinement
+// rounds.
+__global__ void __launch_bounds__(kThreads, 2) k_pcg_solve(PcgArgs a) {
+  __shared__ double s_y[kWarps][12 * kClusterMax];
+  double* ybuf = s_y[threadIdx.x >> 5];
+  unsigned gen = 0;
+  int state = 0, k = 0, rounds = 0;
+  double rz = 0.0, rr = 0.0, rr0 = 0.0;
+  if (!a.mixed) {
+    k = pcg_loop<double>(a, a.tol2, a.max_iter, a.D, a.pblk, kBlkStride, a.Minv, a.x, a.r, a.z, a.p0, a.p1, a.Ap,
+                         a.cpart, ybuf, gen, state, rz, rr, rr0);
+  } else {
+    double tot[1];
+    block_totals<1>(a.cpart + 3 * a.nb, a.nb, tot);
+    const double bb = tot[0];
+    double r64 = bb;  // squared FP64 residual of the current x
+    rr0 = bb;
+    state = bb == 0.0 ? 1 : 0;
+    while (state == 0 && rounds < kRefineMax && k < a.max_iter) {
+      // inner FP32 solve of H32 d = r, asked for the reduction that would
+      // meet the tolerance (not below what FP32 iterations attain)
+      const double want = a.tol2 * bb / r64;
+      const double inner = want > kInnerTolMin * kInnerTolMin ? want : kInnerTolMin * kInnerTolMin;
+      phase_start<float, double>(a, a.r, 1.0, a.Minv32, a.xf, a.rf, a.zf, a.p0f, a.cpart, ybuf);
+      if (!grid_barrier(a.bar, gen)) {
+        state = 3;
+        break;
+      }
+      int st_in = 0;
+      double rzi, rri, rr0i;
+      k += pcg_loop<float>(a, inner, a.max_iter - k, a.D32, a.H32, 144, a.Minv32, a.xf, a.rf, a.zf, a.p0f, a.p1f,
+                           a.Apf, a.cpart, ybuf, gen, st_in, rzi, rri, rr0i);
+      ++rounds;
+      if (st_in == 3 || st_in == 2) {
+        state = st_in;
+        break;
+      }
+      phase_accumulate(a);
+      if (!grid_barrier(a.bar, gen)) {
+        state = 3;
+        break;
+      }
+      phase_residual64(a, a.cpart + 3 * a.nb);
+      if (!grid_barrier(a.bar, gen)) {
+        state = 3;
+        break;
+      }
+      block_totals<1>(a.cpart + 3 * a.nb, a.nb, tot);
+      r64 = tot[0];
+      rz = rzi;
+      if (r64 <= a.tol2 * bb) state = 1;
+    }
+    rr = r64;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.st->scal[0] = rz;
     a.st->scal[2] = rr;
     a.st->scal[3] = rr0;
     a.st->scal[6] = (double)state;
     a.st->scal[7] = (double)k;
+    a.st->scal[8] = (double)rounds;
     if (state == 2 || state == 3) atomicOr(&a.st->flags, ST_PCG_BREAKDOWN);
   }
 }
 
-// r = rhs (dynamic rows), x = 0, z = Minv r, p0 = z, chunk partials of r.z, r.r
+// start of a solve from rhs (times sign): FP64 as phase_start; mixed: x = 0,
+// r = sign rhs (FP64) and the partials of r.r
 __global__ void k_pcg_init(PcgArgs a, const double* __restrict__ rhs, double sign) {
-  __shared__ double sbuf[kWarps][288];
-  double* wbuf = sbuf[threadIdx.x >> 5];
+  __shared__ double s_y[kWarps][12 * kClusterMax];
+  if (!a.mixed) {
+    phase_start<double, double>(a, rhs, sign, a.Minv, a.x, a.r, a.z, a.p0, a.cpart, s_y[threadIdx.x >> 5]);
+    return;
+  }
   const int lane = threadIdx.x & 31;
   const int wgrid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int c = wgrid; c < a.nchunk; c += nw) {
-    double rz = 0.0, rr = 0.0;
-    for (int b = c * kChunk; b < min(a.nb, (c + 1) * kChunk); ++b) {
-      const bool st = a.is_static[b];
-      double rb = 0.0;
-      if (lane < 12) {
-        const int i = 12 * b + lane;
-        rb = st ? 0.0 : sign * rhs[i];
-        a.r[i] = rb;
-        a.x[i] = 0.0;
-      }
-      double zb = 0.0;
-      if (!st) {
-        BlockAcc A;
-#pragma unroll
-        for (int q = 0; q < 5; ++q) A.acc[q] = A.acct[q] = 0.0;
-        acc_block(A, a.Minv + (size_t)144 * b, rb, false);
-        zb = row_sums(A, wbuf);
-      }
-      if (lane < 12) {
-        a.z[12 * b + lane] = zb;
-        a.p0[12 * b + lane] = zb;
-      }
-      rz += sum12(rb * zb);
-      rr += sum12(rb * rb);
+  for (int b = wgrid; b < a.nb; b += nw) {
+    const bool st = a.is_static[b];
+    double rb = 0.0;
+    if (lane < 12) {
+      const int i = 12 * b + lane;
+      rb = st ? 0.0 : sign * rhs[i];
+      a.r[i] = rb;
+      a.x[i] = 0.0;
     }
-    if (lane == 0) {
-      a.cpart[a.nchunk + c] = rz;
-      a.cpart[2 * a.nchunk + c] = rr;
+    const double rr = sum12(rb * rb);
+    if (lane == 0) a.cpart[3 * a.nb + b] = rr;
+  }
+}
+
+// mixed: the rhs of the solve (FP64, kept for the refinement residual)
+__global__ void k_pcg_rhs_copy(int n, const double* rhs, double sign, double* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = sign * rhs[i];
+}
+
+// mixed: FP32 copies of the diagonal blocks, the inverse diagonal blocks and
+// the upper pair blocks (packed 144 apart)
+__global__ void k_blocks_to_fp32(int nb, const DevStatus* cst, const double* D, const double* Minv,
+                                 const double* pblk, float* D32, float* Minv32, float* H32) {
+  const long nd = 144L * nb, nh = 144L * cst->np;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 2 * nd + nh; i += (long)gridDim.x * blockDim.x) {
+    if (i < nd) {
+      D32[i] = (float)D[i];
+    } else if (i < 2 * nd) {
+      Minv32[i - nd] = (float)Minv[i - nd];
+    } else {
+      const long j = i - 2 * nd, p = j / 144;
+      H32[j] = (float)pblk[p * kBlkStride + (j - 144 * p)];
     }
+  }
+}
+
+// Cholesky factors of the preconditioner clusters of two or more bodies:
+// one block per cluster builds the lower triangle of the cluster's dense
+// matrix in shared memory (packed rows; the members' diagonal blocks and the
+// upper blocks of the body pairs inside the cluster, placed below the
+// diagonal by the members' local order), factors it (right-looking, the
+// reciprocal pivots stored on the diagonal) and writes it to its slot.  The
+// cluster matrix is a principal submatrix of the positive definite Newton
+// Hessian, so a failure (a non-positive pivot) is a rounding accident: the
+// cluster is flagged and falls back to its members' inverse diagonal blocks.
+__global__ void __launch_bounds__(256) k_cluster_factor(const DevStatus* __restrict__ cst, const int* c_perm,
+                                                        const int* c_off, const int* c_of, const int* c_loc,
+                                                        const long long* c_foff, const double* D, const int* rowoff,
+                                                        const int2* P, const double* pblk, double* fac, int* ok,
+                                                        DevStatus* st) {
+  extern __shared__ double A[];
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nclu = cst->n_clusters, np = cst->np;
+  for (int c = blockIdx.x; c < nclu; c += gridDim.x) {
+    const int m0 = c_off[c], n = c_off[c + 1] - m0;
+    if (n < 2) continue;
+    const int N = 12 * n;
+    const long NT = ptri(N, 0);
+    for (long i = tid; i < NT; i += nt) A[i] = 0.0;
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    for (int t = tid; t < n * 144; t += nt) {
+      const int i = t / 144, e = t - 144 * i, r = e / 12, cc = e % 12;
+      if (cc <= r) A[ptri(12 * i + r, 12 * i + cc)] = D[144L * c_perm[m0 + i] + e];
+    }
+    for (int i = 0; i < n; ++i) {
+      const int b = c_perm[m0 + i];
+      for (int p = rowoff[b]; p < min(rowoff[b + 1], np); ++p) {
+        const int o = P[p].y;
+        if (c_of[o] != c) continue;
+        const int j = c_loc[o];
+        for (int e = tid; e < 144; e += nt) {
+          const double h = pblk[(size_t)p * kBlkStride + e];  // H_bo(r, cc): row of b, column of o
+          const int r = e / 12, cc = e % 12;
+          if (i > j) A[ptri(12 * i + r, 12 * j + cc)] = h;
+          else A[ptri(12 * j + cc, 12 * i + r)] = h;
+        }
+      }
+    }
+    __syncthreads();
+    for (int k = 0; k < N; ++k) {
+      if (tid == 0) {
+        double d = A[ptri(k, k)];
+        if (!(d > 0.0)) {
+          s_fail = 1;
+          d = 1.0;
+        }
+        A[ptri(k, k)] = 1.0 / sqrt(d);
+      }
+      __syncthreads();
+      const double rk = A[ptri(k, k)];
+      for (int i = k + 1 + tid; i < N; i += nt) A[ptri(i, k)] *= rk;
+      __syncthreads();
+      const int m = N - k - 1;
+      for (int t = tid; t < m * m; t += nt) {
+        const int ii = t / m, jj = t - m * ii;
+        if (jj <= ii) {
+          const int i = k + 1 + ii, j = k + 1 + jj;
+          A[ptri(i, j)] = fma(-A[ptri(i, k)], A[ptri(j, k)], A[ptri(i, j)]);
+        }
+      }
+      __syncthreads();
+    }
+    double* L = fac + c_foff[c];
+    for (long t = tid; t < NT; t += nt) L[t] = A[t];
+    if (tid == 0) {
+      ok[c] = s_fail ? 0 : 1;
+      if (s_fail) atomicAdd(&st->clu_fail, 1);
+    }
+    __syncthreads();
   }
 }
 
@@ -377,34 +680,60 @@ __global__ void k_pcg_init(PcgArgs a, const double* __restrict__ rhs, double sig
 static PcgArgs pcg_args(Scene& s, double* xout, int max_iter, double rel_tol) {
   PcgArgs a;
   a.nb = s.nb;
-  a.nchunk = (s.nb + kChunk - 1) / kChunk;
   a.max_iter = max_iter;
+  a.mixed = s.pcg_mixed ? 1 : 0;
   a.tol2 = rel_tol * rel_tol;
+  a.np = &s.st->np;
   a.is_static = s.is_static.p;
   a.D = s.D.p;
   a.Minv = s.Pinv.p;
+  a.pblk = s.pblk.p;
+  a.D32 = s.D32.p;
+  a.Minv32 = s.Minv32.p;
+  a.H32 = s.H32.p;
   a.rowoff = s.rowoff.p;
   a.in_off = s.in_off.p;
   a.in_list = s.in_list.p;
   a.P = s.P.p;
-  a.pblk = s.pblk.p;
+  a.rhs = s.rhs64.p;
   a.x = xout;
   a.r = s.r.p;
   a.z = s.z.p;
   a.p0 = s.pv.p;
   a.p1 = s.pv2.p;
   a.Ap = s.Ap.p;
+  a.rf = s.vf.p;
+  a.zf = s.vf.p ? s.vf.p + 12L * s.nb : nullptr;
+  a.p0f = s.vf.p ? s.vf.p + 24L * s.nb : nullptr;
+  a.p1f = s.vf.p ? s.vf.p + 36L * s.nb : nullptr;
+  a.Apf = s.vf.p ? s.vf.p + 48L * s.nb : nullptr;
+  a.xf = s.vf.p ? s.vf.p + 60L * s.nb : nullptr;
   a.cpart = s.part.p;
   a.bar = s.pcg_bar.p;
   a.st = s.st;
-  a.np = &s.st->np;
+  a.nclu = &s.st->n_clusters;
+  a.c_perm = s.c_perm.p;
+  a.c_off = s.c_off.p;
+  a.c_foff = s.c_foff.p;
+  a.c_fac = s.c_fac.p;
+  a.c_ok = s.c_ok.p;
   return a;
 }
 
-int pcg_chunks(int nb) { return (nb + kChunk - 1) / kChunk; }
+void launch_cluster_factor(Scene& s) {
+  static const int kSmem = (12 * kClusterMax) * (12 * kClusterMax + 1) / 2 * (int)sizeof(double);
+  if (!s.cluster_attr_set) {
+    cudaFuncSetAttribute(k_cluster_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    s.cluster_attr_set = true;
+  }
+  counted(s);
+  k_cluster_factor<<<sm_grid(s, 1), 256, kSmem, s.stream>>>(s.st, s.c_perm.p, s.c_off.p, s.c_of.p, s.c_loc.p,
+                                                           s.c_foff.p, s.D.p, s.rowoff.p, s.P.p, s.pblk.p,
+                                                           s.c_fac.p, s.c_ok.p, s.st);
+}
 
 // co-resident blocks of the solve kernel on this device (set once per scene)
-int pcg_grid(Scene& s) {
+static int pcg_grid(Scene& s) {
   if (s.pcg_blocks_per_sm <= 0) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_solve, kThreads, 0) != cudaSuccess ||
@@ -414,21 +743,34 @@ int pcg_grid(Scene& s) {
     }
     s.pcg_blocks_per_sm = std::min(per_sm, 2);
   }
-  // enough warps for the chunks, at most one wave of co-resident blocks
-  const int want = (pcg_chunks(s.nb) + kWarps - 1) / kWarps;
+  // enough warps for the rows, at most one wave of co-resident blocks
+  const int want = (s.nb + kWarps - 1) / kWarps;  // one warp per row or cluster
   const int cap = std::max(1, s.pcg_blocks_per_sm * s.num_sms / s.grid_div);
   return std::max(1, std::min(want, cap));
 }
 
+// mixed precision: FP32 copies of the assembled blocks (after the
+// preconditioner's inverse blocks exist)
+void launch_pcg_fp32_blocks(Scene& s) {
+  if (!s.pcg_mixed) return;
+  counted(s);
+  k_blocks_to_fp32<<<sm_grid(s, 8), 256, 0, s.stream>>>(s.nb, s.st, s.D.p, s.Pinv.p, s.pblk.p, s.D32.p, s.Minv32.p,
+                                                        s.H32.p);
+}
+
 void launch_pcg_init(Scene& s, const double* rhs, double sign, double* xout) {
   PcgArgs a = pcg_args(s, xout, 0, 0.0);
+  if (a.mixed) {
+    counted(s);
+    k_pcg_rhs_copy<<<sm_grid(s, 4), 256, 0, s.stream>>>(12 * s.nb, rhs, sign, s.rhs64.p);
+  }
   counted(s);
-  const int grid = std::max(1, std::min((a.nchunk + kWarps - 1) / kWarps, 4 * s.num_sms));
+  const int grid = std::max(1, std::min((s.nb + kWarps - 1) / kWarps, 4 * s.num_sms));
   k_pcg_init<<<grid, kThreads, 0, s.stream>>>(a, rhs, sign);
 }
 
-// the solve from the state k_pcg_init (or the preconditioner's fused start)
-// left; enqueued only (the result is in the status word)
+// the solve from the state k_pcg_init left; enqueued only (the result is in
+// the status word)
 void launch_pcg_solve(Scene& s, double* xout, int max_iter, double rel_tol) {
   PcgArgs a = pcg_args(s, xout, max_iter, rel_tol);
   counted(s);
@@ -448,11 +790,13 @@ void launch_pcg_solve(Scene& s, double* xout, int max_iter, double rel_tol) {
   cudaLaunchKernelEx(&cfg, k_pcg_solve, a);
 }
 
-// algorithmic bytes and FP64 operations of one iteration: every stored block
-// once (diagonal, upper off-diagonal), the inverse diagonal blocks once, the
-// vectors p, z, Ap, x, r read or written once each, the pair list once
+// algorithmic bytes and operations of one (inner) iteration: every stored
+// block once (diagonal, upper off-diagonal, inverse diagonal), the vectors
+// p, z, Ap, x, r read or written once each, the pair list once; 8-byte
+// entries in FP64, 4-byte in the mixed solve's inner iterations
 double pcg_iter_bytes(const Scene& s, long np) {
-  return 8.0 * 144.0 * (2.0 * s.nb + (double)np) + 8.0 * 12.0 * 8.0 * s.nb + 8.0 * np;
+  const double e = s.pcg_mixed ? 4.0 : 8.0;
+  return e * 144.0 * (2.0 * s.nb + (double)np) + e * 12.0 * 8.0 * s.nb + 8.0 * np;
 }
 double pcg_iter_flops(const Scene& s, long np) {
   // block products: diagonal and inverse once, each off-diagonal block twice
@@ -472,7 +816,7 @@ int pcg_result(Scene& s, double* rel_res) {
   return iters;
 }
 
-// with profiling on, the algorithmic bytes and FP64 operations of a finished
+// with profiling on, the algorithmic bytes and operations of a finished
 // solve (its iteration count is known only once the status word is read)
 void pcg_account(Scene& s, int its) {
   if (!s.prof.on || its == -2 || s.dense_n) return;
@@ -489,6 +833,7 @@ int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_
     cudaStreamSynchronize(s.stream);
     return pcg_result(s, rel_res);
   }
+  launch_pcg_fp32_blocks(s);
   launch_pcg_init(s, rhs, 1.0, xout);
   launch_pcg_solve(s, xout, max_iter, rel_tol);
   cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);

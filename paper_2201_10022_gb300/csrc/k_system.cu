@@ -856,16 +856,38 @@ __device__ __forceinline__ bool chol12(double* L) {
 
 // Hessian block of the body terms (Sec. 3.2, Sec. 4): B = M + dt^2 hess V_ortho
 // over q = (p, rows a_i of A), with the closed form
-//   d2 V / da_k da_l = 4 kappa nu [(a_k.a_l - delta_kl) I + delta_kl A^T A + a_l a_k^T],
+//   d2 V / da_k da_l = 4 kappa nu [C_kl I + delta_kl A^T A + a_l a_k^T],
+//   C = A A^T - I,
 // used as it is when it is positive definite (a Cholesky factorisation
-// succeeds) and replaced by its PSD projection otherwise (listed for
-// k_body_hess_fix).  One body per thread; static bodies get I.
+// succeeds).  Otherwise C is replaced by its eigenvalue clamp C+ (3x3 cyclic
+// Jacobi): the Gauss-Newton part of the sum of squares V = kappa nu |C|_F^2
+// stays and the residual curvature is clamped, so the block is positive
+// definite (M is) and equals the true one whenever C is positive
+// semidefinite.  One body per thread; static bodies get I.
 __device__ __forceinline__ int qcomp(int i) { return i < 3 ? i : (i - 3) / 3; }  // spatial row of dof i
 __device__ __forceinline__ int qmono(int i) { return i < 3 ? 0 : 1 + (i - 3) % 3; }  // 1, xbar_x, xbar_y, xbar_z
 
+__device__ __forceinline__ void body_block(const double W[4][4], const double A[3][3], const double C[3][3],
+                                           double s4, double* B) {
+#pragma unroll
+  for (int i = 0; i < 12; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      double v = qcomp(i) == qcomp(j) ? W[qmono(i)][qmono(j)] : 0.0;
+      if (i >= 3 && j >= 3) {
+        const int k = qcomp(i), ck = qmono(i) - 1, l = qcomp(j), cl = qmono(j) - 1;
+        double h = A[l][ck] * A[k][cl];
+        if (ck == cl) h += C[k][l];
+        if (k == l) h += A[0][ck] * A[0][cl] + A[1][ck] * A[1][cl] + A[2][ck] * A[2][cl];
+        v += s4 * h;
+      }
+      B[tri(i, j)] = v;
+    }
+}
+
 __global__ void __launch_bounds__(kBodyWarp) k_body_hess(int nb, const uint8_t* is_static, const double* q,
                                                          const double* mass10, const double* vol,
-                                                         const double* kappa_b, double dt, double* Db, int* fix,
+                                                         const double* kappa_b, double dt, int project, double* Db,
                                                          DevStatus* st) {
   __shared__ double S[kBodyWarp][145];
   const int t = threadIdx.x;
@@ -876,30 +898,42 @@ __global__ void __launch_bounds__(kBodyWarp) k_body_hess(int nb, const uint8_t* 
     const double* m = mass10 + 10 * b;
     const double W[4][4] = {{m[0], m[1], m[2], m[3]}, {m[1], m[4], m[5], m[6]}, {m[2], m[5], m[7], m[8]},
                             {m[3], m[6], m[8], m[9]}};
-    double A[3][3];
+    double A[3][3], C[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int c = 0; c < 3; ++c) A[i][c] = q[12 * b + 3 + 3 * i + c];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        C[k][l] = A[k][0] * A[l][0] + A[k][1] * A[l][1] + A[k][2] * A[l][2] - (k == l ? 1.0 : 0.0);
     const double s4 = dt * dt * 4.0 * kappa_b[b] * vol[b];
-#pragma unroll
-    for (int i = 0; i < 12; ++i)
-#pragma unroll
-      for (int j = 0; j <= i; ++j) {
-        double v = qcomp(i) == qcomp(j) ? W[qmono(i)][qmono(j)] : 0.0;
-        if (i >= 3 && j >= 3) {
-          const int k = qcomp(i), ck = qmono(i) - 1, l = qcomp(j), cl = qmono(j) - 1;
-          double h = A[l][ck] * A[k][cl];
-          if (ck == cl) h += A[k][0] * A[l][0] + A[k][1] * A[l][1] + A[k][2] * A[l][2] - (k == l ? 1.0 : 0.0);
-          if (k == l) h += A[0][ck] * A[0][cl] + A[1][ck] * A[1][cl] + A[2][ck] * A[2][cl];
-          v += s4 * h;
-        }
-        B[tri(i, j)] = v;
-      }
+    body_block(W, A, C, s4, B);
     double L[78];
 #pragma unroll
     for (int k = 0; k < 78; ++k) L[k] = B[k];
-    if (!chol12(L)) fix[atomicAdd(&st->bh_fix, 1)] = (int)b;  // rare: projected afterwards
+    if (project && !chol12(L)) {
+      double Cm[9], V[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Cm[k] = C[k / 3][k % 3];
+      jacobi_eig<3, double>(Cm, V);
+      double Cp[3][3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+          double v = 0.0;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double lam = Cm[4 * c];
+            if (lam > 0.0) v += V[3 * k + c] * lam * V[3 * l + c];
+          }
+          Cp[k][l] = v;
+        }
+      body_block(W, A, Cp, s4, B);
+      atomicAdd(&st->bh_fix, 1);
+    }
   } else {
 #pragma unroll
     for (int i = 0; i < 12; ++i)
@@ -917,26 +951,6 @@ __global__ void __launch_bounds__(kBodyWarp) k_body_hess(int nb, const uint8_t* 
   for (int k = t; k < kBodyWarp * 144; k += kBodyWarp) {
     const int bb = k / 144, e = k - 144 * bb;
     if (b0 + bb < nb) Db[144 * (b0 + bb) + e] = S[bb][e];
-  }
-}
-
-// PSD projection (eigenvalue clamp) of the body blocks that failed Cholesky
-__global__ void k_body_hess_fix(const DevStatus* cst, const int* fix, double* Db) {
-  const int n = cst->bh_fix;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    double* Bk = Db + 144L * fix[k];
-    double Ab[144], V[144];
-    for (int i = 0; i < 144; ++i) Ab[i] = Bk[i];
-    jacobi_eig<12, double>(Ab, V);
-    for (int i = 0; i < 12; ++i)
-      for (int j = 0; j < 12; ++j) {
-        double t = 0.0;
-        for (int c = 0; c < 12; ++c) {
-          const double lam = Ab[13 * c];
-          if (lam > 0.0) t += V[12 * i + c] * lam * V[12 * j + c];
-        }
-        Bk[12 * i + j] = t;
-      }
   }
 }
 
@@ -1241,8 +1255,8 @@ void launch_body_terms(Scene& s, const double* q, bool hess, bool project) {
     counted(s, 2);
     cudaMemsetAsync(reinterpret_cast<char*>(s.st) + offsetof(DevStatus, bh_fix), 0, sizeof(int), s.stream);
     k_body_hess<<<blocks(s.nb, kBodyWarp), kBodyWarp, 0, s.stream>>>(s.nb, s.is_static.p, q, s.mass10.p, s.vol.p,
-                                                                     s.kappa_b.p, s.prm.dt, s.Db.p, s.hfix.p, s.st);
-    if (project) k_body_hess_fix<<<1, 32, 0, s.stream>>>(s.st, s.hfix.p, s.Db.p);
+                                                                     s.kappa_b.p, s.prm.dt, project ? 1 : 0, s.Db.p,
+                                                                     s.st);
   }
 }
 
@@ -1255,11 +1269,13 @@ void launch_gather(Scene& s) {
 void launch_precond(Scene& s) {
   counted(s);
   k_precond<<<blocks(s.nb, kBodyWarp), kBodyWarp, 0, s.stream>>>(s.nb, s.is_static.p, s.D.p, s.Pinv.p, s.st);
+  launch_cluster_factor(s);
 }
 
 // the preconditioner, then the start of the Newton solve H dx = -g
 void launch_precond_start(Scene& s, double* xout) {
   launch_precond(s);
+  launch_pcg_fp32_blocks(s);
   launch_pcg_init(s, s.g.p, -1.0, xout);
 }
 

@@ -4,9 +4,16 @@ cuda:0 (for profilers: a small, self-terminating case).
     python -m paper_2201_10022_gb300.profile_case packed 10 10 10 --evals 2
     python -m paper_2201_10022_gb300.profile_case lattice 25 20 20 --steps 3
     python -m paper_2201_10022_gb300.profile_case throw 4 10 0 --steps 20 --dense --newton-rel 1e-9 --prof
+    python -m paper_2201_10022_gb300.profile_case packed 22 22 21 --solves 2 --pcg-max 200
+
+This module is the profiling entry point of the commands recorded under
+profiles/: each run is bounded (a fixed number of evaluations, steps or
+linear solves), so a profiler capture of it ends by itself.
 
 `packed` evaluates energy, gradient and Hessian of a contact-dense block of
-cubes (every face pair within d-hat); `lattice` advances the lattice pile;
+cubes (every face pair within d-hat), and with --solves runs that many
+linear solves of its Newton system (abd_solve, at most --pcg-max
+iterations each, at --precision); `lattice` advances the lattice pile;
 `throw` advances the throw-into-stack scene (dims: cubes per side of the
 thrown block, stack height, unused).
 """
@@ -26,6 +33,10 @@ def main():
     ap.add_argument("--steps", type=int, default=0)
     ap.add_argument("--prof", action="store_true", help="print per-slot kernel times (CUDA events)")
     ap.add_argument("--dense", action="store_true", help="dense direct solves (dense_max_dofs 3072)")
+    ap.add_argument("--solves", type=int, default=0, help="linear solves of the evaluated Newton system")
+    ap.add_argument("--pcg-max", type=int, default=200, help="PCG iteration cap of those solves")
+    ap.add_argument("--pcg-tol", type=float, default=1e-8, help="PCG relative tolerance of those solves")
+    ap.add_argument("--precision", type=int, default=0, help="0 FP64, 1 mixed")
     ap.add_argument("--newton-rel", type=float, default=0.0,
                     help="Newton tolerance relative to the dynamic bodies' box diagonal (0: library default)")
     a = ap.parse_args()
@@ -36,7 +47,9 @@ def main():
         s = scenes.lattice_pile(nx=nx, ny=ny, nz=nz)
     else:
         s = scenes.throw_stack(n_throw=nx ** 3, n_stack=ny)
-    kw = {}
+    kw = {"precision": a.precision}
+    if a.solves:
+        kw.update(pcg_max=a.pcg_max, pcg_rel_tol=a.pcg_tol)
     if a.dense:
         kw["dense_max_dofs"] = 3072
     if a.newton_rel > 0:
@@ -53,6 +66,18 @@ def main():
         g.set_profiling(True)
     for _ in range(a.evals):
         E, grad, cnt = g.energy_grad_hess(q)
+    solves = []
+    for _ in range(a.solves):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        try:
+            _, sst = g.solve(-grad)
+        except Exception as e:  # the iteration cap is an outcome here, not a failure
+            sst = {"error": str(e).split(":")[0]}
+        e1.record()
+        torch.cuda.synchronize()
+        solves.append(dict(sst, ms=round(e0.elapsed_time(e1), 3)))
     st = None
     if a.steps:
         torch.cuda.synchronize()
@@ -64,6 +89,8 @@ def main():
         st = dict(st, ms_per_step=e0.elapsed_time(e1) / a.steps)
     torch.cuda.synchronize()
     out = {"bodies": s.nb, "active": cnt["n_active"], "candidates": cnt["n_candidates"], "energy": float(E[0])}
+    if solves:
+        out["solves"] = solves
     if st:
         out["steps"] = {k: st[k] for k in ("ms_per_step", "newton_iters", "pcg_iters", "ls_halvings", "n_active",
                                            "kernel_launches")}

@@ -183,3 +183,24 @@ def test_trajectory_friction_slide(abd):
     s = B.build(dict(mu=0.3))
     worst, L = _trajectory(abd, s, 25)
     assert worst <= 1e-8 * L, (worst, L)
+
+
+def test_body_block_projection_when_indefinite(abd):
+    """strongly compressed bodies: M + dt^2 hess V is indefinite and both
+    sides use M + dt^2 PSD(hess V); the diagonal blocks agree with the
+    oracle's and are positive definite"""
+    s = scenes.cube_stack(n=2)
+    q = s.q0.copy()
+    dyn = s.is_static == 0
+    q[dyn, 3:] *= 0.95
+    gpu = abd.AbdScene(s)
+    orc = O.Oracle(s)
+    gpu.energy_grad_hess(torch.tensor(q))
+    st, _, _ = orc.energy_grad_hess(q.reshape(-1))
+    assert st == 0
+    diag, _, _ = gpu.hessian()
+    od, _, _ = orc.hessian()
+    hs = np.abs(od).max()
+    np.testing.assert_allclose(diag, od, atol=1e-9 * hs, rtol=0)
+    for b in np.nonzero(dyn)[0]:
+        assert np.linalg.eigvalsh(diag[b]).min() > 0

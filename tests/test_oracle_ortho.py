@@ -130,7 +130,10 @@ def test_body_block_is_unprojected_when_positive_definite():
 
 def test_body_block_is_projected_when_indefinite():
     """strong compression makes M + dt^2 hess V indefinite: the assembled body
-    block is then its eigenvalue clamp (numpy's eigh as the reference)"""
+    block is then M + dt^2 H+, where H+ is hess V (the oracle's jets) with
+    its residual-curvature part 4 kappa nu C (x) I (C = A A^T - I, over the
+    rows of A) replaced by the eigenvalue clamp of C (numpy's eigh); the block
+    is positive definite"""
     s = scenes.cube_stack(n=2)
     o = O.Oracle(s)
     q = s.q0.reshape(-1).copy()
@@ -144,11 +147,22 @@ def test_body_block_is_projected_when_indefinite():
     for b in range(s.nb):
         if s.is_static[b]:
             continue
-        _, _, Hv = O.ortho(q[12 * b:12 * b + 12], s.kappa_body[b], o.moments(b)[0])
-        B = o.mass_matrix(b) + dt * dt * Hv
-        w, V = np.linalg.eigh(B)
-        if w.min() > 0:
+        vol = o.moments(b)[0]
+        qb = q[12 * b:12 * b + 12]
+        _, _, Hv = O.ortho(qb, s.kappa_body[b], vol)
+        M = o.mass_matrix(b)
+        B = M + dt * dt * Hv
+        if np.linalg.eigvalsh(B).min() > 0:
             continue
         n_proj += 1
-        np.testing.assert_allclose(diag[b], (V * np.maximum(w, 0)) @ V.T, rtol=0, atol=1e-10 * np.abs(B).max())
+        A = qb[3:].reshape(3, 3)
+        C = A @ A.T - np.eye(3)
+        w, V = np.linalg.eigh(C)
+        Cp = (V * np.maximum(w, 0)) @ V.T
+        Hp = Hv.copy()
+        Hp[3:, 3:] += 4 * s.kappa_body[b] * vol * np.kron(Cp - C, np.eye(3))
+        assert np.linalg.eigvalsh(Hp).min() >= -1e-12 * np.abs(Hp).max()
+        np.testing.assert_allclose(diag[b], M + dt * dt * Hp, rtol=0, atol=1e-10 * np.abs(B).max())
+        assert np.linalg.eigvalsh(diag[b]).min() > 0
     assert n_proj > 0
+
