@@ -155,8 +155,9 @@ BARRIER_DRAM_BYTES = 139264
 # capture (None until captured for the kernel as it stands)
 PCG_DRAM_BYTES_PER_ITER = None
 # first steps of the default timed windows: first ground impacts of the
-# bottom layer, bottom layer on the ground with friction, second layer landing
-DEFAULT_WINDOWS = "10,30,50"
+# bottom layer, bottom layer on the ground with friction, second layer
+# landing, third layer landing
+DEFAULT_WINDOWS = "10,30,50,70"
 
 
 def log(msg):
@@ -365,6 +366,67 @@ def batched_run(dev, steps=2, pre_steps=10, seed=5, n_scenes=256):
     }
 
 
+def plain_hash_tests(s, q, dhat, h=None):
+    """Box tests a plain primitive-level uniform hash would run at state q
+    (the culling the paper's i-AABB is set against, Sec. 4.2), on the host:
+    every primitive's box (triangles and edges dilated by dhat, points as
+    points) in each cell it covers, cell edge h (default: the median box
+    extent of the dynamic bodies' triangles); per cell, point-triangle tests
+    between different bodies and edge-edge tests between different bodies,
+    a pair sharing k cells counted k times."""
+    x = vertices(s, q)
+    tri, edge, vb = s.tri, s.edge, s.vbody
+    tlo, thi = x[tri].min(axis=1) - dhat, x[tri].max(axis=1) + dhat
+    elo, ehi = x[edge].min(axis=1) - dhat, x[edge].max(axis=1) + dhat
+    if h is None:
+        dyn_t = s.is_static[vb[tri[:, 0]]] == 0
+        h = float(np.median((thi - tlo)[dyn_t].max(axis=1)))
+
+    def cells(lo, hi):
+        a = np.floor(lo / h).astype(np.int64)
+        b = np.floor(hi / h).astype(np.int64)
+        ext = b - a + 1
+        n = np.prod(ext, axis=1)
+        idx = np.repeat(np.arange(len(lo)), n)
+        off = np.arange(int(n.sum())) - np.repeat(np.cumsum(n) - n, n)
+        e = ext[idx]
+        c = a[idx] + np.stack([off % e[:, 0], (off // e[:, 0]) % e[:, 1], off // (e[:, 0] * e[:, 1])], axis=1)
+        return idx, ((c[:, 0] + (1 << 20)) << 42) + ((c[:, 1] + (1 << 20)) << 21) + (c[:, 2] + (1 << 20))
+
+    pi, pk = cells(x, x)
+    ti, tk = cells(tlo, thi)
+    ei, ek = cells(elo, ehi)
+    keys, inv = np.unique(np.concatenate([pk, tk, ek]), return_inverse=True)
+    n_p, n_t = len(pk), len(tk)
+    parts = [(inv[:n_p], vb[pi]), (inv[n_p:n_p + n_t], vb[tri[ti, 0]]), (inv[n_p + n_t:], vb[edge[ei, 0]])]
+    cnt = [np.bincount(iv, minlength=len(keys)).astype(np.float64) for iv, _ in parts]
+    per_body = []
+    for iv, bodies in parts:
+        u, c = np.unique(iv.astype(np.int64) * s.nb + bodies, return_counts=True)
+        per_body.append((u, c.astype(np.float64)))
+    _, ip, it = np.intersect1d(per_body[0][0], per_body[1][0], return_indices=True)
+    pt = float((cnt[0] * cnt[1]).sum() - (per_body[0][1][ip] * per_body[1][1][it]).sum())
+    ce, cee = cnt[2], per_body[2][1]
+    ee = float(((ce * ce - ce) / 2).sum() - ((cee * cee - cee) / 2).sum())
+    return {"cell_edge_m": h, "box_tests": pt + ee, "point_triangle": pt, "edge_edge": ee}
+
+
+def culling_at_state(g, s):
+    """the library's culling counts for one enumeration at the scene's
+    current state (abd_energy_grad_hess at q), beside a plain primitive
+    hash's at the same state"""
+    q, _ = g.get_state()
+    c0 = g.counters()
+    g.energy_grad_hess(q)
+    c1 = g.counters()
+    lib = {k: c1[k] - c0[k] for k in ("prim_pairs_body", "prim_pairs_iaabb", "prim_pairs_cand")}
+    plain = plain_hash_tests(s, q.cpu().numpy(), s.params["dhat"])
+    return {"primitive_pairs_of_overlapping_body_pairs": lib["prim_pairs_body"],
+            "box_tests_after_iaabb": lib["prim_pairs_iaabb"], "candidates": lib["prim_pairs_cand"],
+            "plain_primitive_hash": plain,
+            "iaabb_tests_per_plain_hash_test": lib["prim_pairs_iaabb"] / max(plain["box_tests"], 1.0)}
+
+
 def window_splits(windows, steps):
     """timed steps per window: `steps` split as evenly as possible, the
     remainder to the last windows"""
@@ -402,7 +464,8 @@ def step_summary(stats, ms):
 
 def run_abd(args, rank, world):
     import torch
-    from paper_2201_10022_gb300.abd import AbdScene, abd_get_state, abd_set_state, abd_step, abd_step_stats
+    from paper_2201_10022_gb300.abd import (AbdError, AbdScene, abd_get_state, abd_set_state, abd_step,
+                                            abd_step_stats)
     import ctypes as C
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -424,20 +487,23 @@ def run_abd(args, rank, world):
     sst = abd_step_stats()
     L0 = bbox_diag(vertices(s, s.q0))
 
-    at = 0               # steps the scene has advanced
-    all_ms, all_stats, e2e_s, mixed_ms = [], [], 0.0, []
+    all_ms, all_stats, mixed_ms = [], [], []
     prof_tot = {}
     per_window = []
     clocks_rows = []
-    for w, (start, nsteps) in enumerate(zip(windows, splits)):
-        if nsteps <= 0:
-            continue
+    state = {"at": 0, "e2e_s": 0.0}  # steps the scene has advanced; e2e seconds
+
+    def run_window(w, start, nsteps):
+        """advance to the window, warm up, then the timed, profiled, e2e and
+        mixed passes over its steps"""
+        at = state["at"]
         first = max(start - args.warmup, at)
         if first > at:
             g.step(first - at)  # advance untimed (device), the pile's own trajectory
             at = first
         g.step(args.warmup)
         at += args.warmup
+        state["at"] = at
         torch.cuda.synchronize()
         log(f"window {w}: warm at step {at}")
         q0, qd0 = g.get_state()
@@ -449,6 +515,7 @@ def run_abd(args, rank, world):
             torch.distributed.barrier()
         torch.cuda.synchronize()
         clk.start()
+        torch.cuda.nvtx.range_push("timed")
         ms, stats = [], []
         for k in range(nsteps):
             flush.zero_()
@@ -459,12 +526,13 @@ def run_abd(args, rank, world):
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
             stats.append(st)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         clocks_rows.append(clk.stop())
-        all_ms += ms
-        all_stats += stats
+        all_ms.extend(ms)
+        all_stats.extend(stats)
 
         # ---- per-kernel-class device times: the same steps again from the
         # same state with the library's event profiling on
@@ -491,41 +559,65 @@ def run_abd(args, rank, world):
             r = r or abd_get_state(g.h, qh.data_ptr(), qdh.data_ptr(), 0)
             if r:
                 raise RuntimeError(f"e2e step failed: {r}")
-        e2e_s += time.perf_counter() - t0
+        state["e2e_s"] += time.perf_counter() - t0
         at = start_end = at + nsteps  # the scene is at the timed window's end state again
+        state["at"] = at
 
         # ---- mixed precision (precision = 1): the same steps from the same
         # state; its end state against the FP64 run's
         mixed = None
         if gm is not None:
-            gm.set_state(q0, qd0)
-            gm.step(1)  # buffer growth outside the timed steps
-            gm.set_state(q0, qd0)
-            torch.cuda.synchronize()
-            ms_m, st_m = [], []
-            for k in range(nsteps):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                st_m.append(gm.step(1))
-                e1.record()
+            try:
+                gm.set_state(q0, qd0)
+                gm.step(1)  # buffer growth outside the timed steps
+                gm.set_state(q0, qd0)
                 torch.cuda.synchronize()
-                ms_m.append(e0.elapsed_time(e1))
-            mixed_ms += ms_m
-            qm, _ = gm.get_state()
-            mixed = step_summary(st_m, ms_m)
-            mixed["max_vertex_deviation_vs_fp64_over_lbbox"] = float(
-                np.abs(vertices(s, qm.cpu().numpy()) - vertices(s, qh.numpy())).max() / L0)
+                ms_m, st_m = [], []
+                for k in range(nsteps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    st_m.append(gm.step(1))
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms_m.append(e0.elapsed_time(e1))
+                mixed_ms.extend(ms_m)
+                qm, _ = gm.get_state()
+                mixed = step_summary(st_m, ms_m)
+                mixed["max_vertex_deviation_vs_fp64_over_lbbox"] = float(
+                    np.abs(vertices(s, qm.cpu().numpy()) - vertices(s, qh.numpy())).max() / L0)
+            except AbdError as e:  # reported in the window, not fatal to the FP64 measurement
+                mixed = {"error": str(e)}
         summ = step_summary(stats, ms)
         summ["steps"] = f"{start_end - nsteps}..{start_end - 1}"
         summ["mixed"] = mixed
         per_window.append(summ)
         log(f"window {w}: steps {summ['steps']} {summ['ms_per_step']:.1f} ms/step, "
             f"{summ['newton_iters_per_step']:.1f} Newton/step, {summ['pcg_iters_per_newton']:.1f} PCG/Newton")
+
+    failed = None
+    for w, (start, nsteps) in enumerate(zip(windows, splits)):
+        if nsteps <= 0 or failed:
+            continue
+        try:
+            run_window(w, start, nsteps)
+        except (AbdError, RuntimeError) as e:  # the step is transactional: report it and stop here
+            failed = {"window_start": start, "error": str(e)}
+            log(f"window {w}: {e}")
     if gm is not None:
         gm.close()
+    culling_state = None
+    if per_window and world == 1:
+        try:
+            culling_state = culling_at_state(g, s)
+            culling_state["state"] = f"end of the last timed window (step {state['at']})"
+        except Exception as e:  # reported in the line, not fatal to the headline measurement
+            culling_state = {"error": f"{type(e).__name__}: {e}"}
+        log("culling counts at the last state done")
+    if not all_ms:
+        raise RuntimeError(f"no timed window completed: {failed}")
     total_ms = max_over_ranks(sum(all_ms), world, dev)
-    e2e_ms = max_over_ranks(1e3 * e2e_s, world, dev)
+    e2e_ms = max_over_ranks(1e3 * state["e2e_s"], world, dev)
     cnt = g.counters()
     log("timed, profiled, e2e and mixed runs done")
     # the adjoint and the many-scene batch are single-GPU figures: under
@@ -602,6 +694,7 @@ def run_abd(args, rank, world):
         "newton_iters_per_step": summ_all["newton_iters_per_step"],
         "pcg_iters_per_newton": summ_all["pcg_iters_per_newton"],
         "windows": per_window,
+        "windows_failed": failed,
         "e2e": {"value": e2e_ms / steps_total, "unit": "ms/step", "h2d_bytes_per_step": 2 * 12 * 8 * s.nb,
                 "d2h_bytes_per_step": 2 * 12 * 8 * s.nb},
         "gpu_launches": summ_all["kernel_launches"],
@@ -614,8 +707,9 @@ def run_abd(args, rank, world):
                     "iaabb_kept_frac": cnt["prim_pairs_iaabb"] / max(cnt["prim_pairs_body"], 1),
                     "candidates_frac_of_iaabb": cnt["prim_pairs_cand"] / max(cnt["prim_pairs_iaabb"], 1),
                     "scope": "every enumeration since the scene was created (advance, warm-up, timed, profiled "
-                             "and e2e steps)"},
-        "mixed": None if gm is None else {
+                             "and e2e steps)",
+                    "at_one_state": culling_state},
+        "mixed": None if gm is None or not mixed_ms else {
             "value": sum(mixed_ms) / len(mixed_ms), "unit": "ms/step",
             "precision": "FP32-stored Hessian blocks and FP32 inner PCG iterations with FP64 iterative refinement of "
                          "the linear residual; FP32 eigenbasis for the barrier Hessian projection; distances, "

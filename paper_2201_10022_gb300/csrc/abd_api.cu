@@ -700,6 +700,7 @@ abd_status abd_create_scene(const abd_scene_desc* d, const abd_params* prm, cons
     grow(s, s.isl, nb);
     grow(s, s.isl_state, 2L * nb);
     grow(s, s.isl_toi, nb);
+    grow(s, s.isl_step, nb);
     grow(s, s.isl_E, 16L * nb);
     grow(s, s.isl_alpha, nb);
     grow(s, s.Eb, 2L * nb);
@@ -869,6 +870,7 @@ void abd_destroy(abd_scene* S) {
   release(s, s.isl);
   release(s, s.isl_state);
   release(s, s.isl_toi);
+  release(s, s.isl_step);
   release(s, s.isl_E);
   release(s, s.isl_alpha);
   for (Buf<double>* b : {&s.q, &s.qdot, &s.qt, &s.qtilde, &s.dq, &s.qtrial, &s.qsave, &s.qdotsave, &s.gb, &s.g, &s.r,

@@ -232,7 +232,7 @@ struct Scene {
   // the iterate, then of the trial), line-search
   // state (accepted, halvings) and step
   Buf<int> uf, isl, isl_state;
-  Buf<unsigned long long> isl_toi, isl_E;
+  Buf<unsigned long long> isl_toi, isl_step, isl_E;
   Buf<double> isl_alpha;
 
   // PCG: residual, preconditioned residual, two alternating directions, H p,

@@ -148,10 +148,12 @@ __device__ __forceinline__ void fx_add(unsigned long long* base, int island, dou
 
 // ---- kernels ------------------------------------------------------------------
 // every body its own root; per-root island state cleared
-__global__ void k_isl_init(int nb, int* parent, unsigned long long* toi, unsigned long long* E, int* lstate) {
+__global__ void k_isl_init(int nb, int* parent, unsigned long long* toi, unsigned long long* step,
+                           unsigned long long* E, int* lstate) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
     parent[b] = b;
     toi[b] = 0x3ff0000000000000ull;  // bits of 1.0
+    step[b] = 0ull;
     for (int k = 0; k < 16; ++k) E[16L * b + k] = 0ull;
     lstate[2 * b] = 0;
     lstate[2 * b + 1] = 0;
@@ -230,14 +232,49 @@ __global__ void k_isl_energy(int which, int nb, const uint8_t* __restrict__ is_s
   }
 }
 
-// start of the line search: each island's step = its CCD bound
+// largest vertex step |J dq| of each island (the bits of non-negative
+// doubles order like the doubles; lanes of one island first take their
+// maximum together)
+__global__ void k_isl_step(int nv, const int* vbody, const uint8_t* is_static, const int* isl, const double4* dx,
+                           unsigned long long* step) {
+  for (int v0 = blockIdx.x * blockDim.x; v0 < nv; v0 += gridDim.x * blockDim.x) {
+    const int v = v0 + threadIdx.x;
+    bool on = v < nv;
+    int key = -1;
+    unsigned long long bits = 0ull;
+    if (on) {
+      const int b = vbody[v];
+      on = !is_static[b];
+      if (on) {
+        const double4 d = dx[v];
+        key = isl[b];
+        bits = (unsigned long long)__double_as_longlong(sqrt(d.x * d.x + d.y * d.y + d.z * d.z));
+      }
+    }
+    const unsigned act = __ballot_sync(kFull, on);
+    if (!on) continue;
+    const unsigned peers = __match_any_sync(act, key);
+    unsigned long long m = bits;
+    for (unsigned q = peers; q; q &= q - 1) {
+      const unsigned long long x = __shfl_sync(peers, bits, __ffs(q) - 1);
+      m = x > m ? x : m;
+    }
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(&step[key], m);
+  }
+}
+
+// start of the line search: each island's step = its CCD bound.  An island
+// whose Newton step is already within the tolerance (converged: the step is
+// a refinement inside the quadratic region) takes it, bounded by CCD,
+// without the energy test, which at that scale measures rounding only.
 __global__ void k_isl_start(int nb, const uint8_t* is_static, const int* isl, const unsigned long long* toi,
-                            double* alpha, int* lstate) {
+                            const unsigned long long* step, double tol, double* alpha, int* lstate) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
     if (is_static[b] || isl[b] != b) continue;
+    const bool done = __longlong_as_double((long long)step[b]) <= tol;
     alpha[b] = __longlong_as_double((long long)toi[b]);
-    lstate[2 * b] = 0;      // 0 pending, 1 accepted
-    lstate[2 * b + 1] = 0;  // halvings
+    lstate[2 * b] = done ? 1 : 0;  // 0 pending, 1 accepted
+    lstate[2 * b + 1] = 0;         // halvings
   }
 }
 
@@ -303,7 +340,7 @@ static int grid_n(long n, int t, int cap) {
 void launch_islands(Scene& s) {
   counted(s, 3);
   const int g = grid_n(s.nb, 256, sm_grid(s, 8));
-  k_isl_init<<<g, 256, 0, s.stream>>>(s.nb, s.uf.p, s.isl_toi.p, s.isl_E.p, s.isl_state.p);
+  k_isl_init<<<g, 256, 0, s.stream>>>(s.nb, s.uf.p, s.isl_toi.p, s.isl_step.p, s.isl_E.p, s.isl_state.p);
   k_isl_link<<<sm_grid(s, 4), 256, 0, s.stream>>>(s.st, s.P.p, s.fpairs.p, s.is_static.p, s.uf.p);
   k_isl_label<<<g, 256, 0, s.stream>>>(s.nb, s.uf.p, s.isl.p);
 }
@@ -316,9 +353,12 @@ void launch_island_energy(Scene& s, int which) {
 }
 
 void launch_island_start(Scene& s) {
-  counted(s);
-  k_isl_start<<<grid_n(s.nb, 256, sm_grid(s, 8)), 256, 0, s.stream>>>(s.nb, s.is_static.p, s.isl.p, s.isl_toi.p,
-                                                                       s.isl_alpha.p, s.isl_state.p);
+  counted(s, 2);
+  // the Newton step per island (dx of this iteration, labels of this swept list)
+  k_isl_step<<<grid_n(s.nv, 256, sm_grid(s, 8)), 256, 0, s.stream>>>(s.nv, s.vbody.p, s.is_static.p, s.isl.p,
+                                                                      s.dx.p, s.isl_step.p);
+  k_isl_start<<<grid_n(s.nb, 256, sm_grid(s, 8)), 256, 0, s.stream>>>(
+      s.nb, s.is_static.p, s.isl.p, s.isl_toi.p, s.isl_step.p, s.newton_tol, s.isl_alpha.p, s.isl_state.p);
 }
 
 void launch_island_trial(Scene& s) {

@@ -796,12 +796,27 @@ void launch_pcg_solve(Scene& s, double* xout, int max_iter, double rel_tol) {
 // entries in FP64, 4-byte in the mixed solve's inner iterations
 double pcg_iter_bytes(const Scene& s, long np) {
   const double e = s.pcg_mixed ? 4.0 : 8.0;
-  return e * 144.0 * (2.0 * s.nb + (double)np) + e * 12.0 * 8.0 * s.nb + 8.0 * np;
+  // the preconditioner's factors (packed lower triangles) or inverse blocks
+  double pre = 0.0;
+  const int* off = s.clu_host + s.nb;
+  for (int c = 0; c < s.nclu; ++c) {
+    const double n = off[c + 1] - off[c];
+    pre += n >= 2 ? 8.0 * (12.0 * n) * (12.0 * n + 1.0) / 2.0 : e * 144.0 * n;
+  }
+  return e * 144.0 * (s.nb + (double)np) + pre + e * 12.0 * 8.0 * s.nb + 8.0 * np;
 }
 double pcg_iter_flops(const Scene& s, long np) {
-  // block products: diagonal and inverse once, each off-diagonal block twice
-  // (as stored and transposed), 2 flops per entry; vector updates
-  return 2.0 * 144.0 * (2.0 * s.nb + 2.0 * (double)np) + 2.0 * 12.0 * 6.0 * s.nb;
+  // block products: the diagonal once and each off-diagonal block twice (as
+  // stored and transposed), 2 flops per entry; the preconditioner: a single
+  // body's inverse block (2 x 144), a cluster's two triangular solves
+  // (2 x N^2, N = 12 n); vector updates
+  double pre = 0.0;
+  const int* off = s.clu_host + s.nb;
+  for (int c = 0; c < s.nclu; ++c) {
+    const double n = off[c + 1] - off[c];
+    pre += n >= 2 ? 2.0 * (12.0 * n) * (12.0 * n) : 2.0 * 144.0 * n;
+  }
+  return 2.0 * 144.0 * (s.nb + 2.0 * (double)np) + pre + 2.0 * 12.0 * 6.0 * s.nb;
 }
 
 // status of the last solve: iterations (>= 0) if converged, -1 at the cap,

@@ -129,3 +129,75 @@ def test_unprojected_hessian_is_positive_definite_at_the_step():
     st, E, g = o.energy_grad_hess(states[2][0].reshape(-1), project=False)
     H = o.dense_hessian()
     assert np.linalg.eigvalsh(H).min() > 0
+
+
+def _contact_scene():
+    B = scenes._Builder("adjoint", 0)
+    gv, gt = scenes.box_mesh(2.0, 2.0, 0.4)
+    B.add(gv, gt, p=(0.0, 0.0, -0.2), static=True)
+    cv, ct = scenes.cube_mesh(0.2)
+    B.add(cv, ct, R=scenes.small_rotation(np.random.default_rng(1), 2.0), p=(0.0, 0.0, 0.1 + 0.0012),
+          v=(0.4, -0.2, 0.05), kappa=1e6)
+    B.add(cv, ct, p=(0.35, 0.0, 0.1 + 0.0012), v=(-0.3, 0.1, 0.0), kappa=2e6)
+    return B.build(dict(mu=0.0))
+
+
+def backward_projected(o, s, states, gq, gqd):
+    """the same chain with the PSD-projected Hessian (the one Newton uses)
+    in place of the true one: lam = H_proj^-1 rhs by numpy, M lam by the
+    oracle's mass matrices"""
+    dt = s.params["dt"]
+    dyn = np.nonzero(s.is_static == 0)[0]
+    idx = np.concatenate([np.arange(12 * b, 12 * b + 12) for b in dyn])
+    for t in range(len(states) - 2, -1, -1):
+        (qt, qdt), (qn, _) = states[t], states[t + 1]
+        o.set_state(qt, qdt)
+        st, _, _ = o.energy_grad_hess(qn.reshape(-1), project=True)
+        assert st == 0
+        H = o.dense_hessian()
+        rhs = (gq + gqd / dt).reshape(-1)
+        lam = np.zeros(12 * s.nb)
+        lam[idx] = np.linalg.solve(H[np.ix_(idx, idx)], rhs[idx])
+        Mlam = np.zeros_like(gq)
+        for b in dyn:
+            Mlam[b] = o.mass_matrix(b) @ lam[12 * b:12 * b + 12]
+        gq, gqd = Mlam - gqd / dt, dt * Mlam
+    gqd[s.is_static == 1] = 0.0
+    return gq, gqd
+
+
+def test_projected_hessian_adjoint_differs_from_the_implicit_function_one():
+    """The implicit-function theorem needs the true Hessian of the IP at the
+    converged step; the Newton loop uses its PSD projection.  Through an
+    active contact the two chains give different gradients: the unprojected
+    one matches central differences of the loss, the projected one is off
+    by more (its mismatch is the difference the adjoint would carry if it
+    reused Newton's Hessian)."""
+    s = _contact_scene()
+    target = np.array([0.3, -0.1, 0.2])
+    n = 4
+    o = O.Oracle(s, newton_rel=1e-14, newton_max=200)
+    states = rollout(o, s.q0.copy(), s.qdot0.copy(), n)
+    g0 = _dloss(states, s, target)
+    _, gqd_true, _ = backward(o, s, states, g0, np.zeros_like(s.q0))
+    _, gqd_proj = backward_projected(o, s, states, g0, np.zeros_like(s.q0))
+
+    def loss_at(qd0):
+        o2 = O.Oracle(s, newton_rel=1e-14, newton_max=200)
+        return _loss(rollout(o2, s.q0.copy(), qd0, n), s, target)
+
+    h = 1e-6
+    err_true, err_proj = [], []
+    for b, k in ((1, 0), (1, 2), (2, 0), (2, 1)):
+        e = np.zeros_like(s.qdot0)
+        e[b, k] = h
+        fd = (loss_at(s.qdot0 + e) - loss_at(s.qdot0 - e)) / (2 * h)
+        scale = max(abs(fd), 1e-9 * np.abs(gqd_true).max())
+        err_true.append(abs(gqd_true[b, k] - fd) / scale)
+        err_proj.append(abs(gqd_proj[b, k] - fd) / scale)
+    rel_diff = np.abs(gqd_true - gqd_proj).max() / np.abs(gqd_true).max()
+    print(f"adjoint through contact: unprojected vs central differences {max(err_true):.2e}, "
+          f"projected {max(err_proj):.2e}; projected vs unprojected gradient {rel_diff:.2e}")
+    assert max(err_true) <= 2e-4
+    assert rel_diff > 10 * max(err_true)
+    assert max(err_proj) > max(err_true)
