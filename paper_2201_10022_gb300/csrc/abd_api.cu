@@ -306,14 +306,16 @@ void eval_system(Scene& s, const double* q, int project, double* newton_x = null
 }
 
 // energy only at positions s.xt (from qv), over the stored candidates; the
-// body and friction terms run beside the pair energies
-void eval_energy(Scene& s, const double* qv) {
-  on_side(s, 0, 2, [&]() { launch_body_terms(s, qv, false); });
-  on_side(s, 1, 3, [&]() { launch_friction_eval(s, s.xt.p, false); });
-  launch_pair_energy(s, s.xt.p);
+// body and friction terms run beside the pair energies.  In the per-island
+// line search only the islands whose step is not yet accepted are evaluated
+// (their island sums are all that is read) and the scene totals are skipped.
+void eval_energy(Scene& s, const double* qv, bool line_search = false) {
+  on_side(s, 0, 2, [&]() { launch_body_terms(s, qv, false, true, line_search); });
+  on_side(s, 1, 3, [&]() { launch_friction_eval(s, s.xt.p, false, line_search); });
+  launch_pair_energy(s, s.xt.p, line_search);
   join_side(s, 0, 2);
   join_side(s, 1, 3);
-  launch_energy_total(s, false);
+  if (!line_search) launch_energy_total(s, false);
 }
 
 // lag friction at q^t: proximity pairs at x(q^t), one record per active pair
@@ -483,7 +485,7 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
       launch_island_start(s);
       launch_island_trial(s);
       launch_transform(s, s.qtrial.p, s.xt.p);
-      eval_energy(s, s.qtrial.p);
+      eval_energy(s, s.qtrial.p, true);
       launch_island_energy(s, 1);
       launch_island_accept(s);
       cudaMemcpyAsync(s.isl_host, s.isl.p, sizeof(int) * s.nb, cudaMemcpyDeviceToHost, s.stream);
@@ -531,7 +533,7 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
       if (s.st_host->flags & ST_INTERSECT) break;
       launch_island_trial(s);
       launch_transform(s, s.qtrial.p, s.xt.p);
-      eval_energy(s, s.qtrial.p);
+      eval_energy(s, s.qtrial.p, true);
       launch_island_energy(s, 1);
       launch_island_accept(s);
       read_status(s);

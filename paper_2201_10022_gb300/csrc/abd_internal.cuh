@@ -350,7 +350,9 @@ void launch_body_boxes(Scene& s, bool swept);
 void launch_body_pairs(Scene& s);                       // rows -> P (uses friction pairs)
 void launch_incoming(Scene& s);
 void launch_assemble(Scene& s);
-void launch_body_terms(Scene& s, const double* q, bool hess, bool project = true);
+// pending_only: line-search rounds, only the bodies / pairs / records of the
+// islands whose step is not yet accepted
+void launch_body_terms(Scene& s, const double* q, bool hess, bool project = true, bool pending_only = false);
 void launch_adjoint_rhs(Scene& s, const double* gq, const double* gqd, double* rhs);
 void launch_adjoint_out(Scene& s, const double* q, const double* lam, double* gq, double* gqd, double* gkappa);
 void launch_gather(Scene& s);
@@ -394,8 +396,8 @@ void launch_enumerate(Scene& s, bool swept, bool ccd);
 void launch_active(Scene& s, const double4* x);
 void launch_barrier(Scene& s, int project, long cap);
 void launch_friction_lag(Scene& s);
-void launch_friction_eval(Scene& s, const double4* x, bool derivs);
-void launch_pair_energy(Scene& s, const double4* x);   // energy only, over candidates
+void launch_friction_eval(Scene& s, const double4* x, bool derivs, bool pending_only = false);
+void launch_pair_energy(Scene& s, const double4* x, bool pending_only = false);  // energy only, over candidates
 
 // ---- launchers (k_island.cu) -------------------------------------------------
 void launch_islands(Scene& s);                 // labels of the current body-pair list

@@ -419,10 +419,13 @@ __global__ void k_friction_lag(DevStatus* cst, const int2* P, const int* aoff, c
 }
 
 __global__ void k_friction_eval(const DevStatus* __restrict__ cst, const FricRec* fr, const double4* x, double eps,
-                                double* fterm, int4* ftermv, bool derivs) {
+                                double* fterm, int4* ftermv, bool derivs, const uint8_t* is_static, const int* isl,
+                                const int* lstate) {
   const int nfr = cst->nfr;
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nfr; f += gridDim.x * blockDim.x) {
     const FricRec& R = fr[f];
+    // line-search rounds: records of islands already accepted are not needed
+    if (isl && lstate[2 * (is_static[R.a] ? isl[R.b] : isl[R.a])] != 0) continue;
     v3 xs[4];
     for (int m = 0; m < 4; ++m) xs[m] = mk(x[R.v[m]]);
     double* T = fterm + (size_t)f * kTermStride;
@@ -446,13 +449,18 @@ __global__ void k_friction_eval(const DevStatus* __restrict__ cst, const FricRec
 // slot (np x nch, summed later in a fixed order)
 __global__ void k_pair_energy(const DevStatus* __restrict__ cst, const int2* cand, const int* ccount,
                               const int* tri, const int* edge, const double4* x, const double* l2e, double dhat,
-                              double kappa, int maxc, int nch, double* Ep, DevStatus* st) {
+                              double kappa, int maxc, int nch, double* Ep, const int2* P, const uint8_t* is_static,
+                              const int* isl, const int* lstate, DevStatus* st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
   const long nw = (long)cst->np * nch;
   const double dh2 = __dmul_rn(dhat, dhat);
   for (long w = (long)blockIdx.x * (blockDim.x >> 5) + warp; w < nw; w += nwarps) {
     const int p = (int)(w / nch), c = (int)(w - (long)p * nch);
+    if (isl) {  // line-search rounds: pairs of islands already accepted are not needed
+      const int2 pr = P[p];
+      if (lstate[2 * (is_static[pr.x] ? isl[pr.y] : isl[pr.x])] != 0) continue;
+    }
     const int n = min(ccount[p], maxc);
     const int k = c * 32 + lane;
     double e = 0.0;
@@ -528,19 +536,22 @@ void launch_friction_lag(Scene& s) {
                                                s.fric.p);
 }
 
-void launch_friction_eval(Scene& s, const double4* x, bool derivs) {
+void launch_friction_eval(Scene& s, const double4* x, bool derivs, bool pending_only) {
   counted(s);
   ProfScope ps(s, PF_FRICTION);
   k_friction_eval<<<sm_grid(s, 4), 128, 0, s.stream>>>(s.st, s.fric.p, x, s.prm.eps_v * s.prm.dt, s.fterm.p,
-                                                s.ftermv.p, derivs);
+                                                s.ftermv.p, derivs, s.is_static.p,
+                                                pending_only ? s.isl.p : nullptr, s.isl_state.p);
 }
 
-void launch_pair_energy(Scene& s, const double4* x) {
+void launch_pair_energy(Scene& s, const double4* x, bool pending_only) {
   const int nch = energy_chunks(s);
   int grid = grid_for(2L * s.nb * nch, 8, sm_grid(s, 32));  // grid-stride over the device's pair count
   counted(s);
   k_pair_energy<<<grid, 256, 0, s.stream>>>(s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.l2e.p,
-                                            s.prm.dhat, s.prm.kappa, s.maxc, nch, s.Epair.p, s.st);
+                                            s.prm.dhat, s.prm.kappa, s.maxc, nch, s.Epair.p, s.P.p,
+                                            s.is_static.p, pending_only ? s.isl.p : nullptr, s.isl_state.p,
+                                            s.st);
 }
 
 }  // namespace abd

@@ -192,7 +192,8 @@ __global__ void k_isl_energy(int which, int nb, const uint8_t* __restrict__ is_s
                              const DevStatus* __restrict__ cst, const double* __restrict__ term,
                              const int4* __restrict__ termv, const double* __restrict__ Epair, int nch,
                              const int2* __restrict__ P, const double* __restrict__ fterm,
-                             const FricRec* __restrict__ fr, unsigned long long* E, DevStatus* st) {
+                             const FricRec* __restrict__ fr, const int* __restrict__ lstate,
+                             unsigned long long* E, DevStatus* st) {
   const long nbar = which == 0 ? (long)cst->nact : (long)cst->np * nch;
   const long nfr = cst->nfr;
   const long n = 2L * nb + nbar + nfr;
@@ -228,6 +229,8 @@ __global__ void k_isl_energy(int which, int nb, const uint8_t* __restrict__ is_s
         v = fterm[f * kTermStride];
       }
     }
+    // a trial's sums are read for the pending islands only
+    if (which == 1 && on && lstate[2 * key] != 0) on = false;
     fx_add(base, key, v, on, st);
   }
 }
@@ -349,7 +352,7 @@ void launch_island_energy(Scene& s, int which) {
   counted(s);
   k_isl_energy<<<sm_grid(s, 8), 256, 0, s.stream>>>(which, s.nb, s.is_static.p, s.isl.p, s.vbody.p, s.Eb.p, s.st,
                                                       s.term.p, s.termv.p, s.Epair.p, energy_chunks(s), s.P.p,
-                                                      s.fterm.p, s.fric.p, s.isl_E.p, s.st);
+                                                      s.fterm.p, s.fric.p, s.isl_state.p, s.isl_E.p, s.st);
 }
 
 void launch_island_start(Scene& s) {

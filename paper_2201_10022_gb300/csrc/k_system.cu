@@ -769,9 +769,11 @@ __global__ void __launch_bounds__(128) k_assemble(const DevStatus* __restrict__ 
 // ---------------------------------------------------------------------------
 __global__ void k_body_terms(int nb, const uint8_t* is_static, const double* q, const double* qtilde,
                              const double* mass10, const double* vol, const double* kappa_b, double dt, double* gb,
-                             double* Eb) {
+                             double* Eb, const int* isl, const int* lstate) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nb) return;
+  // line-search rounds: bodies of islands already accepted are not needed
+  if (isl && !is_static[b] && lstate[2 * isl[b]] != 0) return;
   if (is_static[b]) {
     for (int k = 0; k < 12; ++k) gb[12 * b + k] = 0.0;
     Eb[2 * b] = Eb[2 * b + 1] = 0.0;
@@ -1246,11 +1248,12 @@ void launch_assemble(Scene& s) {
                                             s.fterm.p, s.ftermv.p, s.vbody.p, s.xbar.p, s.pblk.p);
 }
 
-void launch_body_terms(Scene& s, const double* q, bool hess, bool project) {
+void launch_body_terms(Scene& s, const double* q, bool hess, bool project, bool pending_only) {
   counted(s);
   ProfScope pb(s, PF_BODY);
   k_body_terms<<<blocks(s.nb, 64), 64, 0, s.stream>>>(s.nb, s.is_static.p, q, s.qtilde.p, s.mass10.p, s.vol.p,
-                                                       s.kappa_b.p, s.prm.dt, s.gb.p, s.Eb.p);
+                                                       s.kappa_b.p, s.prm.dt, s.gb.p, s.Eb.p,
+                                                       pending_only ? s.isl.p : nullptr, s.isl_state.p);
   if (hess) {
     counted(s, 2);
     cudaMemsetAsync(reinterpret_cast<char*>(s.st) + offsetof(DevStatus, bh_fix), 0, sizeof(int), s.stream);

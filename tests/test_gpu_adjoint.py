@@ -138,12 +138,16 @@ def test_rollout_gradient_matches_central_differences(abd):
 
 def test_adjoint_steps_match_oracle_on_the_throw_stack(abd):
     """the adjoint workload itself (64 cubes thrown at a 10-cube stack, 74
-    dynamic bodies): four steps forward by the oracle (the stack's cubes
-    settle into contact from the third), then each step's adjoint on the
-    GPU (PCG with the cluster preconditioner) against the oracle's (dense
-    Cholesky), for a loss on the mean translation of every dynamic body"""
+    dynamic bodies): five steps forward by the oracle, then the adjoint of
+    the last two (the stack's cubes in contact, 60 and 68 active pairs) on
+    the GPU (PCG with the cluster preconditioner) against the oracle's (dense
+    Cholesky), for a loss on the mean translation of every dynamic body.
+    (At the third step, the first with contact, the unprojected Hessian of
+    the converged state has an eigenvalue of -0.05 against 5e5: there the
+    implicit-function Jacobian is not defined by a Cholesky solve, on either
+    side.)"""
     s = scenes.throw_stack(seed=4)
-    nsteps = 4
+    nsteps, nback = 5, 2
     dyn = s.is_static == 0
     o = O.Oracle(s, newton_max=300)
     o.set_state(s.q0, s.qdot0)
@@ -154,6 +158,7 @@ def test_adjoint_steps_match_oracle_on_the_throw_stack(abd):
         q, qd = o.get_state()
         states.append((q.copy(), qd.copy()))
     assert o.pairs(1)["kind"].size > 0  # contact at the last state
+    states = states[-(nback + 1):]
     g = np.zeros_like(s.q0)
     g[dyn, :3] = 2.0 * (states[-1][0][dyn, :3].mean(axis=0) - np.array([-0.5, 0.0, 0.25])) / dyn.sum()
     gq0, gqd0, gk0 = oracle_backward(o, s, states, g.copy(), np.zeros_like(s.q0))
@@ -162,7 +167,7 @@ def test_adjoint_steps_match_oracle_on_the_throw_stack(abd):
     gq = torch.tensor(g, device=dev)
     gqd = torch.zeros_like(gq)
     gk = torch.zeros(s.nb, dtype=torch.float64, device=dev)
-    for t in range(nsteps - 1, -1, -1):
+    for t in range(nback - 1, -1, -1):
         (qt, qdt), (qn, _) = states[t], states[t + 1]
         st = gpu.adjoint_step(qt, qdt, qn, gq, gqd, gk)
         assert st["rel_residual"] <= 1e-11
