@@ -98,7 +98,7 @@ def lib():
             "orc_grad_rows": (i, [vp, vp, i, vp, vp]),
             "orc_pairs_count": (l, [vp, i]), "orc_pairs_copy": (None, [vp, i, vp, vp, vp, vp, vp]),
             "orc_friction_copy": (None, [vp, vp, vp, vp]),
-            "orc_solve": (i, [vp, vp, vp, vp]), "orc_ccd_toi": (i, [vp, vp, vp, vp]),
+            "orc_solve": (i, [vp, vp, vp, vp]), "orc_ldl_solve": (i, [i, vp, vp, vp]), "orc_ccd_toi": (i, [vp, vp, vp, vp]),
             "orc_step": (i, [vp, i, vp]),
         }
         for name, (res, args) in sig.items():
@@ -193,6 +193,18 @@ def accd(kind, x12, dx12, s=0.1, tmax=1.0, max_iter=10000):
     t = np.zeros(1)
     st = lib().orc_accd(kind, _p(x), _p(dx), s, tmax, max_iter, _p(t))
     return t[0], st
+
+
+def ldl_solve(A, b):
+    """x = A^-1 b for a symmetric (possibly indefinite) A by the LDL^T
+    factorisation without pivoting used by the adjoint's dense solve;
+    returns (status, x), status -1 on a zero pivot"""
+    A = _f64(A)
+    n = A.shape[0]
+    b = _f64(b, n)
+    x = np.zeros(n)
+    r = lib().orc_ldl_solve(n, _p(A), _p(b), _p(x))
+    return r, x
 
 
 def closest_weights(kind, x12):

@@ -120,6 +120,9 @@ void orc_friction_copy(const orc_ctx* c, double* gamma, double* nrm, double* r);
 
 /* --- solve, CCD, step ------------------------------------------------------ */
 int orc_solve(orc_ctx* c, const double* rhs, double* dq, int* iters); /* H dq = rhs, last H */
+/* x = A^-1 b for a symmetric A (n x n, row-major) by A = L D L^T without
+ * pivoting (the adjoint's dense solve); -1 on a zero pivot */
+int orc_ldl_solve(int n, const double* A, const double* b, double* x);
 int orc_ccd_toi(orc_ctx* c, const double* q, const double* dq, double* toi);
 int orc_step(orc_ctx* c, int nsteps, orc_stats* st);
 

@@ -126,6 +126,62 @@ static void chol_solve(int n, const double* L, double* x) {
   }
 }
 
+/* Symmetric indefinite factorisation A = L D L^T, L unit lower triangular,
+ * D diagonal, without pivoting (exists when every leading principal minor is
+ * nonzero; Golub & Van Loan, Matrix Computations, Sec. 4.1, the LDL^T
+ * form).  Column j: v_k = L_jk d_k (k < j), d_j = a_jj - sum_k L_jk v_k,
+ * L_ij = (a_ij - sum_k L_ik v_k) / d_j.  L below the diagonal and D on it,
+ * in place.  Returns -1 on a zero or non-finite pivot. */
+static int ldl(int n, double* A) {
+  double* v = (double*)malloc(sizeof(double) * (n + 1));
+  int bad = 0;
+  for (int j = 0; j < n && !bad; ++j) {
+    double d = A[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) {
+      v[k] = A[(size_t)j * n + k] * A[(size_t)k * n + k];
+      d -= A[(size_t)j * n + k] * v[k];
+    }
+    if (!(fabs(d) > 0.0) || !isfinite(d)) {
+      bad = 1;
+      break;
+    }
+    A[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= A[(size_t)i * n + k] * v[k];
+      A[(size_t)i * n + j] = t / d;
+    }
+  }
+  free(v);
+  return bad ? -1 : 0;
+}
+
+/* L z = b, w = D^-1 z, L^T x = w, in place */
+static void ldl_solve(int n, const double* F, double* x) {
+  for (int i = 0; i < n; ++i) {
+    double s = x[i];
+    for (int k = 0; k < i; ++k) s -= F[(size_t)i * n + k] * x[k];
+    x[i] = s;
+  }
+  for (int i = 0; i < n; ++i) x[i] /= F[(size_t)i * n + i];
+  for (int i = n - 1; i >= 0; --i) {
+    double s = x[i];
+    for (int k = i + 1; k < n; ++k) s -= F[(size_t)k * n + i] * x[k];
+    x[i] = s;
+  }
+}
+
+/* exported for the tests: x = A^-1 b by ldl(); A is not modified */
+int orc_ldl_solve(int n, const double* A, const double* b, double* x) {
+  double* F = (double*)malloc(sizeof(double) * ((size_t)n * n + 1));
+  memcpy(F, A, sizeof(double) * (size_t)n * n);
+  memcpy(x, b, sizeof(double) * n);
+  int r = ldl(n, F);
+  if (r == 0) ldl_solve(n, F, x);
+  free(F);
+  return r;
+}
+
 /* ------------------------------------------------------------------------ */
 /* scene                                                                    */
 /* ------------------------------------------------------------------------ */
@@ -1189,7 +1245,10 @@ static void spmv(const orc_ctx* c, const double* v, double* y) {
   }
 }
 
-int orc_solve(orc_ctx* c, const double* rhs, double* dq, int* iters) {
+/* indefinite != 0: the dense branch factors by ldl() instead of chol() (the
+ * adjoint's unprojected Hessian, which may be indefinite at a converged
+ * state; the implicit function theorem needs it nonsingular only) */
+static int solve_system(orc_ctx* c, const double* rhs, double* dq, int* iters, int indefinite) {
   const orc_scene* s = &c->sc;
   int nb = s->nb;
   int* idx = (int*)malloc(sizeof(int) * nb);
@@ -1218,9 +1277,10 @@ int orc_solve(orc_ctx* c, const double* rhs, double* dq, int* iters) {
           A[(size_t)(12 * b + j) * n + 12 * a + i] = v;
         }
     }
-    if (chol(n, A) != 0) status = ORC_ERR_SOLVE;
+    if ((indefinite ? ldl(n, A) : chol(n, A)) != 0) status = ORC_ERR_SOLVE;
     else {
-      chol_solve(n, A, x);
+      if (indefinite) ldl_solve(n, A, x);
+      else chol_solve(n, A, x);
       for (int b = 0; b < nb; ++b)
         if (idx[b] >= 0)
           for (int i = 0; i < 12; ++i) dq[12 * b + i] = x[12 * idx[b] + i];
@@ -1296,6 +1356,8 @@ int orc_solve(orc_ctx* c, const double* rhs, double* dq, int* iters) {
   free(idx);
   return status;
 }
+
+int orc_solve(orc_ctx* c, const double* rhs, double* dq, int* iters) { return solve_system(c, rhs, dq, iters, 0); }
 
 /* ------------------------------------------------------------------------ */
 /* Sec. 4.1: step-size filter.  Swept candidates over x(q) -> x(q) + J dq,   */
@@ -1487,7 +1549,9 @@ int orc_step(orc_ctx* c, int nsteps, orc_stats* st) {
 /* dL/dq~ = M lam and dL/dkappa_b = -dt^2 lam_b . grad V_b / kappa_b.  The   */
 /* lagged friction quantities are held fixed (their dependence on q^t is     */
 /* not differentiated).  Returns M lam per body (zero rows for static        */
-/* bodies) and dL/dkappa per body.                                          */
+/* bodies) and dL/dkappa per body.  q^{t+1} is a stationary point of E,    */
+/* not always a minimiser (H can have a small negative eigenvalue there);    */
+/* the theorem needs H nonsingular only, so the dense solve is LDL^T.        */
 /* ------------------------------------------------------------------------ */
 int orc_adjoint_step(orc_ctx* c, const double* q_t, const double* qdot_t, const double* q_next, const double* rhs,
                      double* Mlam, double* gkappa) {
@@ -1500,7 +1564,7 @@ int orc_adjoint_step(orc_ctx* c, const double* q_t, const double* qdot_t, const 
   double* lam = (double*)calloc(12 * (size_t)nb, sizeof(double));
   st = orc_energy_grad_hess(c, q_next, E, g, 0);
   int iters = 0;
-  if (st == ORC_OK) st = orc_solve(c, rhs, lam, &iters);
+  if (st == ORC_OK) st = solve_system(c, rhs, lam, &iters, 1);
   const double dt2 = s->dt * s->dt;
   for (int b = 0; b < nb; ++b) {
     double* o = Mlam + 12 * b;

@@ -201,3 +201,66 @@ def test_projected_hessian_adjoint_differs_from_the_implicit_function_one():
     assert max(err_true) <= 2e-4
     assert rel_diff > 10 * max(err_true)
     assert max(err_proj) > max(err_true)
+
+
+def test_ldl_solve_matches_library_solve_on_indefinite_systems():
+    """the adjoint's dense factorisation A = L D L^T (no pivoting) against
+    numpy's LU solve: symmetric matrices with eigenvalues of both signs
+    (where Cholesky does not exist), an SPD matrix, and a zero leading
+    pivot reported as a failure"""
+    rng = np.random.default_rng(11)
+    for n, neg in ((12, 1), (48, 5), (97, 30)):
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        lam = rng.uniform(0.5, 4.0, n)
+        lam[:neg] *= -1.0
+        A = (Q * lam) @ Q.T
+        A = 0.5 * (A + A.T)
+        with pytest.raises(np.linalg.LinAlgError):
+            np.linalg.cholesky(A)
+        b = rng.standard_normal(n)
+        r, x = O.ldl_solve(A, b)
+        assert r == 0
+        ref = np.linalg.solve(A, b)
+        assert np.abs(x - ref).max() <= 1e-10 * np.abs(ref).max()
+        assert np.abs(A @ x - b).max() <= 1e-12 * np.abs(A).max() * np.abs(x).max() * n
+    B = rng.standard_normal((30, 30))
+    A = B @ B.T + 30 * np.eye(30)
+    b = rng.standard_normal(30)
+    r, x = O.ldl_solve(A, b)
+    assert r == 0 and np.allclose(x, np.linalg.solve(A, b), rtol=1e-12, atol=0)
+    r, _ = O.ldl_solve(np.array([[0.0, 1.0], [1.0, 0.0]]), np.ones(2))
+    assert r == -1
+
+
+def test_adjoint_at_an_indefinite_converged_state():
+    """the throw-into-stack workload at its first contact step: Newton's
+    stationary point is not a minimiser of the IP there (the unprojected
+    Hessian has a negative eigenvalue), yet nonsingular, so the implicit
+    function theorem applies; the oracle's adjoint solves with that exact
+    Hessian (M lam with lam = H^-1 rhs by numpy's LU on the oracle's own
+    unprojected matrix)"""
+    s = scenes.throw_stack(seed=4)
+    o = O.Oracle(s, newton_max=300)
+    states = rollout(o, s.q0.copy(), s.qdot0.copy(), 3)
+    (qt, qdt), (qn, _) = states[2], states[3]
+    o.set_state(qt, qdt)
+    st, _, _ = o.energy_grad_hess(qn.reshape(-1), project=False)
+    assert st == 0
+    dyn = np.nonzero(s.is_static == 0)[0]
+    idx = np.concatenate([np.arange(12 * b, 12 * b + 12) for b in dyn])
+    H = o.dense_hessian()[np.ix_(idx, idx)]
+    ev = np.linalg.eigvalsh(H)
+    assert ev.min() < 0.0 < ev.max()
+    assert np.abs(ev).min() > 1e-12 * ev.max()
+    rhs = np.zeros_like(s.q0)
+    rhs[dyn, :3] = np.random.default_rng(2).standard_normal((dyn.size, 3))
+    st, Mlam, _ = o.adjoint_step(qt, qdt, qn, rhs)
+    assert st == 0, O.ERRORS[st]
+    lam = np.zeros(12 * s.nb)
+    lam[idx] = np.linalg.solve(H, rhs.reshape(-1)[idx])
+    ref = np.zeros_like(s.q0)
+    for b in dyn:
+        ref[b] = o.mass_matrix(b) @ lam[12 * b:12 * b + 12]
+    # cond(H) = 5e5 / 0.027 ~ 2e7: eps * cond ~ 4e-9 bounds the difference of
+    # two backward-stable solves
+    assert np.abs(Mlam - ref).max() <= 1e-8 * np.abs(ref).max()
