@@ -79,6 +79,7 @@ void size_pair_buffers(Scene& s, size_t pcap) {
   if (s.prm.precision == 1) grow(s, s.H32, pcap * 144);
   grow(s, s.posbuf, pcap + 1);
   grow(s, s.Epair, pcap * (size_t)energy_chunks(s));
+  grow(s, s.ework, pcap * (size_t)energy_chunks(s));
   grow(s, s.cand, pcap * (size_t)s.maxc);
   grow(s, s.act, pcap * (size_t)s.maxc);
   grow(s, s.act_d2, pcap * (size_t)s.maxc);
@@ -179,6 +180,15 @@ abd_status check_cuda(Scene& s) {
 // kClusterMax bodies, so that a cluster is a compact piece of the contact
 // graph (a stack of bodies rather than a row of neighbours).  Deterministic;
 // uploaded with the cluster count; the factor pool grows when needed.
+// the body pairs of the current list to the host (after a synchronisation:
+// s.st_host holds their count); build_clusters_host uses them and the island
+// labels in s.isl_host
+void fetch_pairs_host(Scene& s) {
+  const long np = std::max(0, s.st_host->np);
+  s.pairs_host.resize(np);
+  if (np) cudaMemcpy(s.pairs_host.data(), s.P.p, sizeof(int2) * np, cudaMemcpyDeviceToHost);
+}
+
 void build_clusters_host(Scene& s) {
   const int nb = s.nb;
   int* perm = s.clu_host;
@@ -187,9 +197,6 @@ void build_clusters_host(Scene& s) {
   int* loc = cof + nb;
   int* ncl = loc + nb;
   long long* foff = reinterpret_cast<long long*>(s.clu_host + 4 * nb + 2);
-  const long np = std::max(0, s.st_host->np);
-  s.pairs_host.resize(np);
-  if (np) cudaMemcpy(s.pairs_host.data(), s.P.p, sizeof(int2) * np, cudaMemcpyDeviceToHost);
   // adjacency of the dynamic bodies (pair order)
   std::vector<int> deg(nb + 1, 0), adj;
   for (const int2& e : s.pairs_host)
@@ -266,6 +273,7 @@ void prepare_clusters(Scene& s) {
   cudaMemcpyAsync(s.isl_host, s.isl.p, sizeof(int) * s.nb, cudaMemcpyDeviceToHost, s.stream);
   cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
   cudaStreamSynchronize(s.stream);
+  fetch_pairs_host(s);
   build_clusters_host(s);
 }
 
@@ -285,7 +293,10 @@ void broad_and_enumerate(Scene& s, bool swept, bool ccd) {
 // the body terms and the incoming-pair lists (which need only q and the
 // body pairs) and the friction terms (only x) run beside the active set and
 // the barrier terms, and join before the assembly
-void eval_system(Scene& s, const double* q, int project, double* newton_x = nullptr) {
+// head: everything up to the assembled blocks and the gathered gradient;
+// tail: the preconditioner (with the PCG's start when newton_x is given) and
+// the energy total.  eval_system runs both.
+void eval_system_head(Scene& s, const double* q, int project) {
   on_side(s, 0, 0, [&]() {
     launch_body_terms(s, q, true, project != 0);
     launch_incoming(s);
@@ -298,11 +309,19 @@ void eval_system(Scene& s, const double* q, int project, double* newton_x = null
   join_side(s, 1, 1);
   launch_assemble(s);
   launch_gather(s);
+}
+
+void eval_system_tail(Scene& s, double* newton_x) {
   if (newton_x)  // and the PCG's start on H dx = -g
     launch_precond_start(s, newton_x);
   else
     launch_precond(s);
   launch_energy_total(s, true);
+}
+
+void eval_system(Scene& s, const double* q, int project, double* newton_x = nullptr) {
+  eval_system_head(s, q, project);
+  eval_system_tail(s, newton_x);
 }
 
 // energy only at positions s.xt (from qv), over the stored candidates; the
@@ -371,12 +390,17 @@ long cand_total(Scene& s) { return s.cand_last; }
 // Run a fixed launch sequence: as a CUDA graph (captured on a private stream
 // the first time and after any buffer reallocation, then replayed on the
 // scene's stream), or directly while profiling or if capture is unavailable.
-// The sequence must not read device results on the host.
-template <typename F>
-void run_segment(Scene& s, Scene::Segment& g, F body) {
+// The sequence must not read device results on the host.  A sequence may hold
+// one device-side while loop: the body calls loop_node() where it goes, and
+// loop() enqueues one pass of the loop's body, ending with the launch that
+// sets the loop's condition (Scene::Segment::loop_cond).  Returns true if the
+// loop ran on the device; otherwise (direct launches, or graph conditionals
+// unavailable) the caller runs it from the host.
+template <typename F, typename L>
+bool run_segment_loop(Scene& s, Scene::Segment& g, F body, L loop) {
   if (!s.graphs || s.prof.on) {
     body();
-    return;
+    return false;
   }
   if (!g.exec || g.gen != s.gen) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -385,33 +409,110 @@ void run_segment(Scene& s, Scene::Segment& g, F body) {
       cudaGetLastError();
       s.graphs = false;
       body();
-      return;
+      return false;
     }
     cudaStream_t user = s.stream;
     const long n0 = s.nlaunch;
     cudaGraph_t gr = nullptr;
+    g.has_loop = false;
+    g.loop_body = nullptr;
+    g.loop_nlaunch = 0;
     bool ok = cudaStreamBeginCapture(s.cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
       s.stream = s.cap_stream;
+      s.capturing = &g;
       body();
+      s.capturing = nullptr;
       s.stream = user;
       ok = cudaStreamEndCapture(s.cap_stream, &gr) == cudaSuccess && gr;
     }
     g.nlaunch = s.nlaunch - n0;
+    // the loop's body, captured into the conditional node's body graph
+    if (ok && g.has_loop) {
+      ok = cudaStreamBeginCaptureToGraph(s.cap_stream, g.loop_body, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        const long n1 = s.nlaunch;
+        s.stream = s.cap_stream;
+        loop();
+        s.stream = user;
+        cudaGraph_t lb = nullptr;
+        ok = cudaStreamEndCapture(s.cap_stream, &lb) == cudaSuccess;
+        g.loop_nlaunch = s.nlaunch - n1;
+      }
+    }
     s.nlaunch = n0;
     if (ok) ok = cudaGraphInstantiate(&g.exec, gr, 0) == cudaSuccess;
     if (gr) cudaGraphDestroy(gr);
-    if (!ok) {  // nothing of the captured body ran: run it directly from now on
+    if (!ok) {  // nothing of the captured body ran
       cudaGetLastError();
       g.exec = nullptr;
-      s.graphs = false;
+      if (g.has_loop && s.loop_graphs) {  // again without the device-side loop
+        s.loop_graphs = false;
+        g.has_loop = false;
+        return run_segment_loop(s, g, body, loop);
+      }
+      s.graphs = false;  // run it directly from now on
       body();
-      return;
+      return false;
     }
     g.gen = s.gen;
   }
   cudaGraphLaunch(g.exec, s.stream);
   s.nlaunch += g.nlaunch;
+  return g.has_loop;
+}
+
+template <typename F>
+void run_segment(Scene& s, Scene::Segment& g, F body) {
+  run_segment_loop(s, g, body, []() {});
+}
+
+// Inside a segment's body while it is captured: a while-loop node at this
+// point of the sequence, entered while the condition (set by a launch just
+// before it, and by the last launch of each pass) is non-zero.  Outside a
+// capture, or if graph conditionals are unavailable, nothing: the caller's
+// host loop runs the passes.
+void loop_node(Scene& s, int max_rounds) {
+  Scene::Segment* g = s.capturing;
+  if (!g || !s.loop_graphs) return;
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t G = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  cudaGraphConditionalHandle h;
+  if (cudaStreamGetCaptureInfo(s.stream, &cs, nullptr, &G, &deps, &ed, &nd) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusActive || cudaGraphConditionalHandleCreate(&h, G, 0, 0) != cudaSuccess) {
+    cudaGetLastError();
+    s.loop_graphs = false;
+    return;
+  }
+  launch_ls_condition(s, h, max_rounds, true);
+  // zero-initialised parameter block (the struct's default constructor is
+  // deleted: it holds a union of node kinds)
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if (cudaStreamGetCaptureInfo(s.stream, &cs, nullptr, &G, &deps, &ed, &nd) != cudaSuccess ||
+      cudaGraphAddNode(&node, G, deps, ed, nd, &np) != cudaSuccess ||
+      cudaStreamUpdateCaptureDependencies(s.stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+          cudaSuccess) {
+    // the capture is left invalid: its end fails and the segment is built
+    // again without the loop
+    cudaGetLastError();
+    g->has_loop = true;
+    g->loop_body = nullptr;
+    return;
+  }
+  g->has_loop = true;
+  g->loop_cond = h;
+  g->loop_body = np.conditional.phGraph_out[0];
 }
 
 // one implicit-Euler step from (q^t, qdot^t); on error the state is unchanged
@@ -424,6 +525,7 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
   launch_transform(s, s.q.p, s.x.p);
   broad_and_enumerate(s, false, false);
   prepare_clusters(s);  // the clusters of the first system
+  bool clusters_due = false;
   read_status(s);
   s.cand_last = (long)s.st_host->n_cand;
   s.last_np = s.st_host->np;
@@ -440,14 +542,25 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
     // back at its end also carries the system's flags and energies, checked
     // before the direction is used (every kernel bounds its work by the
     // clamped counts, so an overflowed system is only discarded)
-    run_segment(s, s.seg_sys[s.fp32_proj ? 1 : 0], [&]() {
+    const int pv = s.fp32_proj ? 1 : 0;
+    run_segment(s, s.seg_head[pv], [&]() {
       launch_transform(s, s.q.p, s.x.p);
+      eval_system_head(s, s.q.p, 1);
+    });
+    // the clusters of the last swept pair list, built on the host while the
+    // head runs (the head reads none of the cluster buffers; their uploads
+    // are queued behind it)
+    if (clusters_due) {
+      build_clusters_host(s);
+      clusters_due = false;
+    }
+    run_segment(s, s.seg_tail[pv], [&]() {
       if (s.dense_n) {
-        eval_system(s, s.q.p, 1);
+        eval_system_tail(s, nullptr);
         launch_negate(s, s.g.p, s.qsave.p, 12L * s.nb);
         launch_dense_solve(s, s.qsave.p, s.dq.p);
       } else {
-        eval_system(s, s.q.p, 1, s.dq.p);
+        eval_system_tail(s, s.dq.p);
         launch_pcg_solve(s, s.dq.p, s.prm.pcg_max, s.prm.pcg_rel_tol);
       }
       cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
@@ -470,7 +583,19 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
     // step length for the convergence test, then (in the same batch) the CCD
     // bound over the swept candidates and the first trial at alpha = bound;
     // the swept candidates also serve the next iteration
-    run_segment(s, s.seg_trial, [&]() {
+    // the halving rounds of the line search, while any island is pending:
+    // on the device (a while loop in the segment's graph) or from the host
+    const int max_rounds = s.prm.ls_max + 2;
+    auto ls_round = [&](bool device) {
+      if (device) launch_ls_round_begin(s);
+      launch_island_trial(s);
+      launch_transform(s, s.qtrial.p, s.xt.p);
+      eval_energy(s, s.qtrial.p, true);
+      launch_island_energy(s, 1);
+      launch_island_accept(s, !device);
+      if (device) launch_ls_condition(s, s.seg_trial.loop_cond, max_rounds, false);
+    };
+    const bool device_ls = run_segment_loop(s, s.seg_trial, [&]() {
       launch_transform_dq(s, s.dq.p);
       cudaMemsetAsync(&s.st->step_bits, 0, sizeof(unsigned long long), s.stream);
       // the step length beside the broad phase; eval_energy's join of side
@@ -478,6 +603,7 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
       on_side(s, 0, 0, [&]() { launch_max_step(s); });
       launch_reset_toi(s);
       broad_and_enumerate(s, true, true);
+      launch_energy_worklist(s);
       // per contact island: E at q from the system's terms (before the
       // trial's energy pass overwrites the body and friction energies), the
       // step = the island's CCD bound, the first trial and its acceptance
@@ -488,13 +614,19 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
       eval_energy(s, s.qtrial.p, true);
       launch_island_energy(s, 1);
       launch_island_accept(s);
+      loop_node(s, max_rounds);
       cudaMemcpyAsync(s.isl_host, s.isl.p, sizeof(int) * s.nb, cudaMemcpyDeviceToHost, s.stream);
       cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
-    });
+    }, [&]() { ls_round(true); });
     cudaStreamSynchronize(s.stream);
+    if (device_ls) {
+      loc.ls_halvings += s.st_host->ls_rounds;
+      s.nlaunch += s.seg_trial.loop_nlaunch * s.st_host->ls_rounds;
+    }
     // the islands of this swept pair list are those of the next system:
-    // its preconditioner clusters
-    build_clusters_host(s);
+    // its preconditioner clusters (built during the next system's head)
+    fetch_pairs_host(s);
+    clusters_due = true;
     double step = bits_to_double(s.st_host->step_bits);
     loc.last_step = step;
     if (!(step == step)) {
@@ -528,14 +660,11 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
     }
     loc.n_islands = s.st_host->n_islands;
     // line search per island: E_i(q + alpha_i dq) <= E_i(q) + slack; islands
-    // that fail halve their own step and are tried again
+    // that fail halve their own step and are tried again (the rounds the
+    // device-side loop left, if any)
     for (int round = 0; s.st_host->ls_pending > 0 && !s.st_host->ls_failed; ++round) {
       if (s.st_host->flags & ST_INTERSECT) break;
-      launch_island_trial(s);
-      launch_transform(s, s.qtrial.p, s.xt.p);
-      eval_energy(s, s.qtrial.p, true);
-      launch_island_energy(s, 1);
-      launch_island_accept(s);
+      ls_round(false);
       read_status(s);
       loc.ls_halvings++;
     }
@@ -837,7 +966,7 @@ void abd_destroy(abd_scene* S) {
   if (!S) return;
   Scene& s = S->s;
   if (s.stream || s.st) cudaStreamSynchronize(s.stream);
-  for (Scene::Segment* g : {&s.seg_sys[0], &s.seg_sys[1], &s.seg_trial})
+  for (Scene::Segment* g : {&s.seg_head[0], &s.seg_head[1], &s.seg_tail[0], &s.seg_tail[1], &s.seg_trial})
     if (g->exec) cudaGraphExecDestroy(g->exec);
   if (s.cap_stream) cudaStreamDestroy(s.cap_stream);
   for (cudaStream_t x : s.side)
@@ -882,7 +1011,7 @@ void abd_destroy(abd_scene* S) {
   for (Buf<double4>* b : {&s.x, &s.dx, &s.x1, &s.xt}) release(s, *b);
   for (Buf<int>* b : {&s.nbr, &s.ncount, &s.rowoff, &s.in_off, &s.in_cnt, &s.in_list, &s.ccount, &s.acount, &s.aoff,
                       &s.fpoff, &s.flagbuf, &s.posbuf, &s.hcount, &s.hoff, &s.large, &s.large_pos, &s.large_list,
-                      &s.slot_cnt, &s.slot_off, &s.entries})
+                      &s.slot_cnt, &s.slot_off, &s.entries, &s.ework})
     release(s, *b);
   release(s, s.P);
   release(s, s.fpairs);
@@ -1319,7 +1448,9 @@ abd_status abd_adjoint_step(abd_scene* S, const double* q_t, const double* qdot_
   launch_adjoint_rhs(s, gq, gqdot, s.qsave.p);
   double rel;
   s.pcg_mixed = false;  // the adjoint's solves stay FP64
-  const int its = run_pcg(s, s.qsave.p, s.dq.p, s.prm.pcg_max, rel_tol, &rel);
+  // the unprojected Hessian may be indefinite at the converged state: the
+  // dense solve takes signed pivots; the PCG reports a breakdown there
+  const int its = run_pcg(s, s.qsave.p, s.dq.p, s.prm.pcg_max, rel_tol, &rel, true);
   launch_adjoint_out(s, q_next, s.dq.p, gq, gqdot, gkappa);
   cudaStreamSynchronize(s.stream);
   if (stats) {
@@ -1328,7 +1459,8 @@ abd_status abd_adjoint_step(abd_scene* S, const double* q_t, const double* qdot_
   }
   if (abd_status c = check_cuda(s)) return c;
   if (its == -2) {
-    s.err = "PCG breakdown (Hessian not positive definite along the iterates)";
+    s.err = s.dense_n ? "dense adjoint solve: zero or non-finite pivot (singular Hessian)"
+                      : "PCG breakdown (Hessian not positive definite along the iterates)";
     return ABD_ERR_PCG_BREAKDOWN;
   }
   if (its == -1) {

@@ -62,6 +62,8 @@ struct DevStatus {
   int ls_pending, n_islands, ls_failed, ls_halv_max;
   int n_clusters;               // preconditioner clusters of the current body-pair list
   int clu_fail;                 // clusters whose Cholesky factorisation failed (block-Jacobi used)
+  int ls_rounds;                // halving rounds run by the device-side line-search loop
+  int n_ework;                  // entries of the (body pair, chunk) work list
 };
 
 // ---- small device helpers shared by the kernel files -----------------------
@@ -150,11 +152,23 @@ struct Scene {
     cudaGraphExec_t exec = nullptr;
     long gen = -1;
     long nlaunch = 0;
+    // a device-side while loop inside the segment (the line search's
+    // halving rounds): its condition, its body graph while the segment is
+    // being built, the launches of one pass of the body
+    bool has_loop = false;
+    cudaGraphConditionalHandle loop_cond = 0;
+    cudaGraph_t loop_body = nullptr;
+    long loop_nlaunch = 0;
   };
+  Segment* capturing = nullptr;  // the segment being captured (run_segment)
+  bool loop_graphs = true;       // device-side loops inside segments (off after a failed build)
   long gen = 0;  // bumped on every buffer (re)allocation
   bool graphs = true;
   cudaStream_t cap_stream = nullptr;
-  Segment seg_sys[2], seg_trial;
+  // per Newton iteration: the system up to the assembled blocks (head), the
+  // preconditioner and the PCG solve (tail; the host builds the clusters
+  // while the head runs), the trial step and line search
+  Segment seg_head[2], seg_tail[2], seg_trial;
   Alloc alloc;
   cudaStream_t stream = nullptr;
   // two side streams for the independent branches of a Newton iteration
@@ -210,6 +224,7 @@ struct Scene {
   Buf<double> fterm;   // friction terms
   Buf<int4> ftermv;
   Buf<double> Epair;   // energy-only pass: barrier energy per (body pair, chunk of 32 candidates)
+  Buf<int> ework;      // the (body pair, chunk) slots p * chunks + c that hold candidates (line search)
 
   // friction
   Buf<FricRec> fric;
@@ -367,7 +382,10 @@ void launch_pcg_init(Scene& s, const double* rhs, double sign, double* xout);
 void launch_pcg_solve(Scene& s, double* xout, int max_iter, double rel_tol);
 int pcg_result(Scene& s, double* rel_res);
 void pcg_account(Scene& s, int its);
-int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res);
+// indefinite: the dense branch factors by signed Cholesky (the adjoint's
+// unprojected system); the PCG branch is unchanged
+int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res,
+            bool indefinite = false);
 void launch_pcg_fp32_blocks(Scene& s);  // mixed precision: FP32 copies of the blocks
 // factors of the preconditioner clusters (after the assembly)
 void launch_cluster_factor(Scene& s);
@@ -377,7 +395,8 @@ double pcg_iter_flops(const Scene& s, long np);
 // dense direct solve (small scenes): order of the padded matrix, 0 if off
 constexpr int kDenseMaxOrder = 3072;
 int dense_order(int nb, int max_dofs);
-void launch_dense_solve(Scene& s, const double* rhs, double* x);
+// indefinite: signed Cholesky (negative pivots accepted), for the adjoint
+void launch_dense_solve(Scene& s, const double* rhs, double* x, bool indefinite = false);
 // the preconditioner (inverse diagonal blocks), then the PCG start on H dx = -g
 void launch_precond_start(Scene& s, double* xout);
 void launch_reset_toi(Scene& s);
@@ -398,12 +417,22 @@ void launch_barrier(Scene& s, int project, long cap);
 void launch_friction_lag(Scene& s);
 void launch_friction_eval(Scene& s, const double4* x, bool derivs, bool pending_only = false);
 void launch_pair_energy(Scene& s, const double4* x, bool pending_only = false);  // energy only, over candidates
+// the (body pair, chunk) slots that hold candidates, for the line search's
+// energy passes (after an enumeration)
+void launch_energy_worklist(Scene& s);
 
 // ---- launchers (k_island.cu) -------------------------------------------------
 void launch_islands(Scene& s);                 // labels of the current body-pair list
 void launch_island_energy(Scene& s, int which); // 0: E at the iterate from the terms; 1: the trial's
 void launch_island_start(Scene& s);            // each island's step = its CCD bound
 void launch_island_trial(Scene& s);            // qtrial = q + alpha_island dq
-void launch_island_accept(Scene& s);           // accept or halve each pending island
+// accept or halve each pending island; reset: clear the counts first (else a
+// preceding launch_ls_round_begin has)
+void launch_island_accept(Scene& s, bool reset = true);
+void launch_ls_round_begin(Scene& s);          // clear the counts, count the round
+// sets the loop condition: islands pending, none failed, no zero distance,
+// fewer than max_rounds rounds; first: the evaluation before the loop (clears
+// the round count)
+void launch_ls_condition(Scene& s, cudaGraphConditionalHandle h, int max_rounds, bool first);
 
 }  // namespace abd

@@ -447,15 +447,19 @@ __global__ void k_friction_eval(const DevStatus* __restrict__ cst, const FricRec
 // pair, chunk of 32 candidates) so that a body pair with many candidates is
 // spread over several warps; each warp writes its partial sum to its own
 // slot (np x nch, summed later in a fixed order)
+//
+// With a work list (the line search), only the slots that hold candidates are
+// visited (ework[0 .. n_ework)); the other slots are neither read nor written.
 __global__ void k_pair_energy(const DevStatus* __restrict__ cst, const int2* cand, const int* ccount,
                               const int* tri, const int* edge, const double4* x, const double* l2e, double dhat,
                               double kappa, int maxc, int nch, double* Ep, const int2* P, const uint8_t* is_static,
-                              const int* isl, const int* lstate, DevStatus* st) {
+                              const int* isl, const int* lstate, const int* ework, DevStatus* st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
-  const long nw = (long)cst->np * nch;
+  const long nw = ework ? (long)cst->n_ework : (long)cst->np * nch;
   const double dh2 = __dmul_rn(dhat, dhat);
-  for (long w = (long)blockIdx.x * (blockDim.x >> 5) + warp; w < nw; w += nwarps) {
+  for (long t = (long)blockIdx.x * (blockDim.x >> 5) + warp; t < nw; t += nwarps) {
+    const long w = ework ? (long)ework[t] : t;
     const int p = (int)(w / nch), c = (int)(w - (long)p * nch);
     if (isl) {  // line-search rounds: pairs of islands already accepted are not needed
       const int2 pr = P[p];
@@ -488,6 +492,20 @@ __global__ void k_pair_energy(const DevStatus* __restrict__ cst, const int2* can
     if (c * 32 < n)
       for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(kFull, e, o);
     if (lane == 0) Ep[w] = e;
+  }
+}
+
+// the (body pair, chunk) slots holding candidates: ceil(min(count, maxc) / 32)
+// per body pair, appended in any order (every slot's energy lands in its own
+// place and the island sums are exact, so the order is immaterial)
+__global__ void k_energy_worklist(const DevStatus* __restrict__ cst, const int* __restrict__ ccount, int maxc,
+                                  int nch, int* ework, DevStatus* st) {
+  const int np = cst->np;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+    const int nc = (min(ccount[p], maxc) + 31) / 32;
+    if (nc == 0) continue;
+    const int base = atomicAdd(&st->n_ework, nc);
+    for (int c = 0; c < nc; ++c) ework[base + c] = p * nch + c;
   }
 }
 
@@ -551,7 +569,14 @@ void launch_pair_energy(Scene& s, const double4* x, bool pending_only) {
   k_pair_energy<<<grid, 256, 0, s.stream>>>(s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.l2e.p,
                                             s.prm.dhat, s.prm.kappa, s.maxc, nch, s.Epair.p, s.P.p,
                                             s.is_static.p, pending_only ? s.isl.p : nullptr, s.isl_state.p,
-                                            s.st);
+                                            pending_only ? s.ework.p : nullptr, s.st);
+}
+
+void launch_energy_worklist(Scene& s) {
+  counted(s, 2);
+  cudaMemsetAsync(&s.st->n_ework, 0, sizeof(int), s.stream);
+  k_energy_worklist<<<grid_for(2L * s.nb, 256, sm_grid(s, 8)), 256, 0, s.stream>>>(s.st, s.ccount.p, s.maxc,
+                                                                                   energy_chunks(s), s.ework.p, s.st);
 }
 
 }  // namespace abd

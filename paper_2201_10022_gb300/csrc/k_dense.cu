@@ -9,6 +9,16 @@
 // substitute (Sec. 5) where the PCG needs many iterations (stacks: long
 // chains of stiff contacts).  A non-positive pivot marks the solve as a
 // breakdown in the status word (scal[6] = 2), like the PCG's.
+//
+// The adjoint's unprojected Hessian may be indefinite at a converged state
+// (a stationary point need not be a minimiser; the implicit function theorem
+// wants it nonsingular only).  For it the factorisation is the signed
+// Cholesky A = L S L^T, S = diag(s_j), s_j = sign of the j-th pivot, without
+// pivoting (the LDL^T factorisation with D = L_jj^2 S); then only a zero or
+// non-finite pivot is a breakdown.  dinv holds s_j / L_jj, positive
+// throughout for the Newton system.
+#include <cfloat>
+
 #include "abd_internal.cuh"
 
 namespace abd {
@@ -40,13 +50,15 @@ __global__ void k_dense_fill(int nb, int N, const uint8_t* is_static, const doub
   }
 }
 
-// Cholesky of the diagonal tile k (lower factor in place; 1 / L_jj in dinv).
-// Warp c holds column c of the tile, lane r its row r (the tile is staged
-// transposed): every step's column scaling and rank-1 update are whole-warp
-// instructions, and the pivot's reciprocal square root is one lane's work
-__global__ void __launch_bounds__(1024) k_dense_potrf(double* A, int N, int k, double* dinv, DevStatus* st) {
+// Cholesky of the diagonal tile k (lower factor in place; s_j / L_jj in
+// dinv).  Warp c holds column c of the tile, lane r its row r (the tile is
+// staged transposed): every step's column scaling and rank-1 update are
+// whole-warp instructions, and the pivot's reciprocal square root is one
+// lane's work.  indefinite != 0 accepts negative pivots (signed Cholesky)
+__global__ void __launch_bounds__(1024) k_dense_potrf(double* A, int N, int k, double* dinv, DevStatus* st,
+                                                      int indefinite) {
   __shared__ double T[kT][kT + 1];  // T[c][r] = A(o + r, o + c)
-  __shared__ double inv;
+  __shared__ double inv, sgn;
   __shared__ int bad;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const long o = (long)kT * k;
@@ -55,27 +67,33 @@ __global__ void __launch_bounds__(1024) k_dense_potrf(double* A, int N, int k, d
   __syncthreads();
   for (int j = 0; j < kT; ++j) {
     if (t == 0) {
-      double d = T[j][j];
-      if (!(d > 0.0)) {
+      double d = T[j][j], sj = 1.0;
+      if (indefinite && d < 0.0) {
+        d = -d;
+        sj = -1.0;
+      }
+      if (!(d > 0.0) || !(d <= DBL_MAX)) {
         bad = 1;
         d = 1.0;  // keep the factor finite; the solve is marked as failed
       }
       const double rs = rsqrt(d);
       T[j][j] = d * rs;
-      inv = rs;
-      dinv[o + j] = rs;
+      inv = sj * rs;
+      sgn = sj;
+      dinv[o + j] = sj * rs;
     }
     __syncthreads();
+    // L_ij = a_ij s_j / L_jj; the trailing update subtracts L_ij s_j L_wj
     if (w == j && lane > j) T[j][lane] *= inv;
     __syncthreads();
-    if (w > j && lane >= w) T[w][lane] -= T[j][lane] * T[j][w];
+    if (w > j && lane >= w) T[w][lane] -= sgn * T[j][lane] * T[j][w];
     __syncthreads();
   }
   if (w >= lane) A[(o + w) * N + o + lane] = T[lane][w];
   if (t == 0 && bad) st->scal[6] = 2.0;
 }
 
-// tiles below the diagonal in column k: X = A_ik L_kk^-T (warp c holds
+// tiles below the diagonal in column k: X = A_ik L_kk^-T S_k (warp c holds
 // column c of X and of L, lane r row r)
 __global__ void __launch_bounds__(1024) k_dense_trsm(double* A, int N, int k, const double* dinv) {
   __shared__ double L[kT][kT + 1], X[kT][kT + 1];  // transposed: [column][row]
@@ -85,17 +103,17 @@ __global__ void __launch_bounds__(1024) k_dense_trsm(double* A, int N, int k, co
   X[lane][w] = A[(oi + w) * N + o + lane];
   __syncthreads();
   for (int j = 0; j < kT; ++j) {
-    if (w == j) X[j][lane] *= dinv[o + j];
+    if (w == j) X[j][lane] *= fabs(dinv[o + j]);
     __syncthreads();
     if (w > j) X[w][lane] -= X[j][lane] * L[j][w];
     __syncthreads();
   }
-  A[(oi + w) * N + o + lane] = X[lane][w];
+  A[(oi + w) * N + o + lane] = dinv[o + lane] < 0.0 ? -X[lane][w] : X[lane][w];
 }
 
-// trailing tiles (i, j), k < j <= i: A_ij -= L_ik L_jk^T
-__global__ void __launch_bounds__(1024) k_dense_syrk(double* A, int N, int k, int nt) {
-  __shared__ double Li[kT][kT + 1], Lj[kT][kT + 1];
+// trailing tiles (i, j), k < j <= i: A_ij -= L_ik S_k L_jk^T
+__global__ void __launch_bounds__(1024) k_dense_syrk(double* A, int N, int k, int nt, const double* dinv) {
+  __shared__ double Li[kT][kT + 1], Lj[kT][kT + 1], S[kT];
   const int t = threadIdx.x, r = t / kT, c = t - kT * (t / kT);
   // blockIdx.x -> (ii, jj), jj <= ii, over the m = nt - k - 1 trailing tiles
   const int m = nt - k - 1;
@@ -109,15 +127,17 @@ __global__ void __launch_bounds__(1024) k_dense_syrk(double* A, int N, int k, in
   const long o = (long)kT * k, oi = (long)kT * (k + 1 + ii), oj = (long)kT * (k + 1 + jj);
   Li[r][c] = A[(oi + r) * N + o + c];
   Lj[r][c] = A[(oj + r) * N + o + c];
+  if (t < kT) S[t] = dinv[o + t] < 0.0 ? -1.0 : 1.0;
   __syncthreads();
   double s = 0.0;
 #pragma unroll 8
-  for (int q = 0; q < kT; ++q) s += Li[r][q] * Lj[c][q];
+  for (int q = 0; q < kT; ++q) s += Li[r][q] * S[q] * Lj[c][q];
   A[(oi + r) * N + oj + c] -= s;
 }
 
-// forward and backward substitution with the factor (one block); static rows
-// of the right-hand side are taken as zero, padding rows are zero
+// forward and backward substitution with the factor (one block): L y = b,
+// z = S y, L^T x = z; static rows of the right-hand side are taken as zero,
+// padding rows are zero
 __global__ void __launch_bounds__(1024) k_dense_trsv(const double* A, int N, int n, const double* dinv,
                                                      const uint8_t* is_static, const double* rhs, double* x,
                                                      const DevStatus* cst) {
@@ -135,7 +155,7 @@ __global__ void __launch_bounds__(1024) k_dense_trsv(const double* A, int N, int
     if (w == 0) {
       double v = y[o + lane];
       for (int j = 0; j < kT; ++j) {
-        const double yj = __shfl_sync(0xffffffffu, v * dinv[o + j], j);
+        const double yj = __shfl_sync(0xffffffffu, v * fabs(dinv[o + j]), j);
         if (lane == j) v = yj;
         if (lane > j) v -= Dt[lane][j] * yj;
       }
@@ -149,6 +169,9 @@ __global__ void __launch_bounds__(1024) k_dense_trsv(const double* A, int N, int
     }
     __syncthreads();
   }
+  for (int i = t; i < N; i += blockDim.x)
+    if (dinv[i] < 0.0) y[i] = -y[i];
+  __syncthreads();
   // L^T x = y
   for (int k = nt - 1; k >= 0; --k) {
     const long o = (long)kT * k;
@@ -157,7 +180,7 @@ __global__ void __launch_bounds__(1024) k_dense_trsv(const double* A, int N, int
     if (w == 0) {
       double v = y[o + lane];
       for (int j = kT - 1; j >= 0; --j) {
-        const double xj = __shfl_sync(0xffffffffu, v * dinv[o + j], j);
+        const double xj = __shfl_sync(0xffffffffu, v * fabs(dinv[o + j]), j);
         if (lane == j) v = xj;
         if (lane < j) v -= Dt[j][lane] * xj;
       }
@@ -196,7 +219,7 @@ int dense_order(int nb, int max_dofs) {
   return N <= kDenseMaxOrder ? (int)N : 0;
 }
 
-void launch_dense_solve(Scene& s, const double* rhs, double* x) {
+void launch_dense_solve(Scene& s, const double* rhs, double* x, bool indefinite) {
   const int N = s.dense_n, nt = N / kT;
   double* A = s.dense.p;
   // algorithmic flops: the factorisation N^3 / 3 and two substitutions 2 N^2
@@ -207,12 +230,12 @@ void launch_dense_solve(Scene& s, const double* rhs, double* x) {
   k_dense_fill<<<sm_grid(s, 4), 256, 0, s.stream>>>(s.nb, N, s.is_static.p, s.D.p, s.P.p, s.pblk.p, s.st, A);
   for (int k = 0; k < nt; ++k) {
     counted(s);
-    k_dense_potrf<<<1, 1024, 0, s.stream>>>(A, N, k, s.dense_dinv.p, s.st);
+    k_dense_potrf<<<1, 1024, 0, s.stream>>>(A, N, k, s.dense_dinv.p, s.st, indefinite ? 1 : 0);
     const int m = nt - k - 1;
     if (m > 0) {
       counted(s, 2);
       k_dense_trsm<<<m, 1024, 0, s.stream>>>(A, N, k, s.dense_dinv.p);
-      k_dense_syrk<<<m * (m + 1) / 2, 1024, 0, s.stream>>>(A, N, k, nt);
+      k_dense_syrk<<<m * (m + 1) / 2, 1024, 0, s.stream>>>(A, N, k, nt, s.dense_dinv.p);
     }
   }
   counted(s, 2);

@@ -185,16 +185,17 @@ __device__ __forceinline__ int pair_island(const int* isl, const uint8_t* is_sta
 // exact per-island energies.  which = 0: the reference energies E0 of the
 // iterate, from the system's stored terms (body energies, barrier terms with
 // their vertices, friction records); which = 1: the trial's, from the
-// energy-only pass (body energies, per body pair and chunk barrier partials,
-// friction records).  One thread per contribution.
+// energy-only pass (body energies, the barrier partials of the (body pair,
+// chunk) slots of the work list, friction records).  One thread per
+// contribution.
 __global__ void k_isl_energy(int which, int nb, const uint8_t* __restrict__ is_static, const int* __restrict__ isl,
                              const int* __restrict__ vbody, const double* __restrict__ Eb,
                              const DevStatus* __restrict__ cst, const double* __restrict__ term,
                              const int4* __restrict__ termv, const double* __restrict__ Epair, int nch,
                              const int2* __restrict__ P, const double* __restrict__ fterm,
                              const FricRec* __restrict__ fr, const int* __restrict__ lstate,
-                             unsigned long long* E, DevStatus* st) {
-  const long nbar = which == 0 ? (long)cst->nact : (long)cst->np * nch;
+                             const int* __restrict__ ework, unsigned long long* E, DevStatus* st) {
+  const long nbar = which == 0 ? (long)cst->nact : (long)cst->n_ework;
   const long nfr = cst->nfr;
   const long n = 2L * nb + nbar + nfr;
   unsigned long long* base = E + 8 * which;
@@ -219,9 +220,10 @@ __global__ void k_isl_energy(int which, int nb, const uint8_t* __restrict__ is_s
           key = pair_island(isl, is_static, vbody[vv.x], vbody[vv.w]);
           v = term[t * kTermStride];
         } else {
-          const int2 pr = P[t / nch];
+          const int w = ework[t];
+          const int2 pr = P[w / nch];
           key = pair_island(isl, is_static, pr.x, pr.y);
-          v = Epair[t];
+          v = Epair[w];
         }
       } else {
         const long f = i - 2L * nb - nbar;
@@ -331,6 +333,24 @@ __global__ void k_isl_accept(int nb, const uint8_t* is_static, const int* isl, d
   }
 }
 
+// start of a halving round of the device-side loop: the counts the acceptance
+// pass accumulates are cleared, the round is counted
+__global__ void k_ls_round_begin(DevStatus* st) {
+  st->ls_pending = 0;
+  st->n_islands = 0;
+  st->ls_failed = 0;
+  st->ls_halv_max = 0;
+  st->ls_rounds += 1;
+}
+
+// condition of the device-side line-search loop (one thread)
+__global__ void k_ls_condition(DevStatus* st, cudaGraphConditionalHandle h, int max_rounds, int first) {
+  if (first) st->ls_rounds = 0;
+  const bool more = st->ls_pending > 0 && st->ls_failed == 0 && !(st->flags & ST_INTERSECT) &&
+                    st->ls_rounds < max_rounds;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -352,7 +372,8 @@ void launch_island_energy(Scene& s, int which) {
   counted(s);
   k_isl_energy<<<sm_grid(s, 8), 256, 0, s.stream>>>(which, s.nb, s.is_static.p, s.isl.p, s.vbody.p, s.Eb.p, s.st,
                                                       s.term.p, s.termv.p, s.Epair.p, energy_chunks(s), s.P.p,
-                                                      s.fterm.p, s.fric.p, s.isl_state.p, s.isl_E.p, s.st);
+                                                      s.fterm.p, s.fric.p, s.isl_state.p, s.ework.p, s.isl_E.p,
+                                                      s.st);
 }
 
 void launch_island_start(Scene& s) {
@@ -370,11 +391,21 @@ void launch_island_trial(Scene& s) {
       s.nb, s.is_static.p, s.isl.p, s.isl_alpha.p, s.q.p, s.dq.p, s.qtrial.p);
 }
 
-void launch_island_accept(Scene& s) {
-  counted(s, 2);
-  cudaMemsetAsync(&s.st->ls_pending, 0, 4 * sizeof(int), s.stream);
+void launch_island_accept(Scene& s, bool reset) {
+  counted(s, reset ? 2 : 1);
+  if (reset) cudaMemsetAsync(&s.st->ls_pending, 0, 4 * sizeof(int), s.stream);
   k_isl_accept<<<grid_n(s.nb, 256, sm_grid(s, 4)), 256, 0, s.stream>>>(
       s.nb, s.is_static.p, s.isl.p, s.prm.ls_slack_rel, s.prm.ls_max, s.isl_E.p, s.isl_alpha.p, s.isl_state.p, s.st);
+}
+
+void launch_ls_round_begin(Scene& s) {
+  counted(s);
+  k_ls_round_begin<<<1, 1, 0, s.stream>>>(s.st);
+}
+
+void launch_ls_condition(Scene& s, cudaGraphConditionalHandle h, int max_rounds, bool first) {
+  counted(s);
+  k_ls_condition<<<1, 1, 0, s.stream>>>(s.st, h, max_rounds, first ? 1 : 0);
 }
 
 }  // namespace abd

@@ -841,9 +841,10 @@ void pcg_account(Scene& s, int its) {
   s.prof.slot[PF_SPMV].flops += n * pcg_iter_flops(s, np);
 }
 
-int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res) {
+int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_tol, double* rel_res,
+            bool indefinite) {
   if (s.dense_n) {
-    launch_dense_solve(s, rhs, xout);
+    launch_dense_solve(s, rhs, xout, indefinite);
     cudaMemcpyAsync(s.st_host, s.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s.stream);
     cudaStreamSynchronize(s.stream);
     return pcg_result(s, rel_res);

@@ -174,3 +174,47 @@ def test_adjoint_steps_match_oracle_on_the_throw_stack(abd):
     np.testing.assert_allclose(gqd.cpu().numpy(), gqd0, rtol=0, atol=1e-9 * np.abs(gqd0).max())
     np.testing.assert_allclose(gq.cpu().numpy(), gq0, rtol=0, atol=1e-9 * np.abs(gq0).max())
     np.testing.assert_allclose(gk.cpu().numpy(), gk0, rtol=0, atol=1e-9 * max(np.abs(gk0).max(), 1e-300))
+
+
+def test_adjoint_matches_oracle_over_20_steps_of_the_throw_stack(abd):
+    """the adjoint workload over a 20-step horizon (the thrown block in
+    flight, the stack settling, the first impacts), with the benchmark's
+    solver setting (dense direct solves): every step's GPU adjoint from the
+    oracle's inputs against the oracle's outputs (states, inputs and outputs
+    from tests/golden/throw_stack_adjoint.npz, written by the oracle alone),
+    then the whole chain on the GPU against the oracle's chain.  Steps whose
+    converged state is a saddle of the IP (unprojected Hessian with a
+    negative eigenvalue) are solved by the signed dense factorisation on the
+    GPU and by LDL^T in the oracle."""
+    import os
+    G = np.load(os.path.join(os.path.dirname(__file__), "golden", "throw_stack_adjoint.npz"))
+    s = scenes.throw_stack(seed=int(G["seed"]))
+    q, qd = G["q"], G["qdot"]
+    n = q.shape[0] - 1
+    assert (G["hess_eig"][:, 0] < 0).any()  # the horizon holds an indefinite step
+    gpu = abd.AbdScene(s, dense_max_dofs=3072)
+    dev = gpu.device
+
+    def t64(a):
+        return torch.tensor(np.ascontiguousarray(a), device=dev)
+
+    # the kappa gradient of a step with no contact and rigid bodies is
+    # rounding noise (1e-49 here): it is compared on the scale of the largest
+    # step's kappa gradient
+    gk_scale = np.abs(G["gk_out"]).max()
+    for t in range(n):
+        gq, gqd = t64(G["gq_in"][t]), t64(G["gqd_in"][t])
+        gk = torch.zeros(s.nb, dtype=torch.float64, device=dev)
+        gpu.adjoint_step(q[t], qd[t], q[t + 1], gq, gqd, gk)
+        for got, ref, scale in ((gq, G["gq_out"][t], np.abs(G["gq_out"][t]).max()),
+                                (gqd, G["gqd_out"][t], np.abs(G["gqd_out"][t]).max()),
+                                (gk, G["gk_out"][t], gk_scale)):
+            np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=0, atol=1e-9 * scale, err_msg=f"step {t}")
+    gq, gqd = t64(G["gq_in"][n - 1]), t64(G["gqd_in"][n - 1])
+    gk = torch.zeros(s.nb, dtype=torch.float64, device=dev)
+    for t in range(n - 1, -1, -1):
+        gpu.adjoint_step(q[t], qd[t], q[t + 1], gq, gqd, gk)
+    gk0 = G["gk_out"].sum(axis=0)
+    np.testing.assert_allclose(gq.cpu().numpy(), G["gq_out"][0], rtol=0, atol=1e-8 * np.abs(G["gq_out"][0]).max())
+    np.testing.assert_allclose(gqd.cpu().numpy(), G["gqd_out"][0], rtol=0, atol=1e-8 * np.abs(G["gqd_out"][0]).max())
+    np.testing.assert_allclose(gk.cpu().numpy(), gk0, rtol=0, atol=1e-8 * np.abs(gk0).max())
