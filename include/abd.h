@@ -223,18 +223,28 @@ ABD_API abd_status abd_ccd_toi(abd_scene* s, const double* q_dev, const double* 
  * receives the statistics of the last step. */
 ABD_API abd_status abd_step(abd_scene* s, int nsteps, abd_step_stats* stats);
 
-/* Launch shape of a scene's kernels.  grid_div divides the grids that are
- * sized by the device rather than by a host-known count (kernels that
- * grid-stride over a count held on the device: barrier terms, assembly
- * blocks, friction records, incoming-pair lists); 1 = one full wave per
- * kernel class (the default), larger values leave SMs to the kernels of
- * other scenes stepped concurrently.  Results do not depend on it (every
- * such kernel writes per-item outputs or exact integer reductions).  Values
- * outside 1..64 return ABD_ERR_INVALID_ARG.  The scene's captured launch
- * sequences are re-captured on its next step. */
+/* Launch shape of a scene's kernels and the size of its preconditioner's
+ * clusters.  grid_div divides the grids that are sized by the device rather
+ * than by a host-known count (kernels that grid-stride over a count held on
+ * the device: barrier terms, assembly blocks, friction records,
+ * incoming-pair lists); 1 = one full wave per kernel class (the default),
+ * larger values leave SMs to the kernels of other scenes stepped
+ * concurrently.  Results do not depend on it (every such kernel writes
+ * per-item outputs or exact integer reductions).  Values outside 1..64
+ * return ABD_ERR_INVALID_ARG.  The scene's captured launch sequences are
+ * re-captured on its next step.
+ *
+ * cluster_max: the PCG's cluster block-Jacobi preconditioner cuts every
+ * contact island (in breadth-first order) into runs of at most cluster_max
+ * bodies and factors each run densely (one SM per run, (12 n)^3 / 3 flop);
+ * 1 = plain block-Jacobi; 0 = the default, 16 (the largest accepted).
+ * Larger runs cost more per factorisation and usually fewer PCG iterations;
+ * the Newton directions differ only within the PCG tolerance.  Values
+ * outside 0..16 return ABD_ERR_INVALID_ARG. */
 typedef struct {
   int grid_div;
-  int reserved[7];   /* zero */
+  int cluster_max;
+  int reserved[6];   /* zero */
 } abd_tuning;
 ABD_API abd_status abd_set_tuning(abd_scene* s, const abd_tuning* t);
 ABD_API abd_status abd_get_tuning(const abd_scene* s, abd_tuning* t);

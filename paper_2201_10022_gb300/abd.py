@@ -74,7 +74,7 @@ class abd_counters(C.Structure):
 
 
 class abd_tuning(C.Structure):
-    _fields_ = [("grid_div", C.c_int), ("reserved", C.c_int * 7)]
+    _fields_ = [("grid_div", C.c_int), ("cluster_max", C.c_int), ("reserved", C.c_int * 6)]
 
 
 def _as_dict(st):
@@ -436,15 +436,18 @@ class AbdScene:
                                          gkappa.data_ptr(), rel_tol, C.byref(st)))
         return _as_dict(st)
 
-    def set_tuning(self, grid_div=1):
+    def set_tuning(self, grid_div=1, cluster_max=0):
+        """grid_div: divisor of the device-sized grids (1..64); cluster_max:
+        bodies per preconditioner cluster (1..16, 0 = the default 16)"""
         t = abd_tuning()
         t.grid_div = int(grid_div)
+        t.cluster_max = int(cluster_max)
         self._check(abd_set_tuning(self.h, t))
 
     def tuning(self):
         t = abd_tuning()
         self._check(abd_get_tuning(self.h, t))
-        return {"grid_div": t.grid_div}
+        return {"grid_div": t.grid_div, "cluster_max": t.cluster_max}
 
     def counters(self):
         c = abd_counters()

@@ -80,6 +80,7 @@ void size_pair_buffers(Scene& s, size_t pcap) {
   grow(s, s.posbuf, pcap + 1);
   grow(s, s.Epair, pcap * (size_t)energy_chunks(s));
   grow(s, s.ework, pcap * (size_t)energy_chunks(s));
+  grow(s, s.large_asm, pcap);
   grow(s, s.cand, pcap * (size_t)s.maxc);
   grow(s, s.act, pcap * (size_t)s.maxc);
   grow(s, s.act_d2, pcap * (size_t)s.maxc);
@@ -241,8 +242,8 @@ void build_clusters_host(Scene& s) {
   int nc = 0;
   long long fo = 0;
   for (size_t k = 0; k + 1 < island_start.size(); ++k) {
-    for (int c0 = island_start[k]; c0 < island_start[k + 1]; c0 += kClusterMax) {
-      const int n = std::min(kClusterMax, island_start[k + 1] - c0);
+    for (int c0 = island_start[k]; c0 < island_start[k + 1]; c0 += s.cluster_max) {
+      const int n = std::min(s.cluster_max, island_start[k + 1] - c0);
       off[nc] = c0;
       foff[nc] = fo;
       if (n >= 2) fo += (long long)(12 * n) * (12 * n + 1) / 2;
@@ -1011,7 +1012,7 @@ void abd_destroy(abd_scene* S) {
   for (Buf<double4>* b : {&s.x, &s.dx, &s.x1, &s.xt}) release(s, *b);
   for (Buf<int>* b : {&s.nbr, &s.ncount, &s.rowoff, &s.in_off, &s.in_cnt, &s.in_list, &s.ccount, &s.acount, &s.aoff,
                       &s.fpoff, &s.flagbuf, &s.posbuf, &s.hcount, &s.hoff, &s.large, &s.large_pos, &s.large_list,
-                      &s.slot_cnt, &s.slot_off, &s.entries, &s.ework})
+                      &s.slot_cnt, &s.slot_off, &s.entries, &s.ework, &s.large_asm})
     release(s, *b);
   release(s, s.P);
   release(s, s.fpairs);
@@ -1319,8 +1320,10 @@ abd_status abd_step(abd_scene* S, int nsteps, abd_step_stats* stats) {
 }
 
 abd_status abd_set_tuning(abd_scene* S, const abd_tuning* t) {
-  if (!S || !t || t->grid_div < 1 || t->grid_div > 64) return ABD_ERR_INVALID_ARG;
+  if (!S || !t || t->grid_div < 1 || t->grid_div > 64 || t->cluster_max < 0 || t->cluster_max > kClusterMax)
+    return ABD_ERR_INVALID_ARG;
   Scene& s = S->s;
+  s.cluster_max = t->cluster_max ? t->cluster_max : kClusterMax;
   if (t->grid_div != s.grid_div) {
     s.grid_div = t->grid_div;
     ++s.gen;  // the captured sequences hold the old grids
@@ -1332,6 +1335,7 @@ abd_status abd_get_tuning(const abd_scene* S, abd_tuning* t) {
   if (!S || !t) return ABD_ERR_INVALID_ARG;
   memset(t, 0, sizeof(*t));
   t->grid_div = S->s.grid_div;
+  t->cluster_max = S->s.cluster_max;
   return ABD_OK;
 }
 

@@ -64,6 +64,8 @@ struct DevStatus {
   int clu_fail;                 // clusters whose Cholesky factorisation failed (block-Jacobi used)
   int ls_rounds;                // halving rounds run by the device-side line-search loop
   int n_ework;                  // entries of the (body pair, chunk) work list
+  int n_large_asm;              // body pairs assembled by a whole block (many terms)
+  int pad5;
 };
 
 // ---- small device helpers shared by the kernel files -----------------------
@@ -139,6 +141,8 @@ struct Prof {
 };
 
 // ---- scene ------------------------------------------------------------------
+constexpr int kClusterMax = 16;  // largest preconditioner cluster (bodies)
+
 struct Scene {
   abd_params prm{};
   int nb = 0, nv = 0, nt = 0, ne = 0, ndyn = 0;
@@ -177,6 +181,7 @@ struct Scene {
   cudaEvent_t ev_fork[5] = {}, ev_join[5] = {};
   int device = 0;    // CUDA device the scene was created on
   int grid_div = 1;  // divisor of the device-sized grids (abd_tuning)
+  int cluster_max = kClusterMax;  // bodies per preconditioner cluster (abd_tuning)
   std::string err;
 
   // topology and body constants
@@ -225,6 +230,7 @@ struct Scene {
   Buf<int4> ftermv;
   Buf<double> Epair;   // energy-only pass: barrier energy per (body pair, chunk of 32 candidates)
   Buf<int> ework;      // the (body pair, chunk) slots p * chunks + c that hold candidates (line search)
+  Buf<int> large_asm;  // body pairs with many terms, assembled a block per pair
 
   // friction
   Buf<FricRec> fric;
@@ -389,7 +395,6 @@ int run_pcg(Scene& s, const double* rhs, double* xout, int max_iter, double rel_
 void launch_pcg_fp32_blocks(Scene& s);  // mixed precision: FP32 copies of the blocks
 // factors of the preconditioner clusters (after the assembly)
 void launch_cluster_factor(Scene& s);
-constexpr int kClusterMax = 16;         // bodies per preconditioner cluster
 double pcg_iter_bytes(const Scene& s, long np);
 double pcg_iter_flops(const Scene& s, long np);
 // dense direct solve (small scenes): order of the padded matrix, 0 if off

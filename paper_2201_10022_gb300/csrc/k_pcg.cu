@@ -274,8 +274,23 @@ __device__ void phase_spmv(const PcgArgs& a, int k, T beta, const T* __restrict_
 // i (i + 1) / 2 + j, reciprocal pivots on the diagonal); one warp, r and z in
 // the rows of the members; ybuf: N doubles of the warp's shared memory.
 // Forward substitution row by row (lane sums in a fixed order), back
-// substitution column by column.
+// substitution column by column.  Row i of L is held in registers (lane l
+// holds entries l, l + 32, ... below the diagonal: kRowChunks per lane for
+// N <= 192; the diagonal entry in every lane), and the next row's loads are
+// issued before the current row's dependent chain, so each step waits on
+// shuffles and shared memory, not on a load from L2.
 __device__ __forceinline__ long ptri(int i, int j) { return (long)i * (i + 1) / 2 + j; }
+
+constexpr int kRowChunks = (12 * kClusterMax + 31) / 32;
+
+// entries 0..len-1 of a packed row into lane-strided registers (zero beyond)
+__device__ __forceinline__ void load_row(const double* Li, int len, int lane, double (&v)[kRowChunks]) {
+#pragma unroll
+  for (int q = 0; q < kRowChunks; ++q) {
+    const int j = lane + 32 * q;
+    v[q] = j < len ? Li[j] : 0.0;
+  }
+}
 
 template <typename T>
 __device__ void cluster_solve(const PcgArgs& a, int c, const T* r, T* z, double* ybuf) {
@@ -284,22 +299,49 @@ __device__ void cluster_solve(const PcgArgs& a, int c, const T* r, T* z, double*
   const double* L = a.c_fac + a.c_foff[c];
   for (int i = lane; i < N; i += 32) ybuf[i] = (double)r[12 * a.c_perm[m0 + i / 12] + i % 12];
   __syncwarp();
+  // the row (off-diagonal entries) and its diagonal entry (the reciprocal
+  // pivot, loaded by every lane) of the current and the next step
+  double cur[kRowChunks], nxt[kRowChunks];
+  double dcur = L[0], dnxt = 0.0;
+  load_row(L, 0, lane, cur);
   for (int i = 0; i < N; ++i) {
-    const double* Li = L + ptri(i, 0);
+    if (i + 1 < N) {
+      load_row(L + ptri(i + 1, 0), i + 1, lane, nxt);
+      dnxt = L[ptri(i + 1, i + 1)];
+    }
     double t = 0.0;
-    for (int j = lane; j < i; j += 32) t = fma(Li[j], ybuf[j], t);
+#pragma unroll
+    for (int q = 0; q < kRowChunks; ++q) {
+      const int j = lane + 32 * q;
+      if (j < i) t = fma(cur[q], ybuf[j], t);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
-    if (lane == 0) ybuf[i] = (ybuf[i] - t) * Li[i];
+    if (lane == 0) ybuf[i] = (ybuf[i] - t) * dcur;
     __syncwarp();
+#pragma unroll
+    for (int q = 0; q < kRowChunks; ++q) cur[q] = nxt[q];
+    dcur = dnxt;
   }
+  load_row(L + ptri(N - 1, 0), N - 1, lane, cur);
+  dcur = L[ptri(N - 1, N - 1)];
   for (int i = N - 1; i >= 0; --i) {
-    const double* Li = L + ptri(i, 0);
-    const double zi = ybuf[i] * Li[i];
+    if (i > 0) {
+      load_row(L + ptri(i - 1, 0), i - 1, lane, nxt);
+      dnxt = L[ptri(i - 1, i - 1)];
+    }
+    const double zi = ybuf[i] * dcur;
     __syncwarp();
-    for (int j = lane; j < i; j += 32) ybuf[j] = fma(-Li[j], zi, ybuf[j]);
+#pragma unroll
+    for (int q = 0; q < kRowChunks; ++q) {
+      const int j = lane + 32 * q;
+      if (j < i) ybuf[j] = fma(-cur[q], zi, ybuf[j]);
+    }
     if (lane == 0) ybuf[i] = zi;
     __syncwarp();
+#pragma unroll
+    for (int q = 0; q < kRowChunks; ++q) cur[q] = nxt[q];
+    dcur = dnxt;
   }
   for (int i = lane; i < N; i += 32) z[12 * a.c_perm[m0 + i / 12] + i % 12] = (T)ybuf[i];
   __syncwarp();

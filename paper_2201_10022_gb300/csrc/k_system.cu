@@ -646,120 +646,199 @@ __device__ int find_fpair(const int2* fp, int n, int a, int b) {
   return (lo < n && fp[lo].x == a && fp[lo].y == b) ? lo : -1;
 }
 
-__global__ void __launch_bounds__(128) k_assemble(const DevStatus* __restrict__ cst, const int2* P, const int* aoff,
-                                                  const double* term,
-                           const int4* termv, const int2* fpairs, const int* fpoff, const double* fterm,
-                           const int4* ftermv, const int* vbody, const double4* xbar, double* pblk) {
-  __shared__ double sH[8][kTermStride];
-  __shared__ double sw[8][4][4];
-  __shared__ int sside[8][4];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int np = cst->np, nfp = cst->nfp, nact = cst->nact;
-  for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < np; p += nwarps) {
-    const int a = P[p].x, b = P[p].y;
-    int t0 = aoff[p], t1 = min(aoff[p + 1], nact);
-    int f0 = 0, f1 = 0;
-    if (nfp > 0) {
-      int q = find_fpair(fpairs, nfp, a, b);
-      if (q >= 0) {
-        f0 = fpoff[q];
-        f1 = fpoff[q + 1];
-      }
+// A body pair's terms: its active barrier terms t0..t1 of term/termv, then
+// its lagged friction records f0..f1 of fterm/ftermv.
+struct PairTerms {
+  int a, t0, t1, f0, f1;
+  __device__ int count() const { return (t1 - t0) + (f1 - f0); }
+};
+
+__device__ __forceinline__ PairTerms pair_terms(const DevStatus* cst, const int2* P, const int* aoff,
+                                                const int2* fpairs, const int* fpoff, int p) {
+  const int nfp = cst->nfp, nact = cst->nact;
+  const int a = P[p].x, b = P[p].y;
+  PairTerms pt{a, aoff[p], min(aoff[p + 1], nact), 0, 0};
+  if (nfp > 0) {
+    int q = find_fpair(fpairs, nfp, a, b);
+    if (q >= 0) {
+      pt.f0 = fpoff[q];
+      pt.f1 = fpoff[q + 1];
     }
-    // lanes 0..26: region r = lane / 9 (0: H_ab, 1: D_a, 2: D_b) and spatial
-    // component pair (c, c2) = ((lane % 9) / 3, lane % 3); each accumulates
-    // the 4x4 block over the weight indices (u, u2) of
-    //   sum_{k on side sk, l on side sl} w_k[u] w_l[u2] H_kl[c][c2]
-    // as two 4x4 products (T = W_sk^T H_c, then T W_sl) with the other side's
-    // weights zeroed; lanes 27..31: the 24 gradient entries and two energies
-    double acc[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) acc[k] = 0.0;
-    const int r = lane / 9, cc = (lane % 9) / 3, c2 = lane % 3;
-    const int sk = r == 2 ? 1 : 0, sl = r == 1 ? 0 : 1;
-    const int nterms = (t1 - t0) + (f1 - f0);
-    for (int it = 0; it < nterms; ++it) {
-      const bool fr = it >= (t1 - t0);
-      const int t = fr ? f0 + (it - (t1 - t0)) : t0 + it;
-      const double* T = (fr ? fterm : term) + (size_t)t * kTermStride;
-      for (int k = lane; k < kTermStride; k += 32) sH[wib][k] = T[k];
-      if (lane < 4) {
-        int4 vv = fr ? ftermv[t] : termv[t];
-        int v = lane == 0 ? vv.x : (lane == 1 ? vv.y : (lane == 2 ? vv.z : vv.w));
-        sside[wib][lane] = vbody[v] == a ? 0 : 1;
-        double4 xb = xbar[v];
-        sw[wib][lane][0] = 1.0;
-        sw[wib][lane][1] = xb.x;
-        sw[wib][lane][2] = xb.y;
-        sw[wib][lane][3] = xb.z;
-      }
-      __syncwarp();
-      const double* H = sH[wib] + 13;
-      const double* g = sH[wib] + 1;
-      if (lane < 27) {
-        double wk[4][4], wl[4][4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            wk[k][u] = sside[wib][k] == sk ? sw[wib][k][u] : 0.0;
-            wl[k][u] = sside[wib][k] == sl ? sw[wib][k][u] : 0.0;
-          }
-        double Tm[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int l = 0; l < 4; ++l) {
-            double x = 0.0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) x += wk[k][u] * H[up12(3 * k + cc, 3 * l + c2)];
-            Tm[u][l] = x;
-          }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int u2 = 0; u2 < 4; ++u2) {
-            double x = acc[4 * u + u2];
-#pragma unroll
-            for (int l = 0; l < 4; ++l) x += Tm[u][l] * wl[l][u2];
-            acc[4 * u + u2] = x;
-          }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          const int gi = (lane - 27) + 5 * j;
-          double c = 0.0;
-          if (gi < 24) {
-            const int sd = gi / 12;
-            int u, ci;
-            inv_dof(gi % 12, u, ci);
-            for (int k = 0; k < 4; ++k)
-              if (sside[wib][k] == sd) c += sw[wib][k][u] * g[3 * k + ci];
-          } else if (gi == 24) {
-            c = fr ? 0.0 : sH[wib][0];
-          } else if (gi == 25) {
-            c = fr ? sH[wib][0] : 0.0;
-          }
-          acc[j] += c;
-        }
-      }
-      __syncwarp();
+  }
+  return pt;
+}
+
+// One warp adds term number it of the pair to its lanes' accumulators.
+// lanes 0..26: region r = lane / 9 (0: H_ab, 1: D_a, 2: D_b) and spatial
+// component pair (c, c2) = ((lane % 9) / 3, lane % 3); each accumulates the
+// 4x4 block over the weight indices (u, u2) of
+//   sum_{k on side sk, l on side sl} w_k[u] w_l[u2] H_kl[c][c2]
+// as two 4x4 products (T = W_sk^T H_c, then T W_sl) with the other side's
+// weights zeroed; lanes 27..31: the 24 gradient entries and two energies.
+// sH, sw, sside: this warp's staging in shared memory.
+__device__ __forceinline__ void assemble_term(const PairTerms& pt, int it, const double* term, const int4* termv,
+                                              const double* fterm, const int4* ftermv, const int* vbody,
+                                              const double4* xbar, double* sHw, double (*sww)[4], int* ssidew,
+                                              double (&acc)[16]) {
+  const int lane = threadIdx.x & 31;
+  const int a = pt.a, t0 = pt.t0, t1 = pt.t1, f0 = pt.f0;
+  const int r = lane / 9, cc = (lane % 9) / 3, c2 = lane % 3;
+  const int sk = r == 2 ? 1 : 0, sl = r == 1 ? 0 : 1;
+    const bool fr = it >= (t1 - t0);
+    const int t = fr ? f0 + (it - (t1 - t0)) : t0 + it;
+    const double* T = (fr ? fterm : term) + (size_t)t * kTermStride;
+    for (int k = lane; k < kTermStride; k += 32) sHw[k] = T[k];
+    if (lane < 4) {
+      int4 vv = fr ? ftermv[t] : termv[t];
+      int v = lane == 0 ? vv.x : (lane == 1 ? vv.y : (lane == 2 ? vv.z : vv.w));
+      ssidew[lane] = vbody[v] == a ? 0 : 1;
+      double4 xb = xbar[v];
+      sww[lane][0] = 1.0;
+      sww[lane][1] = xb.x;
+      sww[lane][2] = xb.y;
+      sww[lane][3] = xb.z;
     }
-    double* out = pblk + (size_t)p * kBlkStride;
+    __syncwarp();
+    const double* H = sHw + 13;
+    const double* g = sHw + 1;
     if (lane < 27) {
+      double wk[4][4], wl[4][4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          wk[k][u] = ssidew[k] == sk ? sww[k][u] : 0.0;
+          wl[k][u] = ssidew[k] == sl ? sww[k][u] : 0.0;
+        }
+      double Tm[4][4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int u2 = 0; u2 < 4; ++u2)
-          out[144 * r + 12 * dof(u, cc) + dof(u2, c2)] = acc[4 * u + u2];
+        for (int l = 0; l < 4; ++l) {
+          double x = 0.0;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) x += wk[k][u] * H[up12(3 * k + cc, 3 * l + c2)];
+          Tm[u][l] = x;
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int u2 = 0; u2 < 4; ++u2) {
+          double x = acc[4 * u + u2];
+#pragma unroll
+          for (int l = 0; l < 4; ++l) x += Tm[u][l] * wl[l][u2];
+          acc[4 * u + u2] = x;
+        }
     } else {
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
         const int gi = (lane - 27) + 5 * j;
-        if (gi < 26) out[432 + gi] = acc[j];
+        double c = 0.0;
+        if (gi < 24) {
+          const int sd = gi / 12;
+          int u, ci;
+          inv_dof(gi % 12, u, ci);
+          for (int k = 0; k < 4; ++k)
+            if (ssidew[k] == sd) c += sww[k][u] * g[3 * k + ci];
+        } else if (gi == 24) {
+          c = fr ? 0.0 : sHw[0];
+        } else if (gi == 25) {
+          c = fr ? sHw[0] : 0.0;
+        }
+        acc[j] += c;
       }
     }
+  __syncwarp();
+}
+
+// the pair's accumulated blocks, gradient parts and energies to its slot
+__device__ __forceinline__ void assemble_write(double* pblk, int p, const double (&acc)[16]) {
+  const int lane = threadIdx.x & 31;
+  const int r = lane / 9, cc = (lane % 9) / 3, c2 = lane % 3;
+  double* out = pblk + (size_t)p * kBlkStride;
+  if (lane < 27) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int u2 = 0; u2 < 4; ++u2)
+        out[144 * r + 12 * dof(u, cc) + dof(u2, c2)] = acc[4 * u + u2];
+  } else {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const int gi = (lane - 27) + 5 * j;
+      if (gi < 26) out[432 + gi] = acc[j];
+    }
+  }
+}
+
+// pairs with more terms than this go to k_assemble_large (a block per pair)
+constexpr int kAssembleLarge = 12;
+constexpr int kAssembleWarps = 8;
+
+// a warp per body pair with at most kAssembleLarge terms (its terms in
+// order); larger pairs are listed for k_assemble_large
+__global__ void __launch_bounds__(128) k_assemble(const DevStatus* cst, const int2* P, const int* aoff,
+                                                  const double* term, const int4* termv, const int2* fpairs,
+                                                  const int* fpoff, const double* fterm, const int4* ftermv,
+                                                  const int* vbody, const double4* xbar, double* pblk,
+                                                  int* large_pairs, DevStatus* st) {
+  __shared__ double sH[4][kTermStride];
+  __shared__ double sw[4][4][4];
+  __shared__ int sside[4][4];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int np = cst->np;
+  for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < np; p += nwarps) {
+    const PairTerms pt = pair_terms(cst, P, aoff, fpairs, fpoff, p);
+    const int nterms = pt.count();
+    if (nterms > kAssembleLarge) {
+      if (lane == 0) large_pairs[atomicAdd(&st->n_large_asm, 1)] = p;
+      continue;
+    }
+    double acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+    for (int it = 0; it < nterms; ++it)
+      assemble_term(pt, it, term, termv, fterm, ftermv, vbody, xbar, sH[wib], sw[wib], sside[wib], acc);
+    assemble_write(pblk, p, acc);
+  }
+}
+
+// a block of kAssembleWarps warps per listed pair: warp w takes terms w,
+// w + kAssembleWarps, ...; the warps' sums are added in warp order (a fixed
+// order, so results do not depend on timing)
+__global__ void __launch_bounds__(32 * kAssembleWarps) k_assemble_large(
+    const DevStatus* __restrict__ cst, const int2* P, const int* aoff, const double* term, const int4* termv,
+    const int2* fpairs, const int* fpoff, const double* fterm, const int4* ftermv, const int* vbody,
+    const double4* xbar, double* pblk, const int* large_pairs) {
+  __shared__ double sH[kAssembleWarps][kTermStride];
+  __shared__ double sw[kAssembleWarps][4][4];
+  __shared__ int sside[kAssembleWarps][4];
+  __shared__ double sacc[kAssembleWarps][16][33];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nl = cst->n_large_asm;
+  for (int k = blockIdx.x; k < nl; k += gridDim.x) {
+    const int p = large_pairs[k];
+    const PairTerms pt = pair_terms(cst, P, aoff, fpairs, fpoff, p);
+    const int nterms = pt.count();
+    double acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+    for (int it = wib; it < nterms; it += kAssembleWarps)
+      assemble_term(pt, it, term, termv, fterm, ftermv, vbody, xbar, sH[wib], sw[wib], sside[wib], acc);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) sacc[wib][j][lane] = acc[j];
+    __syncthreads();
+    if (wib == 0) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        double x = sacc[0][j][lane];
+        for (int w = 1; w < kAssembleWarps; ++w) x += sacc[w][j][lane];
+        acc[j] = x;
+      }
+      assemble_write(pblk, p, acc);
+    }
+    __syncthreads();
   }
 }
 
@@ -1242,10 +1321,15 @@ void launch_negate(Scene& s, const double* in, double* out, long n) {
 }
 
 void launch_assemble(Scene& s) {
-  counted(s);
+  counted(s, 3);
   ProfScope pa(s, PF_ASSEMBLE);
+  cudaMemsetAsync(reinterpret_cast<char*>(s.st) + offsetof(DevStatus, n_large_asm), 0, sizeof(int), s.stream);
   k_assemble<<<sm_grid(s, 16), 128, 0, s.stream>>>(s.st, s.P.p, s.aoff.p, s.term.p, s.termv.p, s.fpairs.p, s.fpoff.p,
-                                            s.fterm.p, s.ftermv.p, s.vbody.p, s.xbar.p, s.pblk.p);
+                                                   s.fterm.p, s.ftermv.p, s.vbody.p, s.xbar.p, s.pblk.p,
+                                                   s.large_asm.p, s.st);
+  k_assemble_large<<<sm_grid(s, 4), 32 * kAssembleWarps, 0, s.stream>>>(
+      s.st, s.P.p, s.aoff.p, s.term.p, s.termv.p, s.fpairs.p, s.fpoff.p, s.fterm.p, s.ftermv.p, s.vbody.p, s.xbar.p,
+      s.pblk.p, s.large_asm.p);
 }
 
 void launch_body_terms(Scene& s, const double* q, bool hess, bool project, bool pending_only) {
