@@ -172,9 +172,15 @@ __device__ __forceinline__ double pair_dist2(int kind, const v3* x, int& type) {
 // Additive CCD (ACCD, cited by Sec. 4.1): conservative advancement along the
 // linear trajectory x + t dx, t in [0, tmax], with the mean displacement
 // removed.  Returns 0 on success, 1 if the iteration cap was reached.
+// bound (may be null): the bits of a time that other evaluations have already
+// established as an upper bound of the minimum this evaluation contributes
+// to; it is re-read every 8 advancement steps and lowers tmax.  A result of
+// tmax then means "no impact before the bound", which leaves the minimum
+// unchanged, so the minimum over all evaluations is exact whatever their
+// timing.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int accd(int kind, const v3* xin, const v3* dx, double s, double tmax, int max_iter,
-                                    double& toi) {
+                                    double& toi, const unsigned long long* bound = nullptr) {
   v3 x[4], p[4];
   v3 mean;
   mean.x = __dmul_rn(__dadd_rn(__dadd_rn(dx[0].x, dx[1].x), __dadd_rn(dx[2].x, dx[3].x)), 0.25);
@@ -223,6 +229,10 @@ __device__ __forceinline__ int accd(int kind, const v3* xin, const v3* dx, doubl
       return 0;
     }
     t = __dadd_rn(t, tl);
+    if (bound && (it & 7) == 7) {
+      const double bt = __longlong_as_double((long long)*(const volatile unsigned long long*)bound);
+      if (bt < tmax) tmax = bt;
+    }
     if (t > tmax) {
       toi = tmax;
       return 0;

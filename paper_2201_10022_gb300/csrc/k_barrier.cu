@@ -42,6 +42,12 @@ namespace {
 
 constexpr unsigned kAll = 0xffffffffu;
 constexpr int kBarWarps = 4;
+// blocks of k_barrier that must fit on one SM (a register bound of
+// 65536 / (32 kBarWarps kBarMinBlocks) per thread)
+#ifndef ABD_BAR_MIN_BLOCKS
+#define ABD_BAR_MIN_BLOCKS 1
+#endif
+constexpr int kBarMinBlocks = ABD_BAR_MIN_BLOCKS;
 
 // Gram factors of the four reduced-coordinate classes: 0 point-point,
 // 1 point-edge, 2 point-plane, 3 line-line (3x3 row-major, upper)
@@ -881,7 +887,7 @@ __device__ __forceinline__ void pp_term(int f, const int4* __restrict__ termv, c
     }
 }
 
-__global__ void __launch_bounds__(32 * kBarWarps) k_barrier(const DevStatus* __restrict__ cst, const int* tlist, long cap,
+__global__ void __launch_bounds__(32 * kBarWarps, kBarMinBlocks) k_barrier(const DevStatus* __restrict__ cst, const int* tlist, long cap,
                                                             const int4* __restrict__ termv,
                                                             const int* __restrict__ tmeta,
                                                             const double* __restrict__ teps,

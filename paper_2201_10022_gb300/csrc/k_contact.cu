@@ -208,7 +208,12 @@ __global__ void k_enumerate(const int2* __restrict__ P, const DevStatus* __restr
 // (body pair, 32 candidates), the minimum time of impact by an atomic
 // minimum on the bits of the positive double (exact, order-independent):
 // over the scene, and over the body pair's contact island (the island of its
-// dynamic body; every island's bound starts at 1)
+// dynamic body; every island's bound starts at 1).  Every candidate publishes
+// its time as soon as it has it, and a candidate still advancing stops once
+// its island's published bound is below its time (the island's minimum is
+// unchanged by that, see accd): a sliding contact with a tiny gap no longer
+// advances to t = 1 in thousands of steps when its island's step is already
+// bounded far below.
 __global__ void k_ccd_chunks(const DevStatus* __restrict__ cst, const int2* cand, const int* ccount, const int* tri,
                              const int* edge, const double4* x, const double4* dx, int maxc, int nch, double ccd_s,
                              int ccd_max, const int2* __restrict__ P, const uint8_t* __restrict__ is_static,
@@ -220,9 +225,12 @@ __global__ void k_ccd_chunks(const DevStatus* __restrict__ cst, const int2* cand
   for (long w = (long)blockIdx.x * (blockDim.x >> 5) + warp; w < nw; w += nwarps) {
     const int p = (int)(w / nch), c = (int)(w - (long)p * nch);
     const int n = min(ccount[p], maxc);
+    if (c * 32 >= n) continue;
     const int k = c * 32 + lane;
     double t = 1.0;
     if (k < n) {
+      const int2 pr = P[p];
+      unsigned long long* bound = isl_toi + (is_static[pr.x] ? isl[pr.y] : isl[pr.x]);
       const int2 cc = cand[(size_t)p * maxc + k];
       const int kind = (unsigned)cc.x >> 31, i = cc.x & 0x7fffffff;
       int v[4];
@@ -232,16 +240,12 @@ __global__ void k_ccd_chunks(const DevStatus* __restrict__ cst, const int2* cand
         xs[m] = mk(x[v[m]]);
         ds[m] = mk(dx[v[m]]);
       }
-      if (accd(kind, xs, ds, ccd_s, 1.0, ccd_max, t)) set_flag(st, ST_CCD_MAXITER);
-    }
-    for (int o = 16; o > 0; o >>= 1) t = fmin(t, __shfl_xor_sync(kFull, t, o));
-    if (lane == 0 && t < 1.0) {
-      const int2 pr = P[p];
-      const int is = is_static[pr.x] ? isl[pr.y] : isl[pr.x];
-      atomicMin(&isl_toi[is], (unsigned long long)__double_as_longlong(t));
+      if (accd(kind, xs, ds, ccd_s, 1.0, ccd_max, t, bound)) set_flag(st, ST_CCD_MAXITER);
+      if (t < 1.0) atomicMin(bound, (unsigned long long)__double_as_longlong(t));
     }
     tmin = fmin(tmin, t);
   }
+  for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_xor_sync(kFull, tmin, o));
   if (lane == 0 && tmin < 1.0) atomicMin(&st->toi_bits, (unsigned long long)__double_as_longlong(tmin));
 }
 

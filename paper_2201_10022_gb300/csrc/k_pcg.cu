@@ -651,7 +651,9 @@ __global__ void __launch_bounds__(256) k_cluster_factor(const DevStatus* __restr
                                                         const int2* P, const double* pblk, double* fac, int* ok,
                                                         DevStatus* st) {
   extern __shared__ double A[];
-  __shared__ int s_fail;
+  __shared__ int s_fail, s_npair;
+  __shared__ int s_rows[kClusterMax + 1];
+  __shared__ int3 s_pair[kClusterMax * (kClusterMax - 1) / 2];  // (pair, row member, column member)
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nclu = cst->n_clusters, np = cst->np;
   for (int c = blockIdx.x; c < nclu; c += gridDim.x) {
@@ -660,25 +662,40 @@ __global__ void __launch_bounds__(256) k_cluster_factor(const DevStatus* __restr
     const int N = 12 * n;
     const long NT = ptri(N, 0);
     for (long i = tid; i < NT; i += nt) A[i] = 0.0;
-    if (tid == 0) s_fail = 0;
+    if (tid == 0) {
+      s_fail = 0;
+      s_npair = 0;
+      // the members' body-pair rows, concatenated
+      s_rows[0] = 0;
+      for (int i = 0; i < n; ++i) {
+        const int b = c_perm[m0 + i];
+        s_rows[i + 1] = s_rows[i] + max(0, min(rowoff[b + 1], np) - rowoff[b]);
+      }
+    }
     __syncthreads();
     for (int t = tid; t < n * 144; t += nt) {
       const int i = t / 144, e = t - 144 * i, r = e / 12, cc = e % 12;
       if (cc <= r) A[ptri(12 * i + r, 12 * i + cc)] = D[144L * c_perm[m0 + i] + e];
     }
-    for (int i = 0; i < n; ++i) {
-      const int b = c_perm[m0 + i];
-      for (int p = rowoff[b]; p < min(rowoff[b + 1], np); ++p) {
-        const int o = P[p].y;
-        if (c_of[o] != c) continue;
-        const int j = c_loc[o];
-        for (int e = tid; e < 144; e += nt) {
-          const double h = pblk[(size_t)p * kBlkStride + e];  // H_bo(r, cc): row of b, column of o
-          const int r = e / 12, cc = e % 12;
-          if (i > j) A[ptri(12 * i + r, 12 * j + cc)] = h;
-          else A[ptri(12 * j + cc, 12 * i + r)] = h;
-        }
-      }
+    // the body pairs between members: every row of every member tested in
+    // parallel (each pair is listed once, in the row of its first body)
+    for (int t = tid; t < s_rows[n]; t += nt) {
+      int i = 0;
+      while (t >= s_rows[i + 1]) ++i;
+      const int p = rowoff[c_perm[m0 + i]] + (t - s_rows[i]);
+      const int o = P[p].y;
+      if (c_of[o] == c) s_pair[atomicAdd(&s_npair, 1)] = make_int3(p, i, c_loc[o]);
+    }
+    __syncthreads();
+    // their blocks H_bo(r, cc) (row of b, column of o), lower triangle
+    for (int t = tid; t < 144 * s_npair; t += nt) {
+      const int k = t / 144, e = t - 144 * k;
+      const int3 q = s_pair[k];
+      const int i = q.y, j = q.z;
+      const double h = pblk[(size_t)q.x * kBlkStride + e];
+      const int r = e / 12, cc = e % 12;
+      if (i > j) A[ptri(12 * i + r, 12 * j + cc)] = h;
+      else A[ptri(12 * j + cc, 12 * i + r)] = h;
     }
     __syncthreads();
     for (int k = 0; k < N; ++k) {
@@ -694,13 +711,13 @@ __global__ void __launch_bounds__(256) k_cluster_factor(const DevStatus* __restr
       const double rk = A[ptri(k, k)];
       for (int i = k + 1 + tid; i < N; i += nt) A[ptri(i, k)] *= rk;
       __syncthreads();
-      const int m = N - k - 1;
-      for (int t = tid; t < m * m; t += nt) {
-        const int ii = t / m, jj = t - m * ii;
-        if (jj <= ii) {
-          const int i = k + 1 + ii, j = k + 1 + jj;
-          A[ptri(i, j)] = fma(-A[ptri(i, k)], A[ptri(j, k)], A[ptri(i, j)]);
-        }
+      // trailing update of the lower triangle: a warp per row, lanes over
+      // the row's columns
+      const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+      for (int i = k + 1 + warp; i < N; i += nwarp) {
+        const double lik = A[ptri(i, k)];
+        double* Ai = A + ptri(i, 0);
+        for (int j = k + 1 + lane; j <= i; j += 32) Ai[j] = fma(-lik, A[ptri(j, k)], Ai[j]);
       }
       __syncthreads();
     }

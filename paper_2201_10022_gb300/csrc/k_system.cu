@@ -343,6 +343,10 @@ __global__ void k_rows(int nb, const uint8_t* is_static, const double* bbox, con
 
 // rows of large bodies: one block scans every body after the large one, in
 // order, with a block-wide ordered compaction; then the friction merge
+// rows of large bodies up to this many entries merge their missing friction
+// neighbours in shared memory
+constexpr int kRowMerge = 6144;
+
 __global__ void k_rows_large(int nb, const uint8_t* is_static, const double* bbox, const float* bbox32, float dh32,
                              double dhat, const int* large_list,
                              const int2* fpairs, const DevStatus* cst, int maxn, int* nbr, int* ncount, DevStatus* st) {
@@ -381,26 +385,25 @@ __global__ void k_rows_large(int nb, const uint8_t* is_static, const double* bbo
       __syncthreads();
     }
     // friction neighbours of the row (fpairs entries with .x == a): the
-    // threads check membership by binary search; the few missing ones are
-    // inserted by one thread
+    // threads check membership by binary search; the missing ones (at most
+    // 256, the row and they at most kRowMerge entries) are merged into the
+    // sorted row in parallel through shared memory, else inserted by one
+    // thread
     __shared__ int frange[2], nmiss;
-    __shared__ int miss[256];
-    if (t == 0) {
+    __shared__ int miss[256], smiss[256];
+    __shared__ int srow[kRowMerge];
+    if (t < 2) {  // first entry with .x >= a (t = 0), first with .x > a (t = 1)
       int lo = 0, hi = nfp;
       while (lo < hi) {
         int mid = (lo + hi) >> 1;
-        if (fpairs[mid].x < a) lo = mid + 1;
+        if (fpairs[mid].x < a + t) lo = mid + 1;
         else hi = mid;
       }
-      int e = lo;
-      while (e < nfp && fpairs[e].x == a) ++e;
-      frange[0] = lo;
-      frange[1] = e;
-      nmiss = 0;
+      frange[t] = lo;
     }
+    if (t == 0) nmiss = 0;
     __syncthreads();
     const int n0 = min(base, maxn);
-    bool overflow_miss = false;
     for (int f = frange[0] + t; f < frange[1]; f += blockDim.x) {
       const int b = fpairs[f].y;
       int lo = 0, hi = n0;
@@ -412,15 +415,54 @@ __global__ void k_rows_large(int nb, const uint8_t* is_static, const double* bbo
       if (!(lo < n0 && out[lo] == b)) {
         int k = atomicAdd(&nmiss, 1);
         if (k < 256) miss[k] = b;
-        else overflow_miss = true;
       }
     }
     __syncthreads();
-    if (t == 0) {
+    const int nm = nmiss;
+    if (nm > 0 && nm <= 256 && base <= maxn && n0 + nm <= kRowMerge) {
+      // sorted misses (distinct body ids: rank = number of smaller ones)
+      for (int i = t; i < nm; i += blockDim.x) {
+        int r = 0;
+        for (int k = 0; k < nm; ++k) r += miss[k] < miss[i];
+        smiss[r] = miss[i];
+      }
+      for (int k = t; k < n0; k += blockDim.x) srow[k] = out[k];
+      __syncthreads();
+      const int total = n0 + nm;
+      // every entry's place in the merged row: its index plus the number of
+      // entries of the other list below it
+      for (int k = t; k < n0; k += blockDim.x) {
+        const int v = srow[k];
+        int lo = 0, hi = nm;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (smiss[mid] < v) lo = mid + 1;
+          else hi = mid;
+        }
+        if (k + lo < maxn) out[k + lo] = v;
+      }
+      for (int i = t; i < nm; i += blockDim.x) {
+        const int v = smiss[i];
+        int lo = 0, hi = n0;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (srow[mid] < v) lo = mid + 1;
+          else hi = mid;
+        }
+        if (i + lo < maxn) out[i + lo] = v;
+      }
+      if (t == 0) {
+        ncount[a] = min(total, maxn);
+        if (total > maxn) {
+          set_flag(st, ST_CAP_ROWS);
+          atomicMax(&st->need_row, total);
+        }
+      }
+    } else if (t == 0) {
       // more misses than the buffer holds: walk every friction neighbour
-      const bool all = nmiss > 256;
-      const int nm = all ? frange[1] - frange[0] : nmiss;
-      for (int i = 0; i < nm; ++i) {
+      const bool all = nm > 256;
+      const int nmw = all ? frange[1] - frange[0] : nm;
+      for (int i = 0; i < nmw; ++i) {
         const int b = all ? fpairs[frange[0] + i].y : miss[i];
         const int n = min(base, maxn);
         int pos = 0;
@@ -438,7 +480,6 @@ __global__ void k_rows_large(int nb, const uint8_t* is_static, const double* bbo
         atomicMax(&st->need_row, base);
       }
     }
-    (void)overflow_miss;
     __syncthreads();
   }
 }
