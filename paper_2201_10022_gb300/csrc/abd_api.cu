@@ -82,6 +82,7 @@ void size_pair_buffers(Scene& s, size_t pcap) {
   grow(s, s.ework, pcap * (size_t)energy_chunks(s));
   grow(s, s.large_asm, pcap);
   grow(s, s.cand, pcap * (size_t)s.maxc);
+  grow(s, s.cdl, pcap * (size_t)s.maxc);
   grow(s, s.act, pcap * (size_t)s.maxc);
   grow(s, s.act_d2, pcap * (size_t)s.maxc);
   grow(s, s.amask, pcap * (size_t)energy_chunks(s));
@@ -589,8 +590,8 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
     const int max_rounds = s.prm.ls_max + 2;
     auto ls_round = [&](bool device) {
       if (device) launch_ls_round_begin(s);
-      launch_island_trial(s);
-      launch_transform(s, s.qtrial.p, s.xt.p);
+      launch_island_trial(s, true);
+      launch_transform(s, s.qtrial.p, s.xt.p, true);
       eval_energy(s, s.qtrial.p, true);
       launch_island_energy(s, 1);
       launch_island_accept(s, !device);
@@ -611,7 +612,7 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
       launch_island_energy(s, 0);
       launch_island_start(s);
       launch_island_trial(s);
-      launch_transform(s, s.qtrial.p, s.xt.p);
+      launch_transform(s, s.qtrial.p, s.xt.p, true);
       eval_energy(s, s.qtrial.p, true);
       launch_island_energy(s, 1);
       launch_island_accept(s);
@@ -1017,6 +1018,7 @@ void abd_destroy(abd_scene* S) {
   release(s, s.P);
   release(s, s.fpairs);
   release(s, s.cand);
+  release(s, s.cdl);
   release(s, s.act);
   release(s, s.termv);
   release(s, s.tmeta);

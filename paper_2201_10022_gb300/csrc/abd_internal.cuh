@@ -212,6 +212,7 @@ struct Scene {
   // candidates / actives per body pair
   int maxc = 0;
   Buf<int2> cand;      // np*maxc: (i | kind << 31, j)
+  Buf<double2> cdl;    // np*maxc: swept candidates' distance at the iterate and its rate bound (CCD pass)
   Buf<int> ccount;
   Buf<int4> act;       // np*maxc: (i | kind << 31, j, type, unused)
   Buf<int> acount, aoff;
@@ -365,7 +366,9 @@ constexpr int kBlkStride = 3 * 144 + 24 + 2;
 void launch_mass_moments(Scene& s);
 void launch_edge_rest(Scene& s);
 void launch_predictor(Scene& s);
-void launch_transform(Scene& s, const double* q, double4* x);
+// pending_only: the line search's trial positions, only for bodies of
+// pending islands
+void launch_transform(Scene& s, const double* q, double4* x, bool pending_only = false);
 void launch_transform_dq(Scene& s, const double* dq);   // dx = J dq, x1 = x + dx
 void launch_body_boxes(Scene& s, bool swept);
 void launch_body_pairs(Scene& s);                       // rows -> P (uses friction pairs)
@@ -430,7 +433,8 @@ void launch_energy_worklist(Scene& s);
 void launch_islands(Scene& s);                 // labels of the current body-pair list
 void launch_island_energy(Scene& s, int which); // 0: E at the iterate from the terms; 1: the trial's
 void launch_island_start(Scene& s);            // each island's step = its CCD bound
-void launch_island_trial(Scene& s);            // qtrial = q + alpha_island dq
+// qtrial = q + alpha_island dq (pending_only: the halving rounds)
+void launch_island_trial(Scene& s, bool pending_only = false);
 // accept or halve each pending island; reset: clear the counts first (else a
 // preceding launch_ls_round_begin has)
 void launch_island_accept(Scene& s, bool reset = true);

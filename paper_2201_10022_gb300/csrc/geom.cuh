@@ -177,10 +177,13 @@ __device__ __forceinline__ double pair_dist2(int kind, const v3* x, int& type) {
 // to; it is re-read every 8 advancement steps and lowers tmax.  A result of
 // tmax then means "no impact before the bound", which leaves the minimum
 // unchanged, so the minimum over all evaluations is exact whatever their
-// timing.
+// timing.  d0_lp (may be null) receives the distance at t = 0 (-1 if not
+// computed) and lp, the bound on the distance's rate of change: the distance
+// at t is at least d0 - t lp.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int accd(int kind, const v3* xin, const v3* dx, double s, double tmax, int max_iter,
-                                    double& toi, const unsigned long long* bound = nullptr) {
+                                    double& toi, const unsigned long long* bound = nullptr,
+                                    double2* d0_lp = nullptr) {
   v3 x[4], p[4];
   v3 mean;
   mean.x = __dmul_rn(__dadd_rn(__dadd_rn(dx[0].x, dx[1].x), __dadd_rn(dx[2].x, dx[3].x)), 0.25);
@@ -203,12 +206,14 @@ __device__ __forceinline__ int accd(int kind, const v3* xin, const v3* dx, doubl
     double mb = nrm[2] > nrm[3] ? nrm[2] : nrm[3];
     lp = __dadd_rn(ma, mb);
   }
+  if (d0_lp) *d0_lp = make_double2(-1.0, lp);  // distance not known yet: no bound
   if (lp == 0.0) {
     toi = tmax;
     return 0;
   }
   int type;
   double d = __dsqrt_rn(pair_dist2(kind, x, type));
+  if (d0_lp) d0_lp->x = d;
   if (d == 0.0) {
     toi = 0.0;
     return 0;

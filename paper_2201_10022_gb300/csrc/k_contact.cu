@@ -217,7 +217,8 @@ __global__ void k_enumerate(const int2* __restrict__ P, const DevStatus* __restr
 __global__ void k_ccd_chunks(const DevStatus* __restrict__ cst, const int2* cand, const int* ccount, const int* tri,
                              const int* edge, const double4* x, const double4* dx, int maxc, int nch, double ccd_s,
                              int ccd_max, const int2* __restrict__ P, const uint8_t* __restrict__ is_static,
-                             const int* __restrict__ isl, unsigned long long* isl_toi, DevStatus* st) {
+                             const int* __restrict__ isl, unsigned long long* isl_toi, double2* cdl,
+                             DevStatus* st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
   const long nw = (long)cst->np * nch;
@@ -240,7 +241,8 @@ __global__ void k_ccd_chunks(const DevStatus* __restrict__ cst, const int2* cand
         xs[m] = mk(x[v[m]]);
         ds[m] = mk(dx[v[m]]);
       }
-      if (accd(kind, xs, ds, ccd_s, 1.0, ccd_max, t, bound)) set_flag(st, ST_CCD_MAXITER);
+      if (accd(kind, xs, ds, ccd_s, 1.0, ccd_max, t, bound, cdl + (size_t)p * maxc + k))
+        set_flag(st, ST_CCD_MAXITER);
       if (t < 1.0) atomicMin(bound, (unsigned long long)__double_as_longlong(t));
     }
     tmin = fmin(tmin, t);
@@ -454,10 +456,17 @@ __global__ void k_friction_eval(const DevStatus* __restrict__ cst, const FricRec
 //
 // With a work list (the line search), only the slots that hold candidates are
 // visited (ework[0 .. n_ework)); the other slots are neither read nor written.
+// In the line search every candidate also carries, from the CCD pass over
+// the same step, its distance d0 at the iterate and the bound lp on the
+// distance's rate of change along the step: at the island's trial step alpha
+// the distance is at least d0 - alpha lp, so where that exceeds d-hat (with a
+// margin of 1e-6 d-hat against rounding) the barrier is zero and the
+// distance is not evaluated.
 __global__ void k_pair_energy(const DevStatus* __restrict__ cst, const int2* cand, const int* ccount,
                               const int* tri, const int* edge, const double4* x, const double* l2e, double dhat,
                               double kappa, int maxc, int nch, double* Ep, const int2* P, const uint8_t* is_static,
-                              const int* isl, const int* lstate, const int* ework, DevStatus* st) {
+                              const int* isl, const int* lstate, const int* ework, const double2* cdl,
+                              const double* alpha, DevStatus* st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
   const long nw = ework ? (long)cst->n_ework : (long)cst->np * nch;
@@ -465,14 +474,22 @@ __global__ void k_pair_energy(const DevStatus* __restrict__ cst, const int2* can
   for (long t = (long)blockIdx.x * (blockDim.x >> 5) + warp; t < nw; t += nwarps) {
     const long w = ework ? (long)ework[t] : t;
     const int p = (int)(w / nch), c = (int)(w - (long)p * nch);
+    double a_isl = -1.0;
     if (isl) {  // line-search rounds: pairs of islands already accepted are not needed
       const int2 pr = P[p];
-      if (lstate[2 * (is_static[pr.x] ? isl[pr.y] : isl[pr.x])] != 0) continue;
+      const int is = is_static[pr.x] ? isl[pr.y] : isl[pr.x];
+      if (lstate[2 * is] != 0) continue;
+      if (cdl) a_isl = alpha[is];
     }
     const int n = min(ccount[p], maxc);
     const int k = c * 32 + lane;
     double e = 0.0;
-    if (k < n) {
+    bool far = false;
+    if (k < n && a_isl >= 0.0) {
+      const double2 dl = cdl[(size_t)p * maxc + k];
+      far = dl.x >= 0.0 && dl.x - a_isl * dl.y > dhat * (1.0 + 1e-6);
+    }
+    if (k < n && !far) {
       int2 cc = cand[(size_t)p * maxc + k];
       int kind = (unsigned)cc.x >> 31, i = cc.x & 0x7fffffff;
       int v[4];
@@ -535,7 +552,7 @@ void launch_enumerate(Scene& s, bool swept, bool ccd) {
     counted(s);
     k_ccd_chunks<<<grid_for(2L * s.nb * nch, 8, sm_grid(s, 32)), 256, 0, s.stream>>>(
         s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, s.x.p, s.dx.p, s.maxc, nch, s.prm.ccd_s, s.prm.ccd_max, s.P.p,
-        s.is_static.p, s.isl.p, s.isl_toi.p, s.st);
+        s.is_static.p, s.isl.p, s.isl_toi.p, s.cdl.p, s.st);
   }
 }
 
@@ -573,7 +590,8 @@ void launch_pair_energy(Scene& s, const double4* x, bool pending_only) {
   k_pair_energy<<<grid, 256, 0, s.stream>>>(s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.l2e.p,
                                             s.prm.dhat, s.prm.kappa, s.maxc, nch, s.Epair.p, s.P.p,
                                             s.is_static.p, pending_only ? s.isl.p : nullptr, s.isl_state.p,
-                                            pending_only ? s.ework.p : nullptr, s.st);
+                                            pending_only ? s.ework.p : nullptr, pending_only ? s.cdl.p : nullptr,
+                                            s.isl_alpha.p, s.st);
 }
 
 void launch_energy_worklist(Scene& s) {

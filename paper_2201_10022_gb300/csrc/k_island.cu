@@ -283,26 +283,36 @@ __global__ void k_isl_start(int nb, const uint8_t* is_static, const int* isl, co
   }
 }
 
-// trial state: q + alpha_island dq (static bodies keep q)
+// trial state: q + alpha_island dq (static bodies keep q); with lstate (the
+// halving rounds) only for the bodies of pending islands (an accepted
+// island's trial state stays as accepted)
 __global__ void k_isl_trial(int nb, const uint8_t* is_static, const int* isl, const double* alpha, const double* q,
-                            const double* dq, double* qtrial) {
+                            const double* dq, const int* lstate, double* qtrial) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 12 * nb; i += gridDim.x * blockDim.x) {
     const int b = i / 12;
-    qtrial[i] = is_static[b] ? q[i] : fma(alpha[isl[b]], dq[i], q[i]);
+    if (is_static[b]) {
+      qtrial[i] = q[i];
+      continue;
+    }
+    const int is = isl[b];
+    if (lstate && lstate[2 * is] != 0) continue;
+    qtrial[i] = fma(alpha[is], dq[i], q[i]);
   }
 }
 
 // acceptance of each pending island: E_i(trial) <= E_i(q) + slack (|E_i(q)| + 1)
 // accepts; otherwise the island's step is halved (at most ls_max times).  The
-// trial accumulators are cleared for the next trial; the counts of pending
-// islands, of islands and of failed islands go to the status word.
+// trial accumulators of the islands that were pending (the only ones a trial
+// adds to) are cleared for the next trial; the counts of pending islands, of
+// islands and of failed islands go to the status word.
 __global__ void k_isl_accept(int nb, const uint8_t* is_static, const int* isl, double slack_rel, int ls_max,
                              unsigned long long* E, double* alpha, int* lstate, DevStatus* st) {
   int pending = 0, islands = 0, failed = 0, halv = 0;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
     if (is_static[b] || isl[b] != b) continue;
     ++islands;
-    if (lstate[2 * b] == 0) {
+    const bool was_pending = lstate[2 * b] == 0;
+    if (was_pending) {
       const double e0 = fx_value(E + 16L * b) - fx_value(E + 16L * b + 4);
       const double et = fx_value(E + 16L * b + 8) - fx_value(E + 16L * b + 12);
       if (et <= e0 + slack_rel * (fabs(e0) + 1.0)) {
@@ -316,8 +326,11 @@ __global__ void k_isl_accept(int nb, const uint8_t* is_static, const int* isl, d
       }
     }
     halv = max(halv, lstate[2 * b + 1]);
+    // only pending islands accumulate trial sums: clear those
+    if (was_pending) {
 #pragma unroll
-    for (int k = 8; k < 16; ++k) E[16L * b + k] = 0ull;
+      for (int k = 8; k < 16; ++k) E[16L * b + k] = 0ull;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     pending += __shfl_xor_sync(kFull, pending, o);
@@ -385,10 +398,11 @@ void launch_island_start(Scene& s) {
       s.nb, s.is_static.p, s.isl.p, s.isl_toi.p, s.isl_step.p, s.newton_tol, s.isl_alpha.p, s.isl_state.p);
 }
 
-void launch_island_trial(Scene& s) {
+void launch_island_trial(Scene& s, bool pending_only) {
   counted(s);
   k_isl_trial<<<grid_n(12L * s.nb, 256, sm_grid(s, 8)), 256, 0, s.stream>>>(
-      s.nb, s.is_static.p, s.isl.p, s.isl_alpha.p, s.q.p, s.dq.p, s.qtrial.p);
+      s.nb, s.is_static.p, s.isl.p, s.isl_alpha.p, s.q.p, s.dq.p, pending_only ? s.isl_state.p : nullptr,
+      s.qtrial.p);
 }
 
 void launch_island_accept(Scene& s, bool reset) {

@@ -100,10 +100,15 @@ __device__ __forceinline__ double4 affine(const double* q, double4 xb) {
   return r;
 }
 
-__global__ void k_transform(int nv, const int* vbody, const double4* xbar, const double* q, double4* x) {
+// vertex positions x = J(xbar) q; with isl (the line search's trial
+// positions) only the vertices of bodies whose island is still pending
+__global__ void k_transform(int nv, const int* vbody, const double4* xbar, const double* q, double4* x,
+                            const int* isl, const int* lstate) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nv) return;
-  x[v] = affine(q + 12 * vbody[v], xbar[v]);
+  const int b = vbody[v];
+  if (isl && lstate[2 * isl[b]] != 0) return;
+  x[v] = affine(q + 12 * b, xbar[v]);
 }
 
 __global__ void k_transform_dq(int nv, const int* vbody, const double4* xbar, const double* dq, const double4* x,
@@ -1262,9 +1267,10 @@ void launch_predictor(Scene& s) {
                                                         s.qtilde.p);
 }
 
-void launch_transform(Scene& s, const double* q, double4* x) {
+void launch_transform(Scene& s, const double* q, double4* x, bool pending_only) {
   counted(s);
-  k_transform<<<blocks(s.nv, 256), 256, 0, s.stream>>>(s.nv, s.vbody.p, s.xbar.p, q, x);
+  k_transform<<<blocks(s.nv, 256), 256, 0, s.stream>>>(s.nv, s.vbody.p, s.xbar.p, q, x,
+                                                       pending_only ? s.isl.p : nullptr, s.isl_state.p);
 }
 
 void launch_transform_dq(Scene& s, const double* dq) {
