@@ -237,10 +237,10 @@ ABD_API abd_status abd_step(abd_scene* s, int nsteps, abd_step_stats* stats);
  * cluster_max: the PCG's cluster block-Jacobi preconditioner cuts every
  * contact island (in breadth-first order) into runs of at most cluster_max
  * bodies and factors each run densely (one SM per run, (12 n)^3 / 3 flop);
- * 1 = plain block-Jacobi; 0 = the default, 16 (the largest accepted).
- * Larger runs cost more per factorisation and usually fewer PCG iterations;
- * the Newton directions differ only within the PCG tolerance.  Values
- * outside 0..16 return ABD_ERR_INVALID_ARG. */
+ * 1 = plain block-Jacobi; 0 = the default, 12; at most 16.  Larger runs
+ * cost more per factorisation and usually fewer PCG iterations; the Newton
+ * directions differ only within the PCG tolerance.  Values outside 0..16
+ * return ABD_ERR_INVALID_ARG. */
 typedef struct {
   int grid_div;
   int cluster_max;

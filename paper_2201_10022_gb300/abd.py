@@ -438,7 +438,7 @@ class AbdScene:
 
     def set_tuning(self, grid_div=1, cluster_max=0):
         """grid_div: divisor of the device-sized grids (1..64); cluster_max:
-        bodies per preconditioner cluster (1..16, 0 = the default 16)"""
+        bodies per preconditioner cluster (1..16, 0 = the default 12)"""
         t = abd_tuning()
         t.grid_div = int(grid_div)
         t.cluster_max = int(cluster_max)

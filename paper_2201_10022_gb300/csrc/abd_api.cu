@@ -240,20 +240,32 @@ void build_clusters_host(Scene& s) {
     }
   }
   island_start.push_back(nd);
-  int nc = 0;
+  // runs of at most cluster_max bodies of each island's order; the clusters
+  // are then listed largest first (stable), so that the largest ones, which
+  // set the time of the factorisation and of every preconditioner
+  // application, go to different SMs (the kernels stride over clusters by
+  // block first); each cluster's result does not depend on its place
+  std::vector<int2> runs;  // (first index into the island order, members)
+  for (size_t k = 0; k + 1 < island_start.size(); ++k)
+    for (int c0 = island_start[k]; c0 < island_start[k + 1]; c0 += s.cluster_max)
+      runs.push_back(make_int2(c0, std::min(s.cluster_max, island_start[k + 1] - c0)));
+  std::stable_sort(runs.begin(), runs.end(), [](const int2& u, const int2& v) { return u.y > v.y; });
+  s.perm_tmp.assign(perm, perm + nd);
+  int nc = 0, m = 0;
   long long fo = 0;
-  for (size_t k = 0; k + 1 < island_start.size(); ++k) {
-    for (int c0 = island_start[k]; c0 < island_start[k + 1]; c0 += s.cluster_max) {
-      const int n = std::min(s.cluster_max, island_start[k + 1] - c0);
-      off[nc] = c0;
-      foff[nc] = fo;
-      if (n >= 2) fo += (long long)(12 * n) * (12 * n + 1) / 2;
-      for (int i = 0; i < n; ++i) {
-        cof[perm[c0 + i]] = nc;
-        loc[perm[c0 + i]] = i;
-      }
-      ++nc;
+  for (const int2& r : runs) {
+    const int n = r.y;
+    off[nc] = m;
+    foff[nc] = fo;
+    if (n >= 2) fo += (long long)(12 * n) * (12 * n + 1) / 2;
+    for (int i = 0; i < n; ++i) {
+      const int b = s.perm_tmp[r.x + i];
+      perm[m + i] = b;
+      cof[b] = nc;
+      loc[b] = i;
     }
+    m += n;
+    ++nc;
   }
   off[nc] = nd;
   foff[nc] = fo;
@@ -605,7 +617,6 @@ abd_status newton_step(Scene& s, abd_step_stats* stats) {
       on_side(s, 0, 0, [&]() { launch_max_step(s); });
       launch_reset_toi(s);
       broad_and_enumerate(s, true, true);
-      launch_energy_worklist(s);
       // per contact island: E at q from the system's terms (before the
       // trial's energy pass overwrites the body and friction energies), the
       // step = the island's CCD bound, the first trial and its acceptance
@@ -1325,7 +1336,7 @@ abd_status abd_set_tuning(abd_scene* S, const abd_tuning* t) {
   if (!S || !t || t->grid_div < 1 || t->grid_div > 64 || t->cluster_max < 0 || t->cluster_max > kClusterMax)
     return ABD_ERR_INVALID_ARG;
   Scene& s = S->s;
-  s.cluster_max = t->cluster_max ? t->cluster_max : kClusterMax;
+  s.cluster_max = t->cluster_max ? t->cluster_max : kClusterDefault;
   if (t->grid_div != s.grid_div) {
     s.grid_div = t->grid_div;
     ++s.gen;  // the captured sequences hold the old grids

@@ -141,7 +141,8 @@ struct Prof {
 };
 
 // ---- scene ------------------------------------------------------------------
-constexpr int kClusterMax = 16;  // largest preconditioner cluster (bodies)
+constexpr int kClusterMax = 16;      // largest preconditioner cluster (bodies)
+constexpr int kClusterDefault = 12;  // default run length (abd_tuning.cluster_max = 0)
 
 struct Scene {
   abd_params prm{};
@@ -164,6 +165,7 @@ struct Scene {
     cudaGraph_t loop_body = nullptr;
     long loop_nlaunch = 0;
   };
+  std::vector<int> perm_tmp;     // host scratch of the cluster build
   Segment* capturing = nullptr;  // the segment being captured (run_segment)
   bool loop_graphs = true;       // device-side loops inside segments (off after a failed build)
   long gen = 0;  // bumped on every buffer (re)allocation
@@ -181,7 +183,7 @@ struct Scene {
   cudaEvent_t ev_fork[5] = {}, ev_join[5] = {};
   int device = 0;    // CUDA device the scene was created on
   int grid_div = 1;  // divisor of the device-sized grids (abd_tuning)
-  int cluster_max = kClusterMax;  // bodies per preconditioner cluster (abd_tuning)
+  int cluster_max = kClusterDefault;  // bodies per preconditioner cluster (abd_tuning)
   std::string err;
 
   // topology and body constants
@@ -425,8 +427,9 @@ void launch_barrier(Scene& s, int project, long cap);
 void launch_friction_lag(Scene& s);
 void launch_friction_eval(Scene& s, const double4* x, bool derivs, bool pending_only = false);
 void launch_pair_energy(Scene& s, const double4* x, bool pending_only = false);  // energy only, over candidates
-// the (body pair, chunk) slots that hold candidates, for the line search's
-// energy passes (after an enumeration)
+// the (body pair, chunk) slots that hold candidates, for every pass over
+// the candidates (CCD, active set, the line search's energy passes); part of
+// every enumeration
 void launch_energy_worklist(Scene& s);
 
 // ---- launchers (k_island.cu) -------------------------------------------------

@@ -218,13 +218,14 @@ __global__ void k_ccd_chunks(const DevStatus* __restrict__ cst, const int2* cand
                              const int* edge, const double4* x, const double4* dx, int maxc, int nch, double ccd_s,
                              int ccd_max, const int2* __restrict__ P, const uint8_t* __restrict__ is_static,
                              const int* __restrict__ isl, unsigned long long* isl_toi, double2* cdl,
-                             DevStatus* st) {
+                             const int* __restrict__ ework, DevStatus* st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
-  const long nw = (long)cst->np * nch;
+  const long nw = cst->n_ework;  // the (body pair, chunk) slots holding candidates
   double tmin = 1.0;
-  for (long w = (long)blockIdx.x * (blockDim.x >> 5) + warp; w < nw; w += nwarps) {
-    const int p = (int)(w / nch), c = (int)(w - (long)p * nch);
+  for (long tw = (long)blockIdx.x * (blockDim.x >> 5) + warp; tw < nw; tw += nwarps) {
+    const int w = ework[tw];
+    const int p = w / nch, c = w - p * nch;
     const int n = min(ccount[p], maxc);
     if (c * 32 >= n) continue;
     const int k = c * 32 + lane;
@@ -256,13 +257,14 @@ __global__ void k_ccd_chunks(const DevStatus* __restrict__ cst, const int2* cand
 // and the chunk's membership mask
 __global__ void k_active(const DevStatus* __restrict__ cst, const int2* cand, const int* ccount, const int* tri,
                          const int* edge, const double4* x, double dhat, int maxc, int nch, int4* act, double* act_d2,
-                         unsigned* amask, DevStatus* st) {
+                         unsigned* amask, const int* __restrict__ ework, DevStatus* st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
-  const long nw = (long)cst->np * nch;
+  const long nw = cst->n_ework;  // the (body pair, chunk) slots holding candidates
   const double dh2 = __dmul_rn(dhat, dhat);
-  for (long w = (long)blockIdx.x * (blockDim.x >> 5) + warp; w < nw; w += nwarps) {
-    const int p = (int)(w / nch), c = (int)(w - (long)p * nch);
+  for (long tw = (long)blockIdx.x * (blockDim.x >> 5) + warp; tw < nw; tw += nwarps) {
+    const int w = ework[tw];
+    const int p = w / nch, c = w - p * nch;
     const int n = min(ccount[p], maxc);
     if (c * 32 >= n) continue;
     const int k = c * 32 + lane;
@@ -547,12 +549,13 @@ void launch_enumerate(Scene& s, bool swept, bool ccd) {
   k_enumerate<<<grid, threads, 0, s.stream>>>(s.P.p, s.st, s.vbeg.p, s.tbeg.p, s.ebeg.p, s.tri.p, s.edge.p, s.x.p,
                                               swept ? s.x1.p : nullptr, s.bbox.p, s.prm.dhat, s.maxc, s.cand.p,
                                               s.ccount.p, s.st);
+  launch_energy_worklist(s);  // the slots holding candidates, for every pass over them
   if (ccd) {
     const int nch = energy_chunks(s);
     counted(s);
     k_ccd_chunks<<<grid_for(2L * s.nb * nch, 8, sm_grid(s, 32)), 256, 0, s.stream>>>(
         s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, s.x.p, s.dx.p, s.maxc, nch, s.prm.ccd_s, s.prm.ccd_max, s.P.p,
-        s.is_static.p, s.isl.p, s.isl_toi.p, s.cdl.p, s.st);
+        s.is_static.p, s.isl.p, s.isl_toi.p, s.cdl.p, s.ework.p, s.st);
   }
 }
 
@@ -563,7 +566,7 @@ void launch_active(Scene& s, const double4* x) {
   // grid-stride over the device's pair count
   k_active<<<grid_for(2L * s.nb * nch, 8, sm_grid(s, 32)), 256, 0, s.stream>>>(
       s.st, s.cand.p, s.ccount.p, s.tri.p, s.edge.p, x, s.prm.dhat, s.maxc, nch, s.act.p, s.act_d2.p, s.amask.p,
-      s.st);
+      s.ework.p, s.st);
   k_active_compact<<<grid_for(2L * s.nb, 8, sm_grid(s, 16)), 256, 0, s.stream>>>(
       s.st, s.ccount.p, s.maxc, nch, s.amask.p, s.act.p, s.act_d2.p, s.acount.p);
 }

@@ -386,11 +386,12 @@ template <typename T>
 __device__ void phase_update(const PcgArgs& a, int k, T alpha, const T* __restrict__ Minv, T* x, T* r, T* z,
                              const T* p0, const T* p1, const T* Ap, double* part, double* ybuf) {
   const int lane = threadIdx.x & 31;
-  const int wgrid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const T* pk = (k & 1) ? p1 : p0;
   const int nclu = *a.nclu;
-  for (int c = wgrid; c < nclu; c += nw) {
+  // block-first order: consecutive clusters (listed largest first) go to
+  // different blocks, hence different SMs
+  for (int c = (threadIdx.x >> 5) * gridDim.x + blockIdx.x; c < nclu; c += nw) {
     const int m0 = a.c_off[c], n = a.c_off[c + 1] - m0;
     for (int i = 0; i < n; ++i) {
       const int b = a.c_perm[m0 + i];
@@ -423,7 +424,9 @@ __device__ void phase_start(const PcgArgs& a, const TR* rhs, double sign, const 
     if (lane == 0) part[a.nb + b] = part[2 * a.nb + b] = 0.0;
   }
   const int nclu = *a.nclu;
-  for (int c = wgrid; c < nclu; c += nw) {
+  // block-first order: consecutive clusters (listed largest first) go to
+  // different blocks, hence different SMs
+  for (int c = (threadIdx.x >> 5) * gridDim.x + blockIdx.x; c < nclu; c += nw) {
     const int m0 = a.c_off[c], n = a.c_off[c + 1] - m0;
     for (int i = 0; i < n; ++i) {
       const int b = a.c_perm[m0 + i];
