@@ -657,6 +657,10 @@ __global__ void __launch_bounds__(256) k_cluster_factor(const DevStatus* __restr
   __shared__ int s_fail, s_npair;
   __shared__ int s_rows[kClusterMax + 1];
   __shared__ int3 s_pair[kClusterMax * (kClusterMax - 1) / 2];  // (pair, row member, column member)
+  // block structure of the factor: bit J of s_mask[I] (J <= I) marks the
+  // 12x12 block (I, J) as possibly nonzero (a body pair, or fill); bit I of
+  // s_col[K] marks the blocks (I, K) of block column K
+  __shared__ unsigned s_mask[kClusterMax], s_col[kClusterMax];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nclu = cst->n_clusters, np = cst->np;
   for (int c = blockIdx.x; c < nclu; c += gridDim.x) {
@@ -665,6 +669,7 @@ __global__ void __launch_bounds__(256) k_cluster_factor(const DevStatus* __restr
     const int N = 12 * n;
     const long NT = ptri(N, 0);
     for (long i = tid; i < NT; i += nt) A[i] = 0.0;
+    if (tid < n) s_mask[tid] = 1u << tid;
     if (tid == 0) {
       s_fail = 0;
       s_npair = 0;
@@ -687,9 +692,28 @@ __global__ void __launch_bounds__(256) k_cluster_factor(const DevStatus* __restr
       while (t >= s_rows[i + 1]) ++i;
       const int p = rowoff[c_perm[m0 + i]] + (t - s_rows[i]);
       const int o = P[p].y;
-      if (c_of[o] == c) s_pair[atomicAdd(&s_npair, 1)] = make_int3(p, i, c_loc[o]);
+      if (c_of[o] == c) {
+        const int j = c_loc[o];
+        s_pair[atomicAdd(&s_npair, 1)] = make_int3(p, i, j);
+        atomicOr(&s_mask[max(i, j)], 1u << min(i, j));
+      }
     }
     __syncthreads();
+    // symbolic factorisation: blocks (I, K) and (J, K) of a column K, K < J <=
+    // I, fill block (I, J)
+    if (tid == 0) {
+      for (int K = 0; K < n; ++K) {
+        unsigned col = 0;
+        for (int I = K; I < n; ++I)
+          if ((s_mask[I] >> K) & 1u) col |= 1u << I;
+        s_col[K] = col;
+        const unsigned below = col & ~((2u << K) - 1u);  // rows I > K
+        for (unsigned m = below; m; m &= m - 1) {
+          const int I = __ffs(m) - 1;
+          s_mask[I] |= below & ((2u << I) - 1u);
+        }
+      }
+    }
     // their blocks H_bo(r, cc) (row of b, column of o), lower triangle
     for (int t = tid; t < 144 * s_npair; t += nt) {
       const int k = t / 144, e = t - 144 * k;
@@ -701,26 +725,73 @@ __global__ void __launch_bounds__(256) k_cluster_factor(const DevStatus* __restr
       else A[ptri(12 * j + cc, 12 * i + r)] = h;
     }
     __syncthreads();
-    for (int k = 0; k < N; ++k) {
-      if (tid == 0) {
-        double d = A[ptri(k, k)];
-        if (!(d > 0.0)) {
-          s_fail = 1;
-          d = 1.0;
+    // right-looking Cholesky by 12-column block columns (a body each).  For
+    // every entry the updates come in the order of the columns, as in the
+    // column-by-column algorithm, so the factor is the same; entries of blocks
+    // outside the symbolic structure stay exactly zero, so their scaling and
+    // updates (products with an exact zero) are skipped.
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+    for (int K = 0; K < n; ++K) {
+      const unsigned colk = s_col[K];
+      const int o = 12 * K;
+      // (1) the diagonal block, one warp: pivots (reciprocals stored on the
+      // diagonal), column scaling and updates inside the block
+      if (warp == 0) {
+        for (int cc = 0; cc < 12; ++cc) {
+          const int k = o + cc;
+          if (lane == 0) {
+            double d = A[ptri(k, k)];
+            if (!(d > 0.0)) {
+              s_fail = 1;
+              d = 1.0;
+            }
+            A[ptri(k, k)] = 1.0 / sqrt(d);
+          }
+          __syncwarp();
+          const double rk = A[ptri(k, k)];
+          if (lane > cc && lane < 12) A[ptri(o + lane, k)] *= rk;
+          __syncwarp();
+          // entries (r, j) of the block with cc < j <= r < 12
+          for (int e = lane; e < 144; e += 32) {
+            const int r = e / 12, j = e - 12 * r;
+            if (j > cc && j <= r) A[ptri(o + r, o + j)] = fma(-A[ptri(o + r, k)], A[ptri(o + j, k)], A[ptri(o + r, o + j)]);
+          }
+          __syncwarp();
         }
-        A[ptri(k, k)] = 1.0 / sqrt(d);
       }
       __syncthreads();
-      const double rk = A[ptri(k, k)];
-      for (int i = k + 1 + tid; i < N; i += nt) A[ptri(i, k)] *= rk;
-      __syncthreads();
-      // trailing update of the lower triangle: a warp per row, lanes over
-      // the row's columns
-      const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
-      for (int i = k + 1 + warp; i < N; i += nwarp) {
-        const double lik = A[ptri(i, k)];
+      // (2) the panel below: a thread per row of the column's blocks, its 12
+      // entries solved in column order against the diagonal block
+      for (int i = o + 12 + tid; i < N; i += nt) {
+        if (!((colk >> (i / 12)) & 1u)) continue;
         double* Ai = A + ptri(i, 0);
-        for (int j = k + 1 + lane; j <= i; j += 32) Ai[j] = fma(-lik, A[ptri(j, k)], Ai[j]);
+        for (int cc = 0; cc < 12; ++cc) {
+          const int k = o + cc;
+          double x = Ai[k];
+          const double* Ak = A + ptri(k, 0);
+          for (int c2 = 0; c2 < cc; ++c2) x = fma(-Ai[o + c2], Ak[o + c2], x);
+          Ai[k] = x * Ak[k];
+        }
+      }
+      __syncthreads();
+      // (3) the trailing blocks (I, J), K < J <= I, of the column's blocks: a
+      // warp per row, lanes over the row's columns, the 12 updates in column
+      // order
+      for (int i = o + 12 + warp; i < N; i += nwarp) {
+        if (!((colk >> (i / 12)) & 1u)) continue;
+        const double* Ai = A + ptri(i, 0);
+        double li[12];
+#pragma unroll
+        for (int cc = 0; cc < 12; ++cc) li[cc] = Ai[o + cc];
+        double* Aw = A + ptri(i, 0);
+        for (int j = o + 12 + lane; j <= i; j += 32) {
+          if (!((colk >> (j / 12)) & 1u)) continue;
+          const double* Aj = A + ptri(j, 0) + o;
+          double x = Aw[j];
+#pragma unroll
+          for (int cc = 0; cc < 12; ++cc) x = fma(-li[cc], Aj[cc], x);
+          Aw[j] = x;
+        }
       }
       __syncthreads();
     }
