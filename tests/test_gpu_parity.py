@@ -152,10 +152,12 @@ def test_pcg_solve_matches_direct_solve(abd, name, s):
     assert np.abs(dq.cpu().numpy()[s.is_static == 1]).max(initial=0.0) == 0.0
 
 
-def _trajectory(abd, s, nsteps, **kw):
+def _trajectory_errors(abd, s, nsteps, **kw):
+    """largest vertex distance between the GPU's and the oracle's states
+    after every step"""
     orc = O.Oracle(s)
     gpu = abd.AbdScene(s, newton_tol=orc.newton_tol, **kw)
-    worst = 0.0
+    errs = []
     for k in range(nsteps):
         gpu.step(1)
         r, st = orc.step(1)
@@ -164,14 +166,27 @@ def _trajectory(abd, s, nsteps, **kw):
         qo, _ = orc.get_state()
         xg = orc.vertices(qg.cpu().numpy().reshape(-1))
         xo = orc.vertices(qo.reshape(-1))
-        worst = max(worst, np.abs(xg - xo).max())
-    return worst, orc.l_bbox
+        errs.append(np.abs(xg - xo).max())
+    return np.array(errs), orc.l_bbox
+
+
+def _trajectory(abd, s, nsteps, **kw):
+    errs, L = _trajectory_errors(abd, s, nsteps, **kw)
+    return errs.max(), L
 
 
 def test_trajectory_cube_stack(abd):
+    """the cube stack over its full 100 steps (settling onto the ground and
+    onto one another, then at rest).  Both sides stop each step within the
+    Newton tolerance (1e-9 of the box diagonal) of the step's minimiser, at
+    different points (the GPU takes its line search per contact island), and
+    the next step starts from there: the difference can grow by about the
+    tolerance per step.  Within 1e-8 of the box diagonal over the first 40
+    steps; within 1e-9 per step over all 100 (measured: 2.9e-8)."""
     s = scenes.cube_stack(seed=1)
-    worst, L = _trajectory(abd, s, 40)
-    assert worst <= 1e-8 * L, (worst, L)
+    errs, L = _trajectory_errors(abd, s, 100)
+    assert errs[:40].max() <= 1e-8 * L, (errs[:40].max(), L)
+    assert errs.max() <= 1e-9 * L * len(errs), (errs.max(), L)
 
 
 def test_trajectory_friction_slide(abd):
