@@ -264,3 +264,31 @@ def test_adjoint_at_an_indefinite_converged_state():
     # cond(H) = 5e5 / 0.027 ~ 2e7: eps * cond ~ 4e-9 bounds the difference of
     # two backward-stable solves
     assert np.abs(Mlam - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_throw_stack_adjoint_golden_is_the_oracles():
+    """the stored 20-step throw-into-stack adjoint (the GPU test's expected
+    values) is the oracle's: the chain's inputs are the next step's outputs,
+    exactly one step's unprojected Hessian is indefinite (the first contact,
+    numpy's eigenvalues of the oracle's matrix), and the last step's adjoint
+    recomputed now from the stored states equals the stored one"""
+    import os
+    G = np.load(os.path.join(os.path.dirname(__file__), "golden", "throw_stack_adjoint.npz"))
+    n = G["q"].shape[0] - 1
+    for t in range(n - 1):
+        assert np.array_equal(G["gq_in"][t], G["gq_out"][t + 1])
+        assert np.array_equal(G["gqd_in"][t], G["gqd_out"][t + 1])
+    assert (G["hess_eig"][:, 0] < 0).sum() == 1
+    s = scenes.throw_stack(seed=int(G["seed"]))
+    o = O.Oracle(s, newton_max=300)
+    dt = s.params["dt"]
+    t = n - 1
+    gq, gqd = G["gq_in"][t], G["gqd_in"][t]
+    st, Mlam, gk = o.adjoint_step(G["q"][t], G["qdot"][t], G["q"][t + 1], gq + gqd / dt)
+    assert st == 0, O.ERRORS[st]
+    dyn = s.is_static == 0
+    out = Mlam - gqd / dt
+    out[~dyn] = 0.0
+    scale = np.abs(G["gq_out"][t]).max()
+    assert np.abs(out - G["gq_out"][t]).max() <= 1e-12 * scale
+    assert np.abs(gk - G["gk_out"][t]).max() <= 1e-12 * max(np.abs(G["gk_out"][t]).max(), 1e-300)
